@@ -1,0 +1,191 @@
+/*
+ * dwsolve.h -- C ABI of the GB300 deflated SAP-GCR solver for the
+ * O(a)-improved Wilson-Dirac equation  D psi = eta  (paper eq. (3.9)).
+ *
+ * Method: M. Luescher, "Local coherence and deflation of the low quark
+ * modes in lattice QCD" (Sections 3-6 and Appendix A).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  Lattice L[0] x L[1] x L[2] x L[3], L[0] = time.  Canonical site index
+ *  ((x0*L1 + x1)*L2 + x2)*L3 + x3 (x0 slowest), V = L0*L1*L2*L3.
+ *  Canonical quark field: V x 4 (spin) x 3 (colour) complex numbers, each
+ *  complex stored as two doubles (re, im) -- "complex128[V][4][3]".
+ *  Canonical gauge field: V x 4 (mu) x 3 x 3 complex, U[x][mu] = link from
+ *  x to x+mu, row-major colour matrix.  Links must be SU(3) (unitary,
+ *  det 1): the library stores two rows and rebuilds the third.
+ *
+ *  D psi(x) = (4+m0) psi(x) + c_sw (i/4) sum_{mu,nu} sigma_{mu nu} F_{mu nu}(x) psi(x)
+ *             - 1/2 sum_mu [(1-gamma_mu) U_mu(x) psi(x+mu) + (1+gamma_mu) U_mu(x-mu)^+ psi(x-mu)]
+ *  in the Euclidean chiral basis (gamma_0 = [[0,-1],[-1,0]],
+ *  gamma_k = [[0,-i s_k],[i s_k,0]], gamma_5 = diag(1,1,-1,-1)), clover-leaf
+ *  F_{mu nu}, fermion field antiperiodic in time when requested.
+ *
+ *  "Packed" fields are the library's internal device layout (block-major
+ *  site order, structure of arrays).  Convert with dw_pack / dw_unpack;
+ *  dw_field_bytes gives the size of one packed field.  Packed fields of
+ *  precision DW_F64 hold doubles, DW_F32 floats.
+ *
+ *  Memory: every *_dev pointer is device memory owned by the caller; the
+ *  library never frees it.  Contexts own their internal buffers and free
+ *  them in *_destroy.  Streams: `stream` is a cudaStream_t (NULL = legacy
+ *  default stream); calls are stream-ordered unless documented as
+ *  synchronous.  One context must not be used by two host threads at once.
+ *
+ *  Errors: functions return a dw_status.  Negative values are failures
+ *  (nothing useful was written); positive values are successes with a
+ *  caveat.  No exceptions cross the ABI.
+ */
+#ifndef DWSOLVE_H
+#define DWSOLVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DW_OK = 0,
+  DW_EINVAL = -1,      /* invalid argument, lattice/block mismatch, non-SU(3) links, rank loss */
+  DW_ENOMEM = -2,      /* device allocation failed */
+  DW_ECUDA = -3,       /* a CUDA call failed (message via dw_last_error) */
+  DW_ENOTCONV = 1,     /* iteration limit reached before the tolerance */
+  DW_ILLCOND = 2       /* a diagonal little block was ill-conditioned (Appendix A.2) */
+} dw_status;
+
+typedef enum { DW_F64 = 0, DW_F32 = 1, DW_BF16 = 2 } dw_prec;
+
+typedef enum { DW_OP_FULL = 0, DW_OP_SCHUR = 1 } dw_op;
+
+typedef struct dw_ctx dw_ctx;
+typedef struct dfl_ctx dfl_ctx;
+
+typedef struct {
+  int L[4];            /* lattice extents, L[0] = time; each a multiple of sap_bs[mu] */
+  double m0;           /* bare mass; hopping parameter kappa = 1/(2 m0 + 8) */
+  double csw;          /* Sheikholeslami-Wohlert coefficient */
+  int antiperiodic;    /* 1: antiperiodic fermion boundary in time, 0: periodic */
+  int sap_bs[4];       /* Schwarz block size: even extents, even block count per direction, <= 512 sites */
+} dw_params;
+
+/* Last error message of the calling thread (static storage, never NULL). */
+const char* dw_last_error(void);
+
+/* Create an operator context from host links (canonical layout, FP64).
+ * Builds the clover term F, A(x) = (4+m0) + c_sw (i/4) sigma F and its
+ * inverse per chiral 6x6 block in FP64 (Section 2.1 operator), and FP32
+ * copies.  Synchronous.  Returns DW_EINVAL on bad extents or non-SU(3)
+ * links (|U U^+ - 1| or |det U - 1| above 1e-10). */
+int dw_create(const dw_params* p, const double* links_host, dw_ctx** out);
+void dw_destroy(dw_ctx* ctx);
+
+/* Bytes of one packed field of precision prec (DW_F64 or DW_F32). */
+size_t dw_field_bytes(const dw_ctx* ctx, int prec);
+/* Number of lattice sites V. */
+long long dw_volume(const dw_ctx* ctx);
+
+/* canonical complex128[nrhs][V][4][3] (device)  <->  nrhs packed fields (device). */
+int dw_pack(dw_ctx* ctx, int prec, int nrhs, const double* canon_dev, void* packed_dev, void* stream);
+int dw_unpack(dw_ctx* ctx, int prec, int nrhs, const void* packed_dev, double* canon_dev, void* stream);
+
+/* out = D in (op = DW_OP_FULL) or, on even sites, out = (A_ee - D_eo A_oo^{-1} D_oe) in
+ * with odd sites of out set to zero (op = DW_OP_SCHUR; even-odd Schur complement).
+ * in/out: nrhs packed fields of precision prec; in != out. */
+int dw_apply(dw_ctx* ctx, int prec, int op, int nrhs, const void* in_dev, void* out_dev, void* stream);
+
+/* xi = M_sap rho: Schwarz alternating procedure (Section 6.1) on the
+ * sap_bs blocks, ncy cycles of (black blocks, white blocks), each block
+ * solve = nmr minimal-residual steps on the even-odd preconditioned block
+ * operator with Dirichlet block boundary.  rho, xi: packed, prec
+ * DW_F32 or DW_F64; rho != xi.  Uses internal workspace of the context. */
+int sap_precondition(dw_ctx* ctx, int prec, int ncy, int nmr, int nrhs,
+                     const void* rho_dev, void* xi_dev, void* stream);
+
+typedef struct {
+  int bs[4];           /* deflation block size: multiple of sap_bs, even block count per direction */
+  int Ns;              /* fields per block, 1..32 */
+  int n_inv;           /* inverse-iteration steps (5.1); 0 = use the start fields as they are */
+  int ncy, nmr;        /* M_sap parameters used by the inverse iteration */
+  int basis_prec;      /* DW_BF16: BF16 basis + FP32 little operator copy (mixed path);
+                          DW_F64: FP64 basis (plain path) */
+  int iter_prec;       /* precision of the inverse iteration: DW_F32 or DW_F64 */
+  double cond_max;     /* largest accepted condition number of a diagonal little block (A.2) */
+} dfl_params;
+
+typedef struct {
+  double seconds;          /* wall time of the build */
+  double seconds_little;   /* of which: little operator assembly (A.1)-(A.3) */
+  double max_block_cond;   /* largest condition-number estimate of B_LL */
+  int Nb;                  /* number of deflation blocks */
+  int N;                   /* little dimension Nb * Ns */
+} dfl_info;
+
+/* Build the deflation subspace (Sections 4.2, 5.3) and the little Dirac
+ * operator (3.2), (A.1)-(A.3).  start_canon_dev: Ns random fields,
+ * complex128[Ns][V][4][3] (the random numbers are an input).  Steps:
+ * n_inv x (psi_l <- M_sap psi_l, normalised); block restriction and
+ * Gram-Schmidt (FP64, two passes); optional BF16 rounding of the basis;
+ * FP64 assembly of B_{LL'} from the stored (rounded) basis; inverses of
+ * the diagonal blocks; global-mode deflation data.  Synchronous.
+ * Returns DW_ILLCOND if a diagonal block exceeds cond_max (the context is
+ * still created; the little solver then works on the full system). */
+int deflation_build(dw_ctx* ctx, const dfl_params* p, const double* start_canon_dev,
+                    dfl_ctx** out, dfl_info* info);
+void dfl_destroy(dfl_ctx* d);
+int dfl_dims(const dfl_ctx* d, int* Nb, int* Ns);
+
+/* Little vectors: complex[Nb][Ns] (re, im interleaved) of precision prec,
+ * block index = lexicographic deflation-block coordinate (x0 slowest).
+ * c = Phi^+ psi  (block restriction of (4.1));  psi = Phi c  (prolongation). */
+int dfl_restrict(dfl_ctx* d, int prec, const void* psi_packed_dev, void* c_dev, void* stream);
+int dfl_prolong(dfl_ctx* d, int prec, const void* c_dev, void* psi_packed_dev, void* stream);
+/* The stored basis as canonical FP64 fields complex128[Ns][V][4][3]: field l
+ * is sum over blocks of phi^L_l (dequantised when stored in BF16). */
+int dfl_basis_export(dfl_ctx* d, double* canon_dev, void* stream);
+/* w = A v with the little operator (3.2)/(A.1) (FP64 master copy). */
+int little_apply(dfl_ctx* d, const double* v_dev, double* w_dev, void* stream);
+/* Solve A v = w (6.1) by even-odd preconditioning (A.2), global-mode
+ * deflation (A.3) and GCR (A.4) to ||w - A v|| <= tol ||w|| (measured on
+ * the even-odd deflated system).  prec: DW_F32 (FP32 operator copy) or
+ * DW_F64.  Synchronous with respect to the host (returns the counts). */
+int little_dirac_solve(dfl_ctx* d, int prec, const void* w_dev, void* v_dev, double tol, int maxit,
+                       int* iters, double* relres, void* stream);
+
+typedef struct {
+  double tol;              /* stop when ||eta - D psi|| <= tol ||eta|| (FP64 residual) */
+  int nkv;                 /* Krylov vectors per GCR cycle (restart length) */
+  int nmx;                 /* maximum total GCR steps */
+  int ncy, nmr;            /* M_sap parameters */
+  int mixed;               /* 1: FP32 D/SAP/little + FP64 restarts; 0: everything FP64 */
+  double inner_rtol;       /* mixed: end a cycle when its residual drops by this factor */
+  double little_tol_out;   /* little-solve tolerance outside cycles (A.5), e.g. 1e-12 */
+  double little_tol_in;    /* inside cycles, scaled by ||rho_0|| / ||D xi_k|| (A.5), e.g. 1e-6 */
+  double little_tol_cap;   /* upper limit of the adapted tolerance, e.g. 1e-1 */
+  int little_nkv, little_maxit;
+} sol_params;
+
+typedef struct {
+  int status;              /* dw_status of this right-hand side */
+  int iterations;          /* GCR steps (Krylov vectors generated) */
+  int restarts;
+  int little_iterations;   /* total little GCR steps */
+  int little_solves;
+  double relres;           /* final ||eta - D psi|| / ||eta|| in FP64 */
+  double seconds;          /* wall time */
+  double t_sap, t_dirac, t_project, t_little, t_orth, t_restart;  /* phase times (s), CUDA events */
+} sol_info;
+
+/* Solve D psi = eta (3.9) for nrhs right-hand sides: FGCR (Section 6.2)
+ * right-preconditioned by M_sap, deflated by d (Sections 3.2, 6.1) with
+ * adapted little-solve precision (A.5); d = NULL gives SAP+GCR.
+ * eta, psi: canonical complex128[nrhs][V][4][3] on the device.
+ * info: nrhs entries (may be NULL).  Synchronous. */
+int gcr_solve(dw_ctx* ctx, dfl_ctx* d, const sol_params* p, int nrhs, const double* eta_dev,
+              double* psi_dev, sol_info* info, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DWSOLVE_H */

@@ -1,0 +1,240 @@
+// Vector kernels on packed fields (flat arrays of complex numbers).
+// Reductions accumulate in FP64 with a fixed order: per-thread partial
+// sums, warp shuffles, one partial per CTA, and the last CTA to finish adds
+// the CTA partials in index order -> results are deterministic.
+#include "dw_common.cuh"
+
+namespace {
+
+constexpr int RB = 256;            // reduction CTA size
+constexpr int RGRID = 304;         // 2 CTAs per SM on 152 SMs
+constexpr int MAXK = 16;           // vectors per multi-dot launch
+
+template <typename T, int K>
+struct Ptrs {
+  const T* p[K];
+};
+
+DW_D double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Reduce NV doubles per thread over the grid into out[0..NV).  partial: RGRID*NV scratch.
+template <int NV>
+__device__ void grid_reduce(double* v, double* partial, unsigned* count, double* out) {
+  __shared__ double sh[RB / 32][NV];
+  __shared__ bool last;
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double s = warp_sum(v[k]);
+    if (lane == 0) sh[w][k] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0;
+    for (int j = 0; j < RB / 32; ++j) s += sh[j][threadIdx.x];
+    partial[blockIdx.x * NV + threadIdx.x] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(count, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x < NV) {
+    double s = 0;
+    for (unsigned b = 0; b < gridDim.x; ++b) s += ((volatile double*)partial)[b * NV + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  if (threadIdx.x == 0) *count = 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RB) dot_kernel(const T* __restrict__ a, const T* __restrict__ b, size_t n,
+                                                 double* partial, unsigned* count, double* out) {
+  double v[3] = {0, 0, 0};   // re, im, |a|^2 (norm comes for free)
+  const cplx<T>* A = reinterpret_cast<const cplx<T>*>(a);
+  const cplx<T>* B = reinterpret_cast<const cplx<T>*>(b);
+  for (size_t i = blockIdx.x * (size_t)RB + threadIdx.x; i < n; i += (size_t)gridDim.x * RB) {
+    cplx<T> x = A[i], y = B[i];
+    v[0] += (double)x.re * y.re + (double)x.im * y.im;
+    v[1] += (double)x.re * y.im - (double)x.im * y.re;
+    v[2] += (double)x.re * x.re + (double)x.im * x.im;
+  }
+  grid_reduce<3>(v, partial, count, out);
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(RB) multi_dot_kernel(Ptrs<T, MAXK> vs, const T* __restrict__ b, size_t n,
+                                                       double* partial, unsigned* count, double* out) {
+  double v[2 * K];
+#pragma unroll
+  for (int k = 0; k < 2 * K; ++k) v[k] = 0;
+  const cplx<T>* B = reinterpret_cast<const cplx<T>*>(b);
+  for (size_t i = blockIdx.x * (size_t)RB + threadIdx.x; i < n; i += (size_t)gridDim.x * RB) {
+    cplx<T> y = B[i];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      cplx<T> x = reinterpret_cast<const cplx<T>*>(vs.p[k])[i];
+      v[2 * k] += (double)x.re * y.re + (double)x.im * y.im;
+      v[2 * k + 1] += (double)x.re * y.im - (double)x.im * y.re;
+    }
+  }
+  grid_reduce<2 * K>(v, partial, count, out);
+}
+
+template <typename T>
+__global__ void axpy_kernel(const T* __restrict__ x, T* __restrict__ y, T ar, T ai, size_t n) {
+  cplx<T>* Y = reinterpret_cast<cplx<T>*>(y);
+  const cplx<T>* X = reinterpret_cast<const cplx<T>*>(x);
+  cplx<T> a = {ar, ai};
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    Y[i] += a * X[i];
+}
+template <typename T>
+__global__ void xpby_kernel(const T* __restrict__ x, T* __restrict__ y, T br, T bi, size_t n) {
+  cplx<T>* Y = reinterpret_cast<cplx<T>*>(y);
+  const cplx<T>* X = reinterpret_cast<const cplx<T>*>(x);
+  cplx<T> b = {br, bi};
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    Y[i] = X[i] + b * Y[i];
+}
+template <typename T>
+__global__ void scale_kernel(T* __restrict__ x, T ar, T ai, size_t n) {
+  cplx<T>* X = reinterpret_cast<cplx<T>*>(x);
+  cplx<T> a = {ar, ai};
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    X[i] = a * X[i];
+}
+template <typename Tin, typename Tout>
+__global__ void convert_kernel(const Tin* __restrict__ x, Tout* __restrict__ y, double s, size_t n2) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = (Tout)((double)x[i] * s);
+}
+template <typename T>
+struct Coefs {
+  double c[2 * MAXK];
+};
+template <typename T, int K>
+__global__ void multi_axpy_kernel(Ptrs<T, MAXK> vs, Coefs<T> cf, T* __restrict__ y, size_t n, int mode) {
+  // mode 0: y -= sum c_k v_k ; mode 1: y = sum c_k v_k
+  cplx<T>* Y = reinterpret_cast<cplx<T>*>(y);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    cplx<T> acc = mode == 0 ? Y[i] : cplx<T>{T(0), T(0)};
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      cplx<T> ck = {(T)cf.c[2 * k], (T)cf.c[2 * k + 1]};
+      cplx<T> x = reinterpret_cast<const cplx<T>*>(vs.p[k])[i];
+      if (mode == 0) acc -= ck * x; else acc += ck * x;
+    }
+    Y[i] = acc;
+  }
+}
+
+inline unsigned ew_grid(size_t n) {
+  size_t b = (n + 255) / 256;
+  return (unsigned)(b < 152 * 16 ? b : 152 * 16);
+}
+
+}  // namespace
+
+template <typename T>
+int blas_dot(dw_ctx* c, const T* a, const T* b, size_t n, double* out3, cudaStream_t s) {
+  // out3 (device): re, im of (a, b) and |a|^2
+  dot_kernel<T><<<RGRID, RB, 0, s>>>(a, b, n, c->d_red, c->d_count, out3);
+  return DW_OK;
+}
+
+template <typename T, int K>
+static void launch_md(dw_ctx* c, const Ptrs<T, MAXK>& p, const T* b, size_t n, double* out, cudaStream_t s) {
+  multi_dot_kernel<T, K><<<RGRID, RB, 0, s>>>(p, b, n, c->d_red, c->d_count, out);
+}
+
+template <typename T>
+int blas_multi_dot(dw_ctx* c, const T* const* vs, int k, const T* b, size_t n, double* out2, cudaStream_t s) {
+  for (int j0 = 0; j0 < k; j0 += MAXK) {
+    int kk = k - j0 < MAXK ? k - j0 : MAXK;
+    Ptrs<T, MAXK> p{};
+    for (int j = 0; j < kk; ++j) p.p[j] = vs[j0 + j];
+    double* o = out2 + 2 * j0;
+    switch (kk) {
+#define MD(K) case K: launch_md<T, K>(c, p, b, n, o, s); break;
+      MD(1) MD(2) MD(3) MD(4) MD(5) MD(6) MD(7) MD(8) MD(9) MD(10) MD(11) MD(12) MD(13) MD(14) MD(15) MD(16)
+#undef MD
+    }
+  }
+  return DW_OK;
+}
+
+template <typename T>
+void blas_axpy(const T* x, T* y, double ar, double ai, size_t n, cudaStream_t s) {
+  axpy_kernel<T><<<ew_grid(n), 256, 0, s>>>(x, y, (T)ar, (T)ai, n);
+}
+template <typename T>
+void blas_xpby(const T* x, T* y, double br, double bi, size_t n, cudaStream_t s) {
+  xpby_kernel<T><<<ew_grid(n), 256, 0, s>>>(x, y, (T)br, (T)bi, n);
+}
+template <typename T>
+void blas_scale(T* x, double ar, double ai, size_t n, cudaStream_t s) {
+  scale_kernel<T><<<ew_grid(n), 256, 0, s>>>(x, (T)ar, (T)ai, n);
+}
+template <typename Tin, typename Tout>
+void blas_convert(const Tin* x, Tout* y, double scale, size_t n, cudaStream_t s) {
+  convert_kernel<Tin, Tout><<<ew_grid(2 * n), 256, 0, s>>>(x, y, scale, 2 * n);
+}
+
+template <typename T, int K>
+static void launch_ma(const Ptrs<T, MAXK>& p, const Coefs<T>& cf, T* y, size_t n, int mode, cudaStream_t s) {
+  multi_axpy_kernel<T, K><<<ew_grid(n), 256, 0, s>>>(p, cf, y, n, mode);
+}
+template <typename T>
+static void multi_axpy_impl(const T* const* vs, int k, const double* coef, T* y, size_t n, int mode,
+                            cudaStream_t s) {
+  for (int j0 = 0; j0 < k; j0 += MAXK) {
+    int kk = k - j0 < MAXK ? k - j0 : MAXK;
+    Ptrs<T, MAXK> p{};
+    Coefs<T> cf{};
+    for (int j = 0; j < kk; ++j) {
+      p.p[j] = vs[j0 + j];
+      cf.c[2 * j] = coef[2 * (j0 + j)];
+      cf.c[2 * j + 1] = coef[2 * (j0 + j) + 1];
+    }
+    int m = (j0 == 0) ? mode : 0;
+    if (m == 1) {
+      // first chunk of a linear combination: y = sum; later chunks: y += sum (negated coefs, mode 0)
+    } else if (j0 > 0 && mode == 1) {
+      for (int j = 0; j < 2 * kk; ++j) cf.c[j] = -cf.c[j];
+    }
+    switch (kk) {
+#define MA(K) case K: launch_ma<T, K>(p, cf, y, n, m, s); break;
+      MA(1) MA(2) MA(3) MA(4) MA(5) MA(6) MA(7) MA(8) MA(9) MA(10) MA(11) MA(12) MA(13) MA(14) MA(15) MA(16)
+#undef MA
+    }
+  }
+}
+template <typename T>
+void blas_multi_axpy(const T* const* vs, int k, const double* coef, T* y, size_t n, cudaStream_t s) {
+  multi_axpy_impl(vs, k, coef, y, n, 0, s);
+}
+template <typename T>
+void blas_lincomb(const T* const* vs, int k, const double* coef, T* out, size_t n, cudaStream_t s) {
+  multi_axpy_impl(vs, k, coef, out, n, 1, s);
+}
+
+#define INST(T)                                                                                      \
+  template int blas_dot<T>(dw_ctx*, const T*, const T*, size_t, double*, cudaStream_t);              \
+  template int blas_multi_dot<T>(dw_ctx*, const T* const*, int, const T*, size_t, double*, cudaStream_t); \
+  template void blas_axpy<T>(const T*, T*, double, double, size_t, cudaStream_t);                    \
+  template void blas_xpby<T>(const T*, T*, double, double, size_t, cudaStream_t);                    \
+  template void blas_scale<T>(T*, double, double, size_t, cudaStream_t);                             \
+  template void blas_multi_axpy<T>(const T* const*, int, const double*, T*, size_t, cudaStream_t);   \
+  template void blas_lincomb<T>(const T* const*, int, const double*, T*, size_t, cudaStream_t);
+INST(float)
+INST(double)
+template void blas_convert<double, float>(const double*, float*, double, size_t, cudaStream_t);
+template void blas_convert<float, double>(const float*, double*, double, size_t, cudaStream_t);
+template void blas_convert<double, double>(const double*, double*, double, size_t, cudaStream_t);
+template void blas_convert<float, float>(const float*, float*, double, size_t, cudaStream_t);

@@ -1,0 +1,339 @@
+// Internal definitions shared by the CUDA translation units of libdwsolve.
+//
+// Packed device layout ("block-major SoA")
+// ----------------------------------------
+// Sites are ordered by Schwarz block: internal index
+//     i = b * svol + p * shv + h
+// with b the SAP block (lexicographic block coordinates, x0 slowest), p the
+// site parity, h the position of the site among the block's sites of that
+// parity in local lexicographic order (h = local_lex / 2; the last block
+// extent is even so every pair of consecutive local sites holds one site
+// of each parity).  Block origins have even coordinates, so local parity
+// equals global parity.  Every Schwarz block is one contiguous index range,
+// which is what the on-chip block solver stages.
+//
+// Per-site data are stored as structure of arrays in 16-byte units:
+//   quark field : 12 complex  (k = 3*spin + colour)  -> 12*8/16 units (FP32: 6 float4, FP64: 12 double2)
+//   link        : rows 0 and 1 of U_mu(x) (6 complex), row 2 rebuilt as conj(row0 x row1)
+//   clover      : per chiral 6x6 Hermitian block 18 complex slots
+//                 (slots 0..2 = real diagonal pairs, 3..17 = upper triangle row-major)
+// Unit u of site i lives at plane u: base[u * V + i], so a warp touching 32
+// consecutive sites reads 512 contiguous bytes per unit.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/dwsolve.h"
+
+#define DW_HD __host__ __device__ __forceinline__
+#define DW_D __device__ __forceinline__
+
+// ---------------------------------------------------------------- complex
+template <typename T>
+struct cplx {
+  T re, im;
+};
+template <typename T> DW_HD cplx<T> mk(T r, T i) { return cplx<T>{r, i}; }
+template <typename T> DW_HD cplx<T> operator+(cplx<T> a, cplx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T> DW_HD cplx<T> operator-(cplx<T> a, cplx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename T> DW_HD cplx<T> operator-(cplx<T> a) { return {-a.re, -a.im}; }
+template <typename T> DW_HD cplx<T> operator*(cplx<T> a, cplx<T> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename T> DW_HD cplx<T> operator*(T s, cplx<T> a) { return {s * a.re, s * a.im}; }
+template <typename T> DW_HD cplx<T>& operator+=(cplx<T>& a, cplx<T> b) { a.re += b.re; a.im += b.im; return a; }
+template <typename T> DW_HD cplx<T>& operator-=(cplx<T>& a, cplx<T> b) { a.re -= b.re; a.im -= b.im; return a; }
+template <typename T> DW_HD cplx<T> conjg(cplx<T> a) { return {a.re, -a.im}; }
+// conj(a) * b
+template <typename T> DW_HD cplx<T> cmulc(cplx<T> a, cplx<T> b) {
+  return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+// i * a
+template <typename T> DW_HD cplx<T> ti(cplx<T> a) { return {-a.im, a.re}; }
+template <typename T> DW_HD T norm2(cplx<T> a) { return a.re * a.re + a.im * a.im; }
+
+// ---------------------------------------------------------------- 16-byte units
+template <typename T> struct Unit;
+template <> struct Unit<float> { using t = float4; static constexpr int C = 2; };
+template <> struct Unit<double> { using t = double2; static constexpr int C = 1; };
+
+DW_D void unpack_unit(const float4& v, cplx<float>* c) { c[0] = {v.x, v.y}; c[1] = {v.z, v.w}; }
+DW_D void unpack_unit(const double2& v, cplx<double>* c) { c[0] = {v.x, v.y}; }
+DW_D float4 pack_unit(const cplx<float>* c) { return make_float4(c[0].re, c[0].im, c[1].re, c[1].im); }
+DW_D double2 pack_unit(const cplx<double>* c) { return make_double2(c[0].re, c[0].im); }
+
+// load NC complex numbers of site i from unit planes (read-only path)
+template <typename T, int NC>
+DW_D void load_site(const T* __restrict__ base, size_t V, size_t i, cplx<T>* out) {
+  using U = typename Unit<T>::t;
+  constexpr int CU = Unit<T>::C;
+  const U* p = reinterpret_cast<const U*>(base);
+#pragma unroll
+  for (int u = 0; u < NC / CU; ++u) unpack_unit(__ldg(p + (size_t)u * V + i), out + u * CU);
+}
+// plain (coherent) load, for buffers written earlier in the same kernel
+template <typename T, int NC>
+DW_D void load_site_rw(const T* base, size_t V, size_t i, cplx<T>* out) {
+  using U = typename Unit<T>::t;
+  constexpr int CU = Unit<T>::C;
+  const U* p = reinterpret_cast<const U*>(base);
+#pragma unroll
+  for (int u = 0; u < NC / CU; ++u) unpack_unit(p[(size_t)u * V + i], out + u * CU);
+}
+template <typename T, int NC>
+DW_D void store_site(T* __restrict__ base, size_t V, size_t i, const cplx<T>* in) {
+  using U = typename Unit<T>::t;
+  constexpr int CU = Unit<T>::C;
+  U* p = reinterpret_cast<U*>(base);
+#pragma unroll
+  for (int u = 0; u < NC / CU; ++u) p[(size_t)u * V + i] = pack_unit(in + u * CU);
+}
+
+// ---------------------------------------------------------------- geometry
+// Neighbour table entry for (parity p, half index h, direction d = 2*mu + (0 forward, 1 backward)):
+// bits 0..14 = half index of the neighbour inside its block, bit 15 = neighbour in another block.
+struct Geom {
+  int L[4];
+  long long V;
+  int sb[4];
+  int svol, shv, lsvol, lshv;    // block volume, half volume and their log2
+  int nsap;                      // number of Schwarz blocks
+  int antiperiodic;
+  const uint16_t* nbtab;         // [2][shv][8]
+  const int* blk_nb;             // [nsap][8]  neighbouring block in direction d
+  const int* blk_x0;             // [nsap]     time coordinate of the block origin
+  const uchar4* loc;             // [2][shv]   local coordinates (l0, l1, l2, l3)
+};
+
+struct SiteRef {
+  int b, p, h;
+};
+DW_D SiteRef decode(const Geom& g, long long i) {
+  SiteRef s;
+  s.b = (int)(i >> g.lsvol);
+  int w = (int)(i & (g.svol - 1));
+  s.p = w >> g.lshv;
+  s.h = w & (g.shv - 1);
+  return s;
+}
+DW_D long long site_index(const Geom& g, int b, int p, int h) {
+  return ((long long)b << g.lsvol) + (p << g.lshv) + h;
+}
+// neighbour of site (b, p, h) in direction d; sets *cross if the hop leaves the block
+DW_D long long neighbour(const Geom& g, const SiteRef& s, int d, bool* cross) {
+  uint16_t e = __ldg(g.nbtab + ((s.p * g.shv + s.h) << 3) + d);
+  bool c = (e >> 15) != 0;
+  *cross = c;
+  int nb = c ? __ldg(g.blk_nb + s.b * 8 + d) : s.b;
+  return site_index(g, nb, 1 - s.p, e & 0x7fff);
+}
+DW_D long long neighbour_of(const Geom& g, long long i, int d) {
+  bool c;
+  return neighbour(g, decode(g, i), d, &c);
+}
+// antiperiodic sign of a time hop: forward from x0 = L0-1, backward from x0 = 0
+DW_D bool time_wrap(const Geom& g, const SiteRef& s, int d) {
+  if (!g.antiperiodic || d > 1) return false;
+  uchar4 l = __ldg(g.loc + s.p * g.shv + s.h);
+  int x0 = __ldg(g.blk_x0 + s.b) + l.x;
+  return d == 0 ? (x0 == g.L[0] - 1) : (x0 == 0);
+}
+
+// ---------------------------------------------------------------- SU(3)
+template <typename T>
+struct SU3 {
+  cplx<T> m[3][3];
+};
+template <typename T>
+DW_D void load_link(const T* __restrict__ links, size_t V, int mu, size_t i, SU3<T>& U) {
+  cplx<T> r[6];
+  load_site<T, 6>(links + (size_t)mu * 12 * V, V, i, r);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    U.m[0][j] = r[j];
+    U.m[1][j] = r[3 + j];
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+    U.m[2][j] = conjg(U.m[0][j1] * U.m[1][j2] - U.m[0][j2] * U.m[1][j1]);
+  }
+}
+template <typename T>
+DW_D void su3_mul(const SU3<T>& U, const cplx<T>* h, cplx<T>* o) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) o[a] = U.m[a][0] * h[0] + U.m[a][1] * h[1] + U.m[a][2] * h[2];
+}
+template <typename T>
+DW_D void su3_dag_mul(const SU3<T>& U, const cplx<T>* h, cplx<T>* o) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) o[a] = cmulc(U.m[0][a], h[0]) + cmulc(U.m[1][a], h[1]) + cmulc(U.m[2][a], h[2]);
+}
+
+// ---------------------------------------------------------------- spin structure
+// gamma_mu = [[0, e_mu], [e_mu^+, 0]] with e_0 = -1, e_k = -i sigma_k.
+// (1 + S gamma_mu) psi = [h ; S e_mu^+ h],  h = psi_up + S e_mu psi_lo  (S = +-1).
+template <int MU, typename T>
+DW_D void e_mul(const cplx<T>& l2, const cplx<T>& l3, cplx<T>& v0, cplx<T>& v1) {
+  if (MU == 0) { v0 = -l2; v1 = -l3; }
+  if (MU == 1) { v0 = -ti(l3); v1 = -ti(l2); }
+  if (MU == 2) { v0 = -l3; v1 = l2; }
+  if (MU == 3) { v0 = -ti(l2); v1 = ti(l3); }
+}
+template <int MU, typename T>
+DW_D void edag_mul(const cplx<T>& h0, const cplx<T>& h1, cplx<T>& w0, cplx<T>& w1) {
+  if (MU == 0) { w0 = -h0; w1 = -h1; }
+  if (MU == 1) { w0 = ti(h1); w1 = ti(h0); }
+  if (MU == 2) { w0 = h1; w1 = -h0; }
+  if (MU == 3) { w0 = ti(h0); w1 = -ti(h1); }
+}
+
+// acc += sign * (1 + S gamma_mu) W psi, W = U (DAG=false) or U^+ (DAG=true)
+template <int MU, int S, bool DAG, typename T>
+DW_D void hop_acc(cplx<T>* acc, const cplx<T>* psi, const SU3<T>& U, T sign) {
+  cplx<T> h[2][3], w[2][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    cplx<T> v0, v1;
+    e_mul<MU>(psi[6 + c], psi[9 + c], v0, v1);
+    if (S > 0) { h[0][c] = psi[c] + v0; h[1][c] = psi[3 + c] + v1; }
+    else       { h[0][c] = psi[c] - v0; h[1][c] = psi[3 + c] - v1; }
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    if (DAG) su3_dag_mul(U, h[a], w[a]); else su3_mul(U, h[a], w[a]);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    cplx<T> l0, l1;
+    edag_mul<MU>(w[0][c], w[1][c], l0, l1);
+    acc[c] += sign * w[0][c];
+    acc[3 + c] += sign * w[1][c];
+    if (S > 0) { acc[6 + c] += sign * l0; acc[9 + c] += sign * l1; }
+    else       { acc[6 + c] -= sign * l0; acc[9 + c] -= sign * l1; }
+  }
+}
+
+// ---------------------------------------------------------------- clover
+// y = A x for one chiral block stored in 18 slots (see layout above)
+template <typename T>
+DW_D void herm6_mul(const cplx<T>* s, const cplx<T>* x, cplx<T>* y) {
+  const T d[6] = {s[0].re, s[0].im, s[1].re, s[1].im, s[2].re, s[2].im};
+#pragma unroll
+  for (int i = 0; i < 6; ++i) y[i] = d[i] * x[i];
+  int k = 3;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+#pragma unroll
+    for (int j = i + 1; j < 6; ++j) {
+      y[i] += s[k] * x[j];
+      y[j] += cmulc(s[k], x[i]);
+      ++k;
+    }
+  }
+}
+template <typename T>
+DW_D void clover_apply(const T* __restrict__ clov, size_t V, size_t i, const cplx<T>* x, cplx<T>* y) {
+  cplx<T> s[18];
+  load_site<T, 18>(clov, V, i, s);
+  herm6_mul(s, x, y);
+  load_site<T, 18>(clov + 36 * V, V, i, s);
+  herm6_mul(s, x + 6, y + 6);
+}
+
+// ---------------------------------------------------------------- contexts
+struct HostTimer;
+
+struct dw_ctx {
+  dw_params p;
+  Geom g;                      // device pointers filled in
+  long long V;
+  int nsb[4];
+  std::vector<int> canon_of;   // internal index -> canonical site (host copy)
+  std::vector<int> blk_colour; // per Schwarz block
+  int* d_canon_of = nullptr;
+  uint16_t* d_nbtab = nullptr;
+  int* d_blk_nb = nullptr;
+  int* d_blk_x0 = nullptr;
+  uchar4* d_loc = nullptr;
+  int* d_colour_list = nullptr;  // blocks of colour 0 then colour 1
+  int ncolour[2] = {0, 0};
+  void* links[2] = {nullptr, nullptr};    // [DW_F64], [DW_F32]
+  void* clov[2] = {nullptr, nullptr};
+  void* clovinv[2] = {nullptr, nullptr};
+  void* sap_r[2] = {nullptr, nullptr};    // SAP residual workspace
+  void* sap_d[2] = {nullptr, nullptr};    // SAP last-correction workspace
+  double* d_red = nullptr;                // reduction scratch
+  unsigned* d_count = nullptr;
+  double* h_red = nullptr;                // pinned host mirror
+};
+
+// error handling ------------------------------------------------------------
+void dw_set_error(const std::string& msg);
+int dw_cuda_fail(cudaError_t e, const char* what);
+#define DW_CUDA(call)                                      \
+  do {                                                     \
+    cudaError_t _e = (call);                               \
+    if (_e != cudaSuccess) return dw_cuda_fail(_e, #call); \
+  } while (0)
+
+template <typename T> constexpr int prec_of() { return sizeof(T) == 8 ? DW_F64 : DW_F32; }
+inline size_t real_size(int prec) { return prec == DW_F64 ? 8 : 4; }
+
+// launch helpers implemented in dw_blas.cu -------------------------------------
+// All reductions accumulate in FP64 and are deterministic (fixed order).
+template <typename T> int blas_dot(dw_ctx* c, const T* a, const T* b, size_t n_cplx, double* out2, cudaStream_t s);
+template <typename T> int blas_multi_dot(dw_ctx* c, const T* const* vs, int k, const T* b, size_t n_cplx,
+                                         double* out2, cudaStream_t s);
+// y = a*x + y  (complex a)
+template <typename T> void blas_axpy(const T* x, T* y, double ar, double ai, size_t n_cplx, cudaStream_t s);
+// y = x + b*y  (complex b)
+template <typename T> void blas_xpby(const T* x, T* y, double br, double bi, size_t n_cplx, cudaStream_t s);
+template <typename T> void blas_scale(T* x, double ar, double ai, size_t n_cplx, cudaStream_t s);
+template <typename Tin, typename Tout> void blas_convert(const Tin* x, Tout* y, double scale, size_t n_cplx,
+                                                        cudaStream_t s);
+// y -= sum_j coef[j] * vs[j]  (coef: host array of k complex)
+template <typename T> void blas_multi_axpy(const T* const* vs, int k, const double* coef, T* y, size_t n_cplx,
+                                           cudaStream_t s);
+// out = sum_j coef[j] * vs[j]
+template <typename T> void blas_lincomb(const T* const* vs, int k, const double* coef, T* out, size_t n_cplx,
+                                        cudaStream_t s);
+
+// dirac / sap entry points used by the solver ---------------------------------------
+template <typename T> void dirac_full(dw_ctx* c, const T* in, T* out, cudaStream_t s);
+template <typename T> int sap_apply(dw_ctx* c, int ncy, int nmr, const T* rho, T* xi, cudaStream_t s);
+
+// ---------------------------------------------------------------- hopping term
+// acc += sign * (1 - gamma_mu) U_mu(x) psi(x+mu) + sign * (1 + gamma_mu) U_mu(x-mu)^+ psi(x-mu)
+// for one direction mu (sign = -1 across the antiperiodic time boundary).
+// The caller multiplies the sum by -1/2.
+template <int MU, typename T>
+DW_D void hop_dir(const Geom& g, const SiteRef& s, long long i, const T* __restrict__ links,
+                  const T* __restrict__ in, cplx<T>* acc) {
+  const size_t V = g.V;
+  bool cr;
+  SU3<T> U;
+  cplx<T> p[12];
+  long long j = neighbour(g, s, 2 * MU, &cr);
+  T sg = time_wrap(g, s, 2 * MU) ? T(-1) : T(1);
+  load_link(links, V, MU, i, U);
+  load_site<T, 12>(in, V, j, p);
+  hop_acc<MU, -1, false>(acc, p, U, sg);
+  j = neighbour(g, s, 2 * MU + 1, &cr);
+  sg = time_wrap(g, s, 2 * MU + 1) ? T(-1) : T(1);
+  load_link(links, V, MU, j, U);
+  load_site<T, 12>(in, V, j, p);
+  hop_acc<MU, +1, true>(acc, p, U, sg);
+}
+template <typename T>
+DW_D void hop_all(const Geom& g, const SiteRef& s, long long i, const T* __restrict__ links,
+                  const T* __restrict__ in, cplx<T>* acc) {
+  hop_dir<0>(g, s, i, links, in, acc);
+  hop_dir<1>(g, s, i, links, in, acc);
+  hop_dir<2>(g, s, i, links, in, acc);
+  hop_dir<3>(g, s, i, links, in, acc);
+}

@@ -1,0 +1,1122 @@
+// Deflation subspace and little Dirac operator.
+//
+//   Section 4.1  block projection  P psi = sum_L sum_l phi^L_l (phi^L_l, psi)
+//   Section 4.2  phi^L_l = Gram-Schmidt of psi_l restricted to block L
+//   Section 5.3  inverse iteration psi_l <- "D^{-1}" psi_l with M_sap  (5.1)
+//   (3.2), A.1   B_{LL'} = (phi^L_k, D phi^{L'}_l)  (L' = L or one of 8 neighbours)
+//   A.2          even-odd little operator  B^ = 1 - B_ee^{-1} B_eo B_oo^{-1} B_oe
+//   A.3          global-mode deflation of the little system
+//   A.4          GCR on the deflated even-odd little system
+//
+// Basis storage: Ns global fields (field l = sum_L phi^L_l) in the packed
+// layout; FP64 for the plain path, BF16 (3 x 16-byte units of 4 complex per
+// site) for the mixed path.  The FP64 copy always holds the values the
+// little operator is built from (dequantised when BF16 is stored).
+// Little vectors: complex[Nb][Ns], block = lexicographic deflation-block index.
+#include <chrono>
+#include <cmath>
+#include <complex>
+
+#include "dw_common.cuh"
+
+using cd = std::complex<double>;
+
+struct dfl_ctx {
+  dw_ctx* c = nullptr;
+  dfl_params p{};
+  int bs[4], nb[4];
+  int Nb = 0, Ns = 0, N = 0, nsub = 0;
+  int* d_sub = nullptr;        // [Nb][nsub] Schwarz blocks of each deflation block
+  int* d_sap2dfl = nullptr;    // [nsap]
+  int* d_bnb = nullptr;        // [Nb][8] neighbouring deflation block
+  // parity lists
+  int Ne = 0, No = 0;
+  int* d_list[2] = {nullptr, nullptr};   // block ids of parity 0 / 1
+  int* d_lnb[2] = {nullptr, nullptr};    // [n_par][8] position of the neighbour in the other list
+  // basis
+  double* basis64 = nullptr;
+  uint4* basis16 = nullptr;
+  // little operator
+  double* B64 = nullptr;                 // [Nb][9][Ns][Ns] column-major complex
+  double* Binv64 = nullptr; float* Binv32 = nullptr;   // [Nb][Ns][Ns]
+  double* M64 = nullptr; float* M32 = nullptr;         // [Nb][8][Ns][Ns]  B_LL^{-1} B_{L,nb(L,d)}
+  bool illcond = false;
+  double max_cond = 0;
+  // global-mode deflation (A.3)
+  bool a3 = false;
+  double* g64 = nullptr; float* g32 = nullptr;         // [Ns][Ne*Ns]
+  double* Bg64 = nullptr; float* Bg32 = nullptr;       // B^ g
+  std::vector<cd> Atil_inv;                            // Ns x Ns row-major
+  // work vectors (little GCR)
+  void* lw[2] = {nullptr, nullptr};                    // per precision
+  size_t lw_count = 0;
+};
+
+namespace {
+
+constexpr int NSMAX = 32;
+
+// ------------------------------------------------------------------ BF16 basis units
+DW_D void bf16_unpack4(const uint4& u, cplx<float>* c) {
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float2 f = __bfloat1622float2(h[j]);
+    c[j] = {f.x, f.y};
+  }
+}
+template <typename T>
+DW_D void load_basis(const double* b64, const uint4* b16, size_t V, int l, size_t i, cplx<T>* out) {
+  if (b16) {
+    const uint4* p = b16 + (size_t)l * 3 * V;
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      cplx<float> c[4];
+      bf16_unpack4(__ldg(p + (size_t)u * V + i), c);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) out[4 * u + j] = {(T)c[j].re, (T)c[j].im};
+    }
+  } else {
+    cplx<double> c[12];
+    load_site<double, 12>(b64 + (size_t)l * 24 * V, V, i, c);
+#pragma unroll
+    for (int j = 0; j < 12; ++j) out[j] = {(T)c[j].re, (T)c[j].im};
+  }
+}
+
+template <typename T>
+DW_D T block_sum(T v, T* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  T s = 0;
+  for (int j = 0; j < (int)(blockDim.x >> 5); ++j) s += sh[j];
+  return s;
+}
+
+// iterate over the sites of deflation block L: site index of the t-th site
+DW_D long long dfl_site(const Geom& g, const int* sub, int nsub, int L, int t) {
+  int sb = sub[L * nsub + (t >> g.lsvol)];
+  return ((long long)sb << g.lsvol) + (t & (g.svol - 1));
+}
+
+// ------------------------------------------------------------------ Gram-Schmidt (FP64)
+__global__ void __launch_bounds__(256) block_gs_kernel(Geom g, const int* __restrict__ sub, int nsub, int Ns,
+                                                       double* basis, int* rank_loss) {
+  __shared__ double sh[8];
+  const int L = blockIdx.x;
+  const size_t V = g.V;
+  const int nsite = nsub * g.svol;
+  for (int l = 0; l < Ns; ++l) {
+    double* vl = basis + (size_t)l * 24 * V;
+    double n0 = 0;
+    for (int t = threadIdx.x; t < nsite; t += blockDim.x) {
+      cplx<double> a[12];
+      load_site_rw<double, 12>(vl, V, dfl_site(g, sub, nsub, L, t), a);
+      for (int k = 0; k < 12; ++k) n0 += norm2(a[k]);
+    }
+    n0 = sqrt(block_sum(n0, sh));
+    for (int pass = 0; pass < 2; ++pass)
+      for (int j = 0; j < l; ++j) {
+        const double* vj = basis + (size_t)j * 24 * V;
+        double cr = 0, ci = 0;
+        for (int t = threadIdx.x; t < nsite; t += blockDim.x) {
+          long long i = dfl_site(g, sub, nsub, L, t);
+          cplx<double> a[12], b[12];
+          load_site_rw<double, 12>(vj, V, i, a);
+          load_site_rw<double, 12>(vl, V, i, b);
+          for (int k = 0; k < 12; ++k) {
+            cplx<double> z = cmulc(a[k], b[k]);
+            cr += z.re; ci += z.im;
+          }
+        }
+        cr = block_sum(cr, sh);
+        ci = block_sum(ci, sh);
+        cplx<double> cc = {cr, ci};
+        for (int t = threadIdx.x; t < nsite; t += blockDim.x) {
+          long long i = dfl_site(g, sub, nsub, L, t);
+          cplx<double> a[12], b[12];
+          load_site_rw<double, 12>(vj, V, i, a);
+          load_site_rw<double, 12>(vl, V, i, b);
+          for (int k = 0; k < 12; ++k) b[k] -= cc * a[k];
+          store_site<double, 12>(vl, V, i, b);
+        }
+        __syncthreads();
+      }
+    double n1 = 0;
+    for (int t = threadIdx.x; t < nsite; t += blockDim.x) {
+      cplx<double> a[12];
+      load_site_rw<double, 12>(vl, V, dfl_site(g, sub, nsub, L, t), a);
+      for (int k = 0; k < 12; ++k) n1 += norm2(a[k]);
+    }
+    n1 = sqrt(block_sum(n1, sh));
+    if (!(n1 > 1e-12 * n0)) {
+      if (threadIdx.x == 0) atomicExch(rank_loss, 1);
+      n1 = 1.0;
+    }
+    double s = 1.0 / n1;
+    for (int t = threadIdx.x; t < nsite; t += blockDim.x) {
+      long long i = dfl_site(g, sub, nsub, L, t);
+      cplx<double> a[12];
+      load_site_rw<double, 12>(vl, V, i, a);
+      for (int k = 0; k < 12; ++k) a[k] = s * a[k];
+      store_site<double, 12>(vl, V, i, a);
+    }
+    __syncthreads();
+  }
+}
+
+// FP64 -> (FP32 ->) BF16, round to nearest even; the FP64 copy takes the rounded values
+__global__ void quantize_kernel(size_t V, int Ns, double* b64, uint4* b16) {
+  size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= V * Ns) return;
+  int l = (int)(t / V);
+  size_t i = t % V;
+  cplx<double> a[12];
+  load_site_rw<double, 12>(b64 + (size_t)l * 24 * V, V, i, a);
+  for (int u = 0; u < 3; ++u) {
+    uint4 q;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&q);
+    for (int j = 0; j < 4; ++j) {
+      cplx<double>& z = a[4 * u + j];
+      h[j] = __floats2bfloat162_rn((float)z.re, (float)z.im);
+      float2 f = __bfloat1622float2(h[j]);
+      z = {(double)f.x, (double)f.y};
+    }
+    b16[((size_t)l * 3 + u) * V + i] = q;
+  }
+  store_site<double, 12>(b64 + (size_t)l * 24 * V, V, i, a);
+}
+
+// ------------------------------------------------------------------ restrict / prolong
+// c[L][k] = (phi^L_k, psi)
+template <typename T>
+__global__ void __launch_bounds__(128) restrict_kernel(Geom g, const int* __restrict__ sub, int nsub, int Ns,
+                                                       const double* b64, const uint4* b16,
+                                                       const T* __restrict__ psi, T* __restrict__ c) {
+  __shared__ double sh[2][NSMAX][4];
+  const int L = blockIdx.x;
+  const size_t V = g.V;
+  const int nsite = nsub * g.svol;
+  cplx<T> acc[NSMAX];
+#pragma unroll
+  for (int k = 0; k < NSMAX; ++k) acc[k] = {T(0), T(0)};
+  for (int t = threadIdx.x; t < nsite; t += blockDim.x) {
+    long long i = dfl_site(g, sub, nsub, L, t);
+    cplx<T> p[12], f[12];
+    load_site<T, 12>(psi, V, i, p);
+#pragma unroll
+    for (int k = 0; k < NSMAX; ++k) {
+      if (k < Ns) {
+        load_basis<T>(b64, b16, V, k, i, f);
+#pragma unroll
+        for (int j = 0; j < 12; ++j) acc[k] += cmulc(f[j], p[j]);
+      }
+    }
+  }
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NSMAX; ++k) {
+    if (k < Ns) {
+      double re = acc[k].re, im = acc[k].im;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+      }
+      if (lane == 0) { sh[0][k][w] = re; sh[1][k][w] = im; }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < Ns) {
+    int k = threadIdx.x;
+    double re = 0, im = 0;
+    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) { re += sh[0][k][j]; im += sh[1][k][j]; }
+    c[2 * ((size_t)L * Ns + k)] = (T)re;
+    c[2 * ((size_t)L * Ns + k) + 1] = (T)im;
+  }
+}
+
+// psi = mode 0: Phi c ; 1: psi + Phi c ; 2: psi - Phi c
+template <typename T>
+__global__ void __launch_bounds__(128) prolong_kernel(Geom g, const int* __restrict__ sap2dfl, int Ns,
+                                                      const double* b64, const uint4* b16,
+                                                      const T* __restrict__ c, T* psi, int mode) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= g.V) return;
+  const size_t V = g.V;
+  const int L = __ldg(sap2dfl + (int)(i >> g.lsvol));
+  cplx<T> out[12], f[12];
+  if (mode == 0) {
+#pragma unroll
+    for (int j = 0; j < 12; ++j) out[j] = {T(0), T(0)};
+  } else {
+    load_site_rw<T, 12>(psi, V, i, out);
+  }
+  const cplx<T>* cc = reinterpret_cast<const cplx<T>*>(c) + (size_t)L * Ns;
+  for (int k = 0; k < Ns; ++k) {
+    cplx<T> ck = cc[k];
+    if (mode == 2) ck = -ck;
+    load_basis<T>(b64, b16, V, k, i, f);
+#pragma unroll
+    for (int j = 0; j < 12; ++j) out[j] += ck * f[j];
+  }
+  store_site<T, 12>(psi, V, i, out);
+}
+
+// ------------------------------------------------------------------ little operator assembly (A.1), FP64
+// CTA (L, l, part): part 0: (phi^L_k, D_L phi^L_l) with D_L the deflation-block (Dirichlet) operator;
+// part 1+d: (phi^L_k, hop_d phi^{nb(L,d)}_l) over the face of L in direction d.
+template <int MU>
+DW_D void part_dir(const Geom& g, const SiteRef& s, long long i, const double* __restrict__ links,
+                   const double* __restrict__ f, const int* __restrict__ sap2dfl, int myL, int sel,
+                   cplx<double>* acc) {
+  // sel: -1 -> all hops staying inside the deflation block; d -> only direction d if it leaves the block
+  for (int dir = 0; dir < 2; ++dir) {
+    int d = 2 * MU + dir;
+    if (sel >= 0 && sel != d) continue;
+    bool cr;
+    long long j = neighbour(g, s, d, &cr);
+    int nL = cr ? __ldg(sap2dfl + (int)(j >> g.lsvol)) : myL;
+    bool inside = nL == myL;
+    if ((sel < 0) != inside) continue;
+    double sg = time_wrap(g, s, d) ? -1.0 : 1.0;
+    SU3<double> U;
+    cplx<double> p[12];
+    load_link(links, g.V, MU, dir == 0 ? i : j, U);
+    load_site<double, 12>(f, g.V, j, p);
+    if (dir == 0) hop_acc<MU, -1, false>(acc, p, U, sg);
+    else hop_acc<MU, +1, true>(acc, p, U, sg);
+  }
+}
+
+__global__ void __launch_bounds__(128) assemble_kernel(Geom g, const int* __restrict__ sub, int nsub,
+                                                       const int* __restrict__ sap2dfl, int Ns,
+                                                       const double* __restrict__ links,
+                                                       const double* __restrict__ clov,
+                                                       const double* __restrict__ basis, double* B) {
+  __shared__ double sh[2][NSMAX][4];
+  const int l = blockIdx.x % Ns;
+  const int part = (blockIdx.x / Ns) % 9;
+  const int L = blockIdx.x / (9 * Ns);
+  const size_t V = g.V;
+  const int nsite = nsub * g.svol;
+  const double* fl = basis + (size_t)l * 24 * V;
+  cplx<double> acc[NSMAX];
+  for (int k = 0; k < NSMAX; ++k) acc[k] = {0.0, 0.0};
+  for (int t = threadIdx.x; t < nsite; t += blockDim.x) {
+    long long i = dfl_site(g, sub, nsub, L, t);
+    SiteRef s = decode(g, i);
+    cplx<double> w[12], h[12];
+    for (int j = 0; j < 12; ++j) h[j] = {0.0, 0.0};
+    int sel = part - 1;
+    part_dir<0>(g, s, i, links, fl, sap2dfl, L, sel, h);
+    part_dir<1>(g, s, i, links, fl, sap2dfl, L, sel, h);
+    part_dir<2>(g, s, i, links, fl, sap2dfl, L, sel, h);
+    part_dir<3>(g, s, i, links, fl, sap2dfl, L, sel, h);
+    bool any = false;
+    for (int j = 0; j < 12; ++j) {
+      w[j] = -0.5 * h[j];
+      any |= (h[j].re != 0.0 || h[j].im != 0.0);
+    }
+    if (part == 0) {
+      cplx<double> p[12], y[12];
+      load_site<double, 12>(fl, V, i, p);
+      clover_apply(clov, V, i, p, y);
+      for (int j = 0; j < 12; ++j) w[j] += y[j];
+      any = true;
+    }
+    if (!any) continue;
+    for (int k = 0; k < Ns; ++k) {
+      cplx<double> f[12];
+      load_site<double, 12>(basis + (size_t)k * 24 * V, V, i, f);
+      for (int j = 0; j < 12; ++j) acc[k] += cmulc(f[j], w[j]);
+    }
+  }
+  int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  for (int k = 0; k < Ns; ++k) {
+    double re = acc[k].re, im = acc[k].im;
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) { sh[0][k][wp] = re; sh[1][k][wp] = im; }
+  }
+  __syncthreads();
+  if (threadIdx.x < Ns) {
+    int k = threadIdx.x;
+    double re = 0, im = 0;
+    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) { re += sh[0][k][j]; im += sh[1][k][j]; }
+    size_t off = ((((size_t)L * 9 + part) * Ns + l) * Ns + k) * 2;
+    B[off] = re;
+    B[off + 1] = im;
+  }
+}
+
+// one CTA (32 threads) per block: Gauss-Jordan inverse of B_LL with partial pivoting in shared
+// memory (column-major in and out) and the 1-norm condition number ||B||_1 ||B^{-1}||_1
+__global__ void __launch_bounds__(32) block_inverse_kernel(int Ns, const double* __restrict__ B, double* Binv64,
+                                                           float* Binv32, double* cond) {
+  __shared__ cplx<double> A[NSMAX][NSMAX + 1], X[NSMAX][NSMAX + 1];
+  __shared__ int piv_s;
+  __shared__ bool sing;
+  const int L = blockIdx.x, t = threadIdx.x;
+  const double* src = B + (size_t)L * 9 * Ns * Ns * 2;
+  double colsum = 0;
+  if (t < Ns)
+    for (int row = 0; row < Ns; ++row) {
+      A[row][t] = {src[2 * (t * Ns + row)], src[2 * (t * Ns + row) + 1]};
+      X[row][t] = {row == t ? 1.0 : 0.0, 0.0};
+      colsum += sqrt(norm2(A[row][t]));
+    }
+  double n1 = colsum;
+  for (int o = 16; o > 0; o >>= 1) n1 = fmax(n1, __shfl_xor_sync(0xffffffffu, n1, o));
+  if (t == 0) sing = false;
+  __syncwarp();
+  for (int c = 0; c < Ns; ++c) {
+    // pivot: largest |A[r][c]|, r >= c
+    double v = (t >= c && t < Ns) ? norm2(A[t][c]) : -1.0;
+    int r = t;
+    for (int o = 16; o > 0; o >>= 1) {
+      double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+      int r2 = __shfl_xor_sync(0xffffffffu, r, o);
+      if (v2 > v || (v2 == v && r2 < r)) { v = v2; r = r2; }
+    }
+    if (t == 0) { piv_s = r; if (!(v > 0.0)) sing = true; }
+    __syncwarp();
+    if (sing) break;
+    int pv = piv_s;
+    if (pv != c && t < Ns) {
+      cplx<double> tmp = A[c][t]; A[c][t] = A[pv][t]; A[pv][t] = tmp;
+      tmp = X[c][t]; X[c][t] = X[pv][t]; X[pv][t] = tmp;
+    }
+    __syncwarp();
+    cplx<double> p = A[c][c];
+    double pn = norm2(p);
+    cplx<double> pinv = {p.re / pn, -p.im / pn};
+    __syncwarp();
+    if (t < Ns) { A[c][t] = A[c][t] * pinv; X[c][t] = X[c][t] * pinv; }
+    __syncwarp();
+    if (t < Ns && t != c) {
+      cplx<double> f = A[t][c];
+      for (int b2 = 0; b2 < Ns; ++b2) { A[t][b2] -= f * A[c][b2]; X[t][b2] -= f * X[c][b2]; }
+    }
+    __syncwarp();
+  }
+  double ni = 0;
+  if (t < Ns)
+    for (int row = 0; row < Ns; ++row) {
+      size_t o = (((size_t)L * Ns + t) * Ns + row) * 2;
+      Binv64[o] = X[row][t].re;
+      Binv64[o + 1] = X[row][t].im;
+      Binv32[o] = (float)X[row][t].re;
+      Binv32[o + 1] = (float)X[row][t].im;
+      ni += sqrt(norm2(X[row][t]));
+    }
+  for (int o = 16; o > 0; o >>= 1) ni = fmax(ni, __shfl_xor_sync(0xffffffffu, ni, o));
+  if (t == 0) cond[L] = sing ? INFINITY : n1 * ni;
+}
+
+// M[L][d] = Binv[L] * B[L][1+d]   (column-major, thread per entry)
+__global__ void neighbour_products_kernel(int Nb, int Ns, const double* __restrict__ B,
+                                          const double* __restrict__ Binv, double* M64, float* M32) {
+  size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  size_t total = (size_t)Nb * 8 * Ns * Ns;
+  if (t >= total) return;
+  int row = (int)(t % Ns);
+  int col = (int)((t / Ns) % Ns);
+  int d = (int)((t / ((size_t)Ns * Ns)) % 8);
+  int L = (int)(t / ((size_t)Ns * Ns * 8));
+  const double* bi = Binv + (size_t)L * Ns * Ns * 2;
+  const double* bd = B + ((size_t)L * 9 + 1 + d) * Ns * Ns * 2;
+  cplx<double> s = {0, 0};
+  for (int j = 0; j < Ns; ++j) {
+    cplx<double> a = {bi[2 * (j * Ns + row)], bi[2 * (j * Ns + row) + 1]};
+    cplx<double> b = {bd[2 * (col * Ns + j)], bd[2 * (col * Ns + j) + 1]};
+    s += a * b;
+  }
+  M64[2 * t] = s.re;
+  M64[2 * t + 1] = s.im;
+  M32[2 * t] = (float)s.re;
+  M32[2 * t + 1] = (float)s.im;
+}
+
+// ------------------------------------------------------------------ little vector kernels
+// out[i] = base_coef * base[i] - sum_d M[blk_i][d] src[lnb[i][d]]   (one warp per block, lane = row)
+// base may be null (then the first term is absent).  M column-major: M[((L*8+d)*Ns + col)*Ns + row].
+template <typename T>
+__global__ void little_hop_kernel(int n, int Ns, const int* __restrict__ list, const int* __restrict__ lnb,
+                                  const T* __restrict__ M, const T* __restrict__ src, const T* base, T* out) {
+  int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (wid >= n) return;
+  const int L = __ldg(list + wid);
+  const cplx<T>* Mc = reinterpret_cast<const cplx<T>*>(M);
+  const cplx<T>* S = reinterpret_cast<const cplx<T>*>(src);
+  cplx<T> acc = {T(0), T(0)};
+  for (int d = 0; d < 8; ++d) {
+    int j = __ldg(lnb + wid * 8 + d);
+    const cplx<T>* m = Mc + ((size_t)L * 8 + d) * Ns * Ns;
+    const cplx<T>* sv = S + (size_t)j * Ns;
+    for (int col = 0; col < Ns; ++col) {
+      cplx<T> v = sv[col];
+      if (lane < Ns) acc += m[(size_t)col * Ns + lane] * v;
+    }
+  }
+  if (lane < Ns) {
+    cplx<T>* O = reinterpret_cast<cplx<T>*>(out);
+    cplx<T> b = base ? reinterpret_cast<const cplx<T>*>(base)[(size_t)wid * Ns + lane] : cplx<T>{T(0), T(0)};
+    O[(size_t)wid * Ns + lane] = b - acc;
+  }
+}
+
+// out[i] = Binv[blk_i] * src[i]  (compact parity list vectors)
+template <typename T>
+__global__ void little_bdiag_kernel(int n, int Ns, const int* __restrict__ list, const T* __restrict__ Binv,
+                                    const T* __restrict__ src, T* out) {
+  int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (wid >= n) return;
+  const int L = __ldg(list + wid);
+  const cplx<T>* m = reinterpret_cast<const cplx<T>*>(Binv) + (size_t)L * Ns * Ns;
+  const cplx<T>* sv = reinterpret_cast<const cplx<T>*>(src) + (size_t)wid * Ns;
+  cplx<T> acc = {T(0), T(0)};
+  for (int col = 0; col < Ns; ++col) {
+    cplx<T> v = sv[col];
+    if (lane < Ns) acc += m[(size_t)col * Ns + lane] * v;
+  }
+  if (lane < Ns) reinterpret_cast<cplx<T>*>(out)[(size_t)wid * Ns + lane] = acc;
+}
+
+// gather a parity part of a full little vector ([Nb][Ns]) into compact order / scatter back
+template <typename Tin, typename Tout>
+__global__ void little_gather_kernel(int n, int Ns, const int* __restrict__ list, const Tin* __restrict__ full,
+                                     Tout* part) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * Ns) return;
+  int i = t / Ns, k = t % Ns;
+  size_t src = ((size_t)list[i] * Ns + k) * 2;
+  part[2 * (size_t)t] = (Tout)full[src];
+  part[2 * (size_t)t + 1] = (Tout)full[src + 1];
+}
+template <typename Tin, typename Tout>
+__global__ void little_scatter_kernel(int n, int Ns, const int* __restrict__ list, const Tin* __restrict__ part,
+                                      Tout* full) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * Ns) return;
+  int i = t / Ns, k = t % Ns;
+  size_t dst = ((size_t)list[i] * Ns + k) * 2;
+  full[dst] = (Tout)part[2 * (size_t)t];
+  full[dst + 1] = (Tout)part[2 * (size_t)t + 1];
+}
+
+// full little operator w = A v (FP64), one warp per block
+__global__ void little_full_kernel(int Nb, int Ns, const int* __restrict__ bnb, const double* __restrict__ B,
+                                   const double* __restrict__ v, double* w) {
+  int L = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (L >= Nb) return;
+  const cplx<double>* Bc = reinterpret_cast<const cplx<double>*>(B);
+  const cplx<double>* vc = reinterpret_cast<const cplx<double>*>(v);
+  cplx<double> acc = {0, 0};
+  for (int part = 0; part < 9; ++part) {
+    int src = part == 0 ? L : bnb[L * 8 + part - 1];
+    const cplx<double>* m = Bc + ((size_t)L * 9 + part) * Ns * Ns;
+    for (int col = 0; col < Ns; ++col) {
+      cplx<double> x = vc[(size_t)src * Ns + col];
+      if (lane < Ns) acc += m[(size_t)col * Ns + lane] * x;
+    }
+  }
+  if (lane < Ns) reinterpret_cast<cplx<double>*>(w)[(size_t)L * Ns + lane] = acc;
+}
+
+inline unsigned warps_grid(int n, int threads = 128) { return (unsigned)((n * 32 + threads - 1) / threads); }
+
+}  // namespace
+
+// ====================================================================== host side
+template <typename T>
+static const T* Mp(dfl_ctx* d);
+template <> const float* Mp<float>(dfl_ctx* d) { return d->M32; }
+template <> const double* Mp<double>(dfl_ctx* d) { return d->M64; }
+template <typename T>
+static const T* Binvp(dfl_ctx* d);
+template <> const float* Binvp<float>(dfl_ctx* d) { return d->Binv32; }
+template <> const double* Binvp<double>(dfl_ctx* d) { return d->Binv64; }
+template <typename T>
+static const T* gp(dfl_ctx* d);
+template <> const float* gp<float>(dfl_ctx* d) { return d->g32; }
+template <> const double* gp<double>(dfl_ctx* d) { return d->g64; }
+template <typename T>
+static const T* Bgp(dfl_ctx* d);
+template <> const float* Bgp<float>(dfl_ctx* d) { return d->Bg32; }
+template <> const double* Bgp<double>(dfl_ctx* d) { return d->Bg64; }
+
+// B^ v_e = v_e - M_eo (M_oe v_e);  tmp_o: No*Ns complex
+template <typename T>
+static void apply_bhat(dfl_ctx* d, const T* ve, T* tmp_o, T* out, cudaStream_t s) {
+  little_hop_kernel<T><<<warps_grid(d->No), 128, 0, s>>>(d->No, d->Ns, d->d_list[1], d->d_lnb[1], Mp<T>(d), ve,
+                                                        nullptr, tmp_o);
+  // tmp_o = -M_oe v_e; out = v_e - M_eo(M_oe v_e) = v_e + M_eo tmp_o  ->  use base = v_e and src = -tmp
+  little_hop_kernel<T><<<warps_grid(d->Ne), 128, 0, s>>>(d->Ne, d->Ns, d->d_list[0], d->d_lnb[0], Mp<T>(d), tmp_o,
+                                                        nullptr, out);
+  // out = -M_eo tmp_o = M_eo M_oe v_e ; final = v_e - out
+  blas_xpby<T>(ve, out, -1.0, 0.0, (size_t)d->Ne * d->Ns, s);
+}
+
+extern "C" int dfl_dims(const dfl_ctx* d, int* Nb, int* Ns) {
+  if (!d) { dw_set_error("dfl_dims: null context"); return DW_EINVAL; }
+  if (Nb) *Nb = d->Nb;
+  if (Ns) *Ns = d->Ns;
+  return DW_OK;
+}
+
+extern "C" void dfl_destroy(dfl_ctx* d) {
+  if (!d) return;
+  void* ptrs[] = {d->d_sub, d->d_sap2dfl, d->d_bnb, d->d_list[0], d->d_list[1], d->d_lnb[0], d->d_lnb[1],
+                  d->basis64, d->basis16, d->B64, d->Binv64, d->Binv32, d->M64, d->M32, d->g64, d->g32,
+                  d->Bg64, d->Bg32, d->lw[0], d->lw[1]};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete d;
+}
+
+template <typename T>
+static int restrict_t(dfl_ctx* d, const T* psi, T* c, cudaStream_t s) {
+  restrict_kernel<T><<<d->Nb, 128, 0, s>>>(d->c->g, d->d_sub, d->nsub, d->Ns, d->basis16 ? nullptr : d->basis64,
+                                            d->basis16, psi, c);
+  return DW_OK;
+}
+template <typename T>
+static int prolong_t(dfl_ctx* d, const T* c, T* psi, int mode, cudaStream_t s) {
+  unsigned blocks = (unsigned)((d->c->V + 127) / 128);
+  prolong_kernel<T><<<blocks, 128, 0, s>>>(d->c->g, d->d_sap2dfl, d->Ns, d->basis16 ? nullptr : d->basis64,
+                                            d->basis16, c, psi, mode);
+  return DW_OK;
+}
+int dfl_restrict_f32(dfl_ctx* d, const float* psi, float* c, cudaStream_t s) { return restrict_t(d, psi, c, s); }
+int dfl_restrict_f64(dfl_ctx* d, const double* psi, double* c, cudaStream_t s) { return restrict_t(d, psi, c, s); }
+int dfl_prolong_f32(dfl_ctx* d, const float* c, float* psi, int mode, cudaStream_t s) {
+  return prolong_t(d, c, psi, mode, s);
+}
+int dfl_prolong_f64(dfl_ctx* d, const double* c, double* psi, int mode, cudaStream_t s) {
+  return prolong_t(d, c, psi, mode, s);
+}
+
+extern "C" int dfl_restrict(dfl_ctx* d, int prec, const void* psi, void* c, void* stream) {
+  if (!d || !psi || !c || (prec != DW_F32 && prec != DW_F64)) { dw_set_error("dfl_restrict: bad argument"); return DW_EINVAL; }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (prec == DW_F64) restrict_t(d, (const double*)psi, (double*)c, s);
+  else restrict_t(d, (const float*)psi, (float*)c, s);
+  DW_CUDA(cudaGetLastError());
+  return DW_OK;
+}
+extern "C" int dfl_prolong(dfl_ctx* d, int prec, const void* c, void* psi, void* stream) {
+  if (!d || !psi || !c || (prec != DW_F32 && prec != DW_F64)) { dw_set_error("dfl_prolong: bad argument"); return DW_EINVAL; }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (prec == DW_F64) prolong_t(d, (const double*)c, (double*)psi, 0, s);
+  else prolong_t(d, (const float*)c, (float*)psi, 0, s);
+  DW_CUDA(cudaGetLastError());
+  return DW_OK;
+}
+extern "C" int dfl_basis_export(dfl_ctx* d, double* canon, void* stream) {
+  if (!d || !canon) { dw_set_error("dfl_basis_export: bad argument"); return DW_EINVAL; }
+  return dw_unpack(d->c, DW_F64, d->Ns, d->basis64, canon, stream);
+}
+extern "C" int little_apply(dfl_ctx* d, const double* v, double* w, void* stream) {
+  if (!d || !v || !w || v == w) { dw_set_error("little_apply: bad argument"); return DW_EINVAL; }
+  little_full_kernel<<<warps_grid(d->Nb), 128, 0, (cudaStream_t)stream>>>(d->Nb, d->Ns, d->d_bnb, d->B64, v, w);
+  DW_CUDA(cudaGetLastError());
+  return DW_OK;
+}
+
+// ---------------------------------------------------------------------- little GCR
+// Work buffers (precision T), each n = Ne*Ns complex:
+//   0..nkv-1 chi, nkv..2nkv-1 xi (= rho_k copies), then rho, t, tmp_o, wt, yo, ...
+template <typename T>
+static T* lwork(dfl_ctx* d, int idx) {
+  constexpr int P = prec_of<T>();
+  size_t n = (size_t)d->Ne * d->Ns * 2;
+  return (T*)d->lw[P] + (size_t)idx * n;
+}
+
+static int sync_read(dw_ctx* c, const double* dev, int count, double* host, cudaStream_t s) {
+  DW_CUDA(cudaMemcpyAsync(c->h_red, dev, count * sizeof(double), cudaMemcpyDeviceToHost, s));
+  DW_CUDA(cudaStreamSynchronize(s));
+  for (int i = 0; i < count; ++i) host[i] = c->h_red[i];
+  return DW_OK;
+}
+
+// P~_L u (in place): u -= (B^ g) A~^{-1} g^+ u.  scratch: device double[2*Ns]
+template <typename T>
+static int little_PL(dfl_ctx* d, T* u, cudaStream_t s) {
+  const int Ns = d->Ns;
+  size_t n = (size_t)d->Ne * Ns;
+  std::vector<const T*> gs(Ns), bgs(Ns);
+  for (int l = 0; l < Ns; ++l) { gs[l] = gp<T>(d) + (size_t)l * 2 * n; bgs[l] = Bgp<T>(d) + (size_t)l * 2 * n; }
+  double* dres = d->c->d_red + 65536;
+  blas_multi_dot<T>(d->c, gs.data(), Ns, u, n, dres, s);
+  std::vector<double> h(2 * Ns);
+  int rc = sync_read(d->c, dres, 2 * Ns, h.data(), s);
+  if (rc) return rc;
+  std::vector<double> y(2 * Ns);
+  for (int a = 0; a < Ns; ++a) {
+    cd acc = 0;
+    for (int b = 0; b < Ns; ++b) acc += d->Atil_inv[a * Ns + b] * cd(h[2 * b], h[2 * b + 1]);
+    y[2 * a] = acc.real();
+    y[2 * a + 1] = acc.imag();
+  }
+  blas_multi_axpy<T>(bgs.data(), Ns, y.data(), u, n, s);
+  return DW_OK;
+}
+
+// v_e += g A~^{-1} g^+ r   (the coarse correction)
+template <typename T>
+static int little_coarse_add(dfl_ctx* d, const T* r, T* v, cudaStream_t s) {
+  const int Ns = d->Ns;
+  size_t n = (size_t)d->Ne * Ns;
+  std::vector<const T*> gs(Ns);
+  for (int l = 0; l < Ns; ++l) gs[l] = gp<T>(d) + (size_t)l * 2 * n;
+  double* dres = d->c->d_red + 65536;
+  blas_multi_dot<T>(d->c, gs.data(), Ns, r, n, dres, s);
+  std::vector<double> h(2 * Ns);
+  int rc = sync_read(d->c, dres, 2 * Ns, h.data(), s);
+  if (rc) return rc;
+  std::vector<double> y(2 * Ns);
+  for (int a = 0; a < Ns; ++a) {
+    cd acc = 0;
+    for (int b = 0; b < Ns; ++b) acc += d->Atil_inv[a * Ns + b] * cd(h[2 * b], h[2 * b + 1]);
+    y[2 * a] = -acc.real();        // multi_axpy subtracts
+    y[2 * a + 1] = -acc.imag();
+  }
+  blas_multi_axpy<T>(gs.data(), Ns, y.data(), v, n, s);
+  return DW_OK;
+}
+
+// Solve B^ v_e = b_e (deflated by A.3 when available) by restarted GCR.  Returns iterations.
+template <typename T>
+static int little_gcr(dfl_ctx* d, const T* b, T* v, double tol, int maxit, int nkv, int* iters, double* relres,
+                      cudaStream_t s) {
+  const int Ns = d->Ns;
+  const size_t n = (size_t)d->Ne * Ns;
+  T* chi0 = lwork<T>(d, 0);
+  T* xi0 = lwork<T>(d, nkv);
+  T* rho = lwork<T>(d, 2 * nkv);
+  T* tmpo = lwork<T>(d, 2 * nkv + 1);
+  T* rhs = lwork<T>(d, 2 * nkv + 2);
+  T* t = lwork<T>(d, 2 * nkv + 3);
+  auto chi = [&](int k) { return chi0 + (size_t)k * 2 * n; };
+  auto xi = [&](int k) { return xi0 + (size_t)k * 2 * n; };
+  double* dres = d->c->d_red + 65536;
+  std::vector<double> hbuf(2 * (nkv + 2));
+  // rhs = P~_L b
+  DW_CUDA(cudaMemcpyAsync(rhs, b, n * 2 * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  int rc;
+  if (d->a3 && (rc = little_PL<T>(d, rhs, s))) return rc;
+  blas_dot<T>(d->c, rhs, rhs, n, dres, s);
+  if ((rc = sync_read(d->c, dres, 3, hbuf.data(), s))) return rc;
+  const double bn = sqrt(hbuf[2]);
+  DW_CUDA(cudaMemsetAsync(v, 0, n * 2 * sizeof(T), s));
+  *iters = 0;
+  *relres = 0;
+  if (bn == 0.0) {
+    if (d->a3) little_coarse_add<T>(d, b, v, s);
+    return DW_OK;
+  }
+  DW_CUDA(cudaMemcpyAsync(rho, rhs, n * 2 * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  double rn = bn;
+  int total = 0;
+  std::vector<cd> a(nkv), cc(nkv);
+  std::vector<cd> bb((size_t)nkv * nkv);
+  while (rn > tol * bn && total < maxit) {
+    int k = 0;
+    for (; k < nkv && total < maxit; ++k, ++total) {
+      DW_CUDA(cudaMemcpyAsync(xi(k), rho, n * 2 * sizeof(T), cudaMemcpyDeviceToDevice, s));
+      apply_bhat<T>(d, xi(k), tmpo, chi(k), s);
+      if (d->a3 && (rc = little_PL<T>(d, chi(k), s))) return rc;
+      if (k > 0) {
+        std::vector<const T*> prev(k);
+        for (int j = 0; j < k; ++j) prev[j] = chi(j);
+        blas_multi_dot<T>(d->c, prev.data(), k, chi(k), n, dres, s);
+        if ((rc = sync_read(d->c, dres, 2 * k, hbuf.data(), s))) return rc;
+        std::vector<double> coef(2 * k);
+        for (int j = 0; j < k; ++j) {
+          bb[(size_t)j * nkv + k] = cd(hbuf[2 * j], hbuf[2 * j + 1]);
+          coef[2 * j] = hbuf[2 * j];
+          coef[2 * j + 1] = hbuf[2 * j + 1];
+        }
+        blas_multi_axpy<T>(prev.data(), k, coef.data(), chi(k), n, s);
+      }
+      blas_dot<T>(d->c, chi(k), rho, n, dres, s);
+      if ((rc = sync_read(d->c, dres, 3, hbuf.data(), s))) return rc;
+      double ck = sqrt(hbuf[2]);
+      if (!(ck > 0)) break;
+      cc[k] = ck;
+      a[k] = cd(hbuf[0], hbuf[1]) / ck;
+      blas_scale<T>(chi(k), 1.0 / ck, 0.0, n, s);
+      blas_axpy<T>(chi(k), rho, -a[k].real(), -a[k].imag(), n, s);
+      blas_dot<T>(d->c, rho, rho, n, dres, s);
+      if ((rc = sync_read(d->c, dres, 3, hbuf.data(), s))) return rc;
+      rn = sqrt(hbuf[2]);
+      if (rn <= tol * bn) { ++k; ++total; break; }
+    }
+    // back substitution and update v += sum beta_k xi_k
+    std::vector<cd> beta(k);
+    for (int j = k - 1; j >= 0; --j) {
+      cd sacc = a[j];
+      for (int i = j + 1; i < k; ++i) sacc -= bb[(size_t)j * nkv + i] * beta[i];
+      beta[j] = sacc / cc[j];
+    }
+    std::vector<const T*> xs(k);
+    std::vector<double> coef(2 * k);
+    for (int j = 0; j < k; ++j) { xs[j] = xi(j); coef[2 * j] = -beta[j].real(); coef[2 * j + 1] = -beta[j].imag(); }
+    if (k > 0) blas_multi_axpy<T>(xs.data(), k, coef.data(), v, n, s);
+    // true residual of the deflated system: rho = rhs - P~_L B^ v
+    apply_bhat<T>(d, v, tmpo, t, s);
+    if (d->a3 && (rc = little_PL<T>(d, t, s))) return rc;
+    DW_CUDA(cudaMemcpyAsync(rho, rhs, n * 2 * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    blas_axpy<T>(t, rho, -1.0, 0.0, n, s);
+    blas_dot<T>(d->c, rho, rho, n, dres, s);
+    if ((rc = sync_read(d->c, dres, 3, hbuf.data(), s))) return rc;
+    rn = sqrt(hbuf[2]);
+    if (k == 0) break;
+  }
+  *iters = total;
+  *relres = rn / bn;
+  if (d->a3) {
+    // v = P~_R chi + g A~^{-1} g^+ b = chi + g A~^{-1} g^+ (b - B^ chi)
+    apply_bhat<T>(d, v, tmpo, t, s);
+    DW_CUDA(cudaMemcpyAsync(rho, b, n * 2 * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    blas_axpy<T>(t, rho, -1.0, 0.0, n, s);
+    if ((rc = little_coarse_add<T>(d, rho, v, s))) return rc;
+  }
+  return rn <= tol * bn ? DW_OK : DW_ENOTCONV;
+}
+
+static int ensure_little_work(dfl_ctx* d, int prec, int nkv) {
+  size_t count = (size_t)2 * nkv + 8;
+  size_t n = (size_t)d->Ne * d->Ns * 2;
+  if (d->lw[prec] && d->lw_count >= count) return DW_OK;
+  for (int p = 0; p < 2; ++p)
+    if (d->lw[p]) { cudaFree(d->lw[p]); d->lw[p] = nullptr; }
+  d->lw_count = count;
+  DW_CUDA(cudaMalloc(&d->lw[DW_F64], count * n * sizeof(double)));
+  DW_CUDA(cudaMalloc(&d->lw[DW_F32], count * n * sizeof(float)));
+  return DW_OK;
+}
+
+// Full little solve A v = w (prec T; w, v: [Nb][Ns] complex of T)
+template <typename T>
+static int little_solve_t(dfl_ctx* d, const T* w, T* v, double tol, int maxit, int nkv, int* iters, double* relres,
+                          cudaStream_t s) {
+  int rc = ensure_little_work(d, prec_of<T>(), nkv);
+  if (rc) return rc;
+  const int Ns = d->Ns;
+  size_t n_e = (size_t)d->Ne * Ns, n_o = (size_t)d->No * Ns;
+  T* we = lwork<T>(d, 2 * nkv + 4);
+  T* wo = lwork<T>(d, 2 * nkv + 5);
+  T* yo = lwork<T>(d, 2 * nkv + 6);
+  T* wt = lwork<T>(d, 2 * nkv + 7);
+  unsigned ge = (unsigned)((n_e + 255) / 256), go = (unsigned)((n_o + 255) / 256);
+  little_gather_kernel<T, T><<<ge, 256, 0, s>>>(d->Ne, Ns, d->d_list[0], w, we);
+  little_gather_kernel<T, T><<<go, 256, 0, s>>>(d->No, Ns, d->d_list[1], w, wo);
+  // yo = B_oo^{-1} w_o ; wt = B_ee^{-1} w_e - M_eo yo
+  little_bdiag_kernel<T><<<warps_grid(d->No), 128, 0, s>>>(d->No, Ns, d->d_list[1], Binvp<T>(d), wo, yo);
+  little_bdiag_kernel<T><<<warps_grid(d->Ne), 128, 0, s>>>(d->Ne, Ns, d->d_list[0], Binvp<T>(d), we, wt);
+  little_hop_kernel<T><<<warps_grid(d->Ne), 128, 0, s>>>(d->Ne, Ns, d->d_list[0], d->d_lnb[0], Mp<T>(d), yo, wt, we);
+  // we now holds w~_e ; solve B^ v_e = w~_e into wt
+  rc = little_gcr<T>(d, we, wt, tol, maxit, nkv, iters, relres, s);
+  if (rc < 0) return rc;
+  // v_o = yo - M_oe v_e  -> into wo
+  little_hop_kernel<T><<<warps_grid(d->No), 128, 0, s>>>(d->No, Ns, d->d_list[1], d->d_lnb[1], Mp<T>(d), wt, yo, wo);
+  little_scatter_kernel<T, T><<<ge, 256, 0, s>>>(d->Ne, Ns, d->d_list[0], wt, v);
+  little_scatter_kernel<T, T><<<go, 256, 0, s>>>(d->No, Ns, d->d_list[1], wo, v);
+  DW_CUDA(cudaGetLastError());
+  return rc;
+}
+int little_solve_f32(dfl_ctx* d, const float* w, float* v, double tol, int maxit, int nkv, int* it, double* rr,
+                     cudaStream_t s) {
+  return little_solve_t(d, w, v, tol, maxit, nkv, it, rr, s);
+}
+int little_solve_f64(dfl_ctx* d, const double* w, double* v, double tol, int maxit, int nkv, int* it, double* rr,
+                     cudaStream_t s) {
+  return little_solve_t(d, w, v, tol, maxit, nkv, it, rr, s);
+}
+int dfl_nlittle(const dfl_ctx* d) { return d->N; }
+
+extern "C" int little_dirac_solve(dfl_ctx* d, int prec, const void* w, void* v, double tol, int maxit, int* iters,
+                                  double* relres, void* stream) {
+  if (!d || !w || !v || w == v || (prec != DW_F32 && prec != DW_F64) || maxit < 1 || !(tol > 0)) {
+    dw_set_error("little_dirac_solve: bad argument");
+    return DW_EINVAL;
+  }
+  int it = 0;
+  double rr = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = prec == DW_F64 ? little_solve_t(d, (const double*)w, (double*)v, tol, maxit, 24, &it, &rr, s)
+                          : little_solve_t(d, (const float*)w, (float*)v, tol, maxit, 24, &it, &rr, s);
+  if (iters) *iters = it;
+  if (relres) *relres = rr;
+  if (rc >= 0) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return dw_cuda_fail(e, "little_dirac_solve");
+  }
+  return rc;
+}
+
+// ---------------------------------------------------------------------- build
+static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_ctx* d, dfl_info* info) {
+  const Geom& g = c->g;
+  const size_t V = c->V;
+  const int Ns = p->Ns;
+  cudaStream_t s = 0;
+  auto t0 = std::chrono::steady_clock::now();
+  // ---- tables
+  std::vector<int> bcoord((size_t)d->Nb * 4), sap2dfl(g.nsap), sub((size_t)d->Nb * d->nsub, -1), fill(d->Nb, 0),
+      bnb((size_t)d->Nb * 8);
+  for (int L = 0; L < d->Nb; ++L) {
+    int r = L;
+    for (int mu = 3; mu >= 0; --mu) { bcoord[L * 4 + mu] = r % d->nb[mu]; r /= d->nb[mu]; }
+    for (int dd = 0; dd < 8; ++dd) {
+      int mu = dd / 2, sg = (dd & 1) ? -1 : 1;
+      int nc[4] = {bcoord[L * 4], bcoord[L * 4 + 1], bcoord[L * 4 + 2], bcoord[L * 4 + 3]};
+      nc[mu] = (nc[mu] + sg + d->nb[mu]) % d->nb[mu];
+      bnb[L * 8 + dd] = ((nc[0] * d->nb[1] + nc[1]) * d->nb[2] + nc[2]) * d->nb[3] + nc[3];
+    }
+  }
+  for (int b = 0; b < g.nsap; ++b) {
+    int r = b, bc[4];
+    for (int mu = 3; mu >= 0; --mu) { bc[mu] = r % c->nsb[mu]; r /= c->nsb[mu]; }
+    int dc[4];
+    for (int mu = 0; mu < 4; ++mu) dc[mu] = bc[mu] * g.sb[mu] / d->bs[mu];
+    int L = ((dc[0] * d->nb[1] + dc[1]) * d->nb[2] + dc[2]) * d->nb[3] + dc[3];
+    sap2dfl[b] = L;
+    sub[(size_t)L * d->nsub + fill[L]++] = b;
+  }
+  // parity lists and neighbour positions
+  std::vector<int> list[2], pos(d->Nb);
+  for (int L = 0; L < d->Nb; ++L) {
+    int par = (bcoord[L * 4] + bcoord[L * 4 + 1] + bcoord[L * 4 + 2] + bcoord[L * 4 + 3]) & 1;
+    pos[L] = (int)list[par].size();
+    list[par].push_back(L);
+  }
+  d->Ne = (int)list[0].size();
+  d->No = (int)list[1].size();
+  std::vector<int> lnb[2];
+  for (int par = 0; par < 2; ++par)
+    for (int L : list[par])
+      for (int dd = 0; dd < 8; ++dd) lnb[par].push_back(pos[bnb[L * 8 + dd]]);
+  auto up = [&](int** dst, const std::vector<int>& v) -> int {
+    DW_CUDA(cudaMalloc(dst, v.size() * sizeof(int)));
+    DW_CUDA(cudaMemcpy(*dst, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice));
+    return DW_OK;
+  };
+  int rc;
+  if ((rc = up(&d->d_sub, sub)) || (rc = up(&d->d_sap2dfl, sap2dfl)) || (rc = up(&d->d_bnb, bnb)) ||
+      (rc = up(&d->d_list[0], list[0])) || (rc = up(&d->d_list[1], list[1])) || (rc = up(&d->d_lnb[0], lnb[0])) ||
+      (rc = up(&d->d_lnb[1], lnb[1])))
+    return rc;
+
+  // ---- inverse iteration (5.1) in the requested precision
+  const int ip = p->iter_prec == DW_F64 ? DW_F64 : DW_F32;
+  const size_t fb = dw_field_bytes(c, ip);
+  void* work = nullptr;
+  void* tmp = nullptr;
+  DW_CUDA(cudaMalloc(&work, fb * Ns));
+  DW_CUDA(cudaMalloc(&tmp, fb));
+  struct Free { void* a; void* b; ~Free() { if (a) cudaFree(a); if (b) cudaFree(b); } } guard{work, tmp};
+  if ((rc = dw_pack(c, ip, Ns, start, work, s))) return rc;
+  const size_t n = V * 12;
+  std::vector<double> h(3);
+  for (int it = 0; it < p->n_inv; ++it)
+    for (int l = 0; l < Ns; ++l) {
+      if (ip == DW_F64) {
+        double* w = (double*)work + (size_t)l * 24 * V;
+        if ((rc = sap_apply<double>(c, p->ncy, p->nmr, w, (double*)tmp, s))) return rc;
+        blas_dot<double>(c, (double*)tmp, (double*)tmp, n, c->d_red + 65536, s);
+        if ((rc = sync_read(c, c->d_red + 65536, 3, h.data(), s))) return rc;
+        blas_convert<double, double>((double*)tmp, w, 1.0 / sqrt(h[2]), n, s);
+      } else {
+        float* w = (float*)work + (size_t)l * 24 * V;
+        if ((rc = sap_apply<float>(c, p->ncy, p->nmr, w, (float*)tmp, s))) return rc;
+        blas_dot<float>(c, (float*)tmp, (float*)tmp, n, c->d_red + 65536, s);
+        if ((rc = sync_read(c, c->d_red + 65536, 3, h.data(), s))) return rc;
+        blas_convert<float, float>((float*)tmp, w, 1.0 / sqrt(h[2]), n, s);
+      }
+    }
+  // ---- block Gram-Schmidt in FP64
+  DW_CUDA(cudaMalloc(&d->basis64, (size_t)Ns * 24 * V * sizeof(double)));
+  if (ip == DW_F64) DW_CUDA(cudaMemcpyAsync(d->basis64, work, fb * Ns, cudaMemcpyDeviceToDevice, s));
+  else blas_convert<float, double>((const float*)work, d->basis64, 1.0, n * Ns, s);
+  int* d_flag = (int*)(c->d_count + 40);
+  DW_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), s));
+  block_gs_kernel<<<d->Nb, 256, 0, s>>>(g, d->d_sub, d->nsub, Ns, d->basis64, d_flag);
+  int flag = 0;
+  DW_CUDA(cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DW_CUDA(cudaStreamSynchronize(s));
+  if (flag) { dw_set_error("deflation_build: rank loss in the block Gram-Schmidt"); return DW_EINVAL; }
+  if (p->basis_prec == DW_BF16) {
+    DW_CUDA(cudaMalloc(&d->basis16, (size_t)Ns * 3 * V * sizeof(uint4)));
+    size_t tot = V * Ns;
+    quantize_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(V, Ns, d->basis64, d->basis16);
+  }
+  auto t1 = std::chrono::steady_clock::now();
+  // ---- little operator (A.1) from the stored basis, FP64
+  const size_t mat = (size_t)Ns * Ns * 2;
+  DW_CUDA(cudaMalloc(&d->B64, d->Nb * 9 * mat * sizeof(double)));
+  assemble_kernel<<<(unsigned)(d->Nb * 9 * Ns), 128, 0, s>>>(g, d->d_sub, d->nsub, d->d_sap2dfl, Ns,
+                                                            (const double*)c->links[DW_F64],
+                                                            (const double*)c->clov[DW_F64], d->basis64, d->B64);
+  DW_CUDA(cudaGetLastError());
+  DW_CUDA(cudaMalloc(&d->Binv64, d->Nb * mat * sizeof(double)));
+  DW_CUDA(cudaMalloc(&d->Binv32, d->Nb * mat * sizeof(float)));
+  DW_CUDA(cudaMalloc(&d->M64, d->Nb * 8 * mat * sizeof(double)));
+  DW_CUDA(cudaMalloc(&d->M32, d->Nb * 8 * mat * sizeof(float)));
+  double* d_cond;
+  DW_CUDA(cudaMalloc(&d_cond, d->Nb * sizeof(double)));
+  block_inverse_kernel<<<d->Nb, 32, 0, s>>>(Ns, d->B64, d->Binv64, d->Binv32, d_cond);
+  size_t tot = (size_t)d->Nb * 8 * Ns * Ns;
+  neighbour_products_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d->Nb, Ns, d->B64, d->Binv64, d->M64,
+                                                                          d->M32);
+  std::vector<double> cond(d->Nb);
+  DW_CUDA(cudaMemcpyAsync(cond.data(), d_cond, d->Nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+  DW_CUDA(cudaStreamSynchronize(s));
+  cudaFree(d_cond);
+  d->max_cond = 0;
+  for (double x : cond) d->max_cond = std::max(d->max_cond, std::isfinite(x) ? x : INFINITY);
+  d->illcond = !(d->max_cond <= p->cond_max);
+
+  // ---- global-mode deflation (A.3): g_l = even-block part of Phi^+ psi_l, orthonormalised
+  d->a3 = false;
+  if (!d->illcond) {
+    const size_t ne = (size_t)d->Ne * Ns;
+    std::vector<cd> G((size_t)Ns * ne);
+    double* cfull;
+    DW_CUDA(cudaMalloc(&cfull, (size_t)d->N * 2 * sizeof(double)));
+    double* f64 = nullptr;
+    if (ip == DW_F32) DW_CUDA(cudaMalloc(&f64, fb * 2));
+    std::vector<double> hc((size_t)d->N * 2);
+    for (int l = 0; l < Ns; ++l) {
+      const double* src;
+      if (ip == DW_F64) src = (const double*)work + (size_t)l * 24 * V;
+      else {
+        blas_convert<float, double>((const float*)work + (size_t)l * 24 * V, f64, 1.0, n, s);
+        src = f64;
+      }
+      restrict_kernel<double><<<d->Nb, 128, 0, s>>>(g, d->d_sub, d->nsub, Ns, d->basis64, nullptr, src, cfull);
+      DW_CUDA(cudaMemcpyAsync(hc.data(), cfull, hc.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+      DW_CUDA(cudaStreamSynchronize(s));
+      for (int i = 0; i < d->Ne; ++i)
+        for (int k = 0; k < Ns; ++k) {
+          size_t o = ((size_t)list[0][i] * Ns + k) * 2;
+          G[(size_t)l * ne + (size_t)i * Ns + k] = cd(hc[o], hc[o + 1]);
+        }
+    }
+    cudaFree(cfull);
+    if (f64) cudaFree(f64);
+    // modified Gram-Schmidt with re-orthogonalisation (host, FP64)
+    bool ok = true;
+    for (int l = 0; l < Ns && ok; ++l) {
+      cd* v = &G[(size_t)l * ne];
+      double n0 = 0;
+      for (size_t i = 0; i < ne; ++i) n0 += std::norm(v[i]);
+      for (int pass = 0; pass < 2; ++pass)
+        for (int j = 0; j < l; ++j) {
+          const cd* u = &G[(size_t)j * ne];
+          cd z = 0;
+          for (size_t i = 0; i < ne; ++i) z += std::conj(u[i]) * v[i];
+          for (size_t i = 0; i < ne; ++i) v[i] -= z * u[i];
+        }
+      double n1 = 0;
+      for (size_t i = 0; i < ne; ++i) n1 += std::norm(v[i]);
+      if (!(n1 > 1e-24 * n0)) { ok = false; break; }
+      double sc = 1.0 / sqrt(n1);
+      for (size_t i = 0; i < ne; ++i) v[i] *= sc;
+    }
+    if (ok) {
+      if ((rc = ensure_little_work(d, DW_F64, 24))) return rc;
+      DW_CUDA(cudaMalloc(&d->g64, Ns * ne * 2 * sizeof(double)));
+      DW_CUDA(cudaMalloc(&d->g32, Ns * ne * 2 * sizeof(float)));
+      DW_CUDA(cudaMalloc(&d->Bg64, Ns * ne * 2 * sizeof(double)));
+      DW_CUDA(cudaMalloc(&d->Bg32, Ns * ne * 2 * sizeof(float)));
+      DW_CUDA(cudaMemcpy(d->g64, G.data(), Ns * ne * sizeof(cd), cudaMemcpyHostToDevice));
+      blas_convert<double, float>(d->g64, d->g32, 1.0, Ns * ne, s);
+      double* tmpo = lwork<double>(d, 0);
+      for (int l = 0; l < Ns; ++l)
+        apply_bhat<double>(d, d->g64 + (size_t)l * ne * 2, tmpo, d->Bg64 + (size_t)l * ne * 2, s);
+      blas_convert<double, float>(d->Bg64, d->Bg32, 1.0, Ns * ne, s);
+      // A~ = g^+ B^ g
+      std::vector<cd> Bg((size_t)Ns * ne);
+      DW_CUDA(cudaMemcpyAsync(Bg.data(), d->Bg64, Ns * ne * sizeof(cd), cudaMemcpyDeviceToHost, s));
+      DW_CUDA(cudaStreamSynchronize(s));
+      std::vector<cd> At((size_t)Ns * Ns), X((size_t)Ns * Ns);
+      for (int a = 0; a < Ns; ++a)
+        for (int b = 0; b < Ns; ++b) {
+          cd z = 0;
+          for (size_t i = 0; i < ne; ++i) z += std::conj(G[(size_t)a * ne + i]) * Bg[(size_t)b * ne + i];
+          At[a * Ns + b] = z;
+          X[a * Ns + b] = a == b ? 1.0 : 0.0;
+        }
+      for (int col = 0; col < Ns && ok; ++col) {   // Gauss-Jordan with partial pivoting
+        int piv = col;
+        for (int r = col + 1; r < Ns; ++r)
+          if (std::abs(At[r * Ns + col]) > std::abs(At[piv * Ns + col])) piv = r;
+        if (std::abs(At[piv * Ns + col]) == 0.0) { ok = false; break; }
+        for (int b = 0; b < Ns; ++b) { std::swap(At[col * Ns + b], At[piv * Ns + b]); std::swap(X[col * Ns + b], X[piv * Ns + b]); }
+        cd pinv = 1.0 / At[col * Ns + col];
+        for (int b = 0; b < Ns; ++b) { At[col * Ns + b] *= pinv; X[col * Ns + b] *= pinv; }
+        for (int r = 0; r < Ns; ++r) {
+          if (r == col) continue;
+          cd f = At[r * Ns + col];
+          for (int b = 0; b < Ns; ++b) { At[r * Ns + b] -= f * At[col * Ns + b]; X[r * Ns + b] -= f * X[col * Ns + b]; }
+        }
+      }
+      if (ok) { d->Atil_inv = X; d->a3 = true; }
+    }
+  }
+  auto t2 = std::chrono::steady_clock::now();
+  if (info) {
+    info->seconds = std::chrono::duration<double>(t2 - t0).count();
+    info->seconds_little = std::chrono::duration<double>(t2 - t1).count();
+    info->max_block_cond = d->max_cond;
+    info->Nb = d->Nb;
+    info->N = d->N;
+  }
+  return d->illcond ? DW_ILLCOND : DW_OK;
+}
+
+extern "C" int deflation_build(dw_ctx* c, const dfl_params* p, const double* start, dfl_ctx** out, dfl_info* info) {
+  if (!c || !p || !start || !out) { dw_set_error("deflation_build: null argument"); return DW_EINVAL; }
+  *out = nullptr;
+  if (p->Ns < 1 || p->Ns > NSMAX || p->n_inv < 0 || p->ncy < 0 || p->nmr < 0 ||
+      (p->basis_prec != DW_BF16 && p->basis_prec != DW_F64)) {
+    dw_set_error("deflation_build: Ns must be in 1..32, counts non-negative, basis_prec DW_BF16 or DW_F64");
+    return DW_EINVAL;
+  }
+  dfl_ctx* d = new dfl_ctx();
+  d->c = c;
+  d->p = *p;
+  d->Ns = p->Ns;
+  d->Nb = 1;
+  d->nsub = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    int b = p->bs[mu];
+    if (b <= 0 || b % c->g.sb[mu] != 0 || c->p.L[mu] % b != 0 || (c->p.L[mu] / b) % 2 != 0) {
+      delete d;
+      dw_set_error("deflation_build: bs[mu] must be a multiple of the Schwarz block dividing L[mu] an even number of times");
+      return DW_EINVAL;
+    }
+    d->bs[mu] = b;
+    d->nb[mu] = c->p.L[mu] / b;
+    d->Nb *= d->nb[mu];
+    d->nsub *= b / c->g.sb[mu];
+  }
+  d->N = d->Nb * d->Ns;
+  int rc = build_impl(c, p, start, d, info);
+  if (rc < 0) { dfl_destroy(d); return rc; }
+  *out = d;
+  return rc;
+}

@@ -1,0 +1,295 @@
+// Deflated, Schwarz-preconditioned flexible GCR for D psi = eta (3.9).
+//
+// Paper: deflated equation (3.10)-(3.11), right preconditioning by M_sap
+// (6.2), GCR with restarts and inexact preconditioning (Section 6.2),
+// adapted little-solve precision and high-precision restart residuals (A.5).
+//
+// Every restart:
+//   rho = eta - D psi                            FP64
+//   c = A^{-1} Phi^+ rho  (FP64 little solve, little_tol_out); psi += Phi c; rho = eta - D psi
+//   stop if ||rho|| <= tol ||eta||
+//   one GCR cycle in the inner precision on  P_L D M_sap phi = rho / ||rho||:
+//       xi_k = M_sap rho_k,  w = D xi_k,  chi_k = P_L w = w - D Phi A^{-1} Phi^+ w
+//       (little tolerance min(cap, tol_in * ||rho_0|| / ||w||))
+//       Gram-Schmidt of chi_k against chi_0..k-1, rho_{k+1} = rho_k - a_k chi_k
+//   psi += ||rho|| * sum_k beta_k xi_k           FP64 accumulation
+// The -Phi A^{-1} Phi^+ D zeta part of P_R zeta is supplied by the next
+// restart's deflation correction, so psi ends as psi + P_R zeta + Phi A^{-1} Phi^+ rho.
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <vector>
+
+#include "dw_common.cuh"
+
+using cd = std::complex<double>;
+
+// provided by dw_dfl.cu
+int dfl_restrict_f32(dfl_ctx*, const float*, float*, cudaStream_t);
+int dfl_restrict_f64(dfl_ctx*, const double*, double*, cudaStream_t);
+int dfl_prolong_f32(dfl_ctx*, const float*, float*, int, cudaStream_t);
+int dfl_prolong_f64(dfl_ctx*, const double*, double*, int, cudaStream_t);
+int little_solve_f32(dfl_ctx*, const float*, float*, double, int, int, int*, double*, cudaStream_t);
+int little_solve_f64(dfl_ctx*, const double*, double*, double, int, int, int*, double*, cudaStream_t);
+int dfl_nlittle(const dfl_ctx*);
+
+namespace {
+
+inline int restrict_(dfl_ctx* d, const float* a, float* b, cudaStream_t s) { return dfl_restrict_f32(d, a, b, s); }
+inline int restrict_(dfl_ctx* d, const double* a, double* b, cudaStream_t s) { return dfl_restrict_f64(d, a, b, s); }
+inline int prolong_(dfl_ctx* d, const float* a, float* b, int m, cudaStream_t s) { return dfl_prolong_f32(d, a, b, m, s); }
+inline int prolong_(dfl_ctx* d, const double* a, double* b, int m, cudaStream_t s) { return dfl_prolong_f64(d, a, b, m, s); }
+inline int lsolve_(dfl_ctx* d, const float* w, float* v, double tol, int maxit, int nkv, int* it, double* rr,
+                   cudaStream_t s) {
+  return little_solve_f32(d, w, v, tol, maxit, nkv, it, rr, s);
+}
+inline int lsolve_(dfl_ctx* d, const double* w, double* v, double tol, int maxit, int nkv, int* it, double* rr,
+                   cudaStream_t s) {
+  return little_solve_f64(d, w, v, tol, maxit, nkv, it, rr, s);
+}
+
+enum Phase { PH_SAP, PH_DIRAC, PH_PROJECT, PH_LITTLE, PH_ORTH, PH_RESTART, PH_N };
+
+struct Timers {
+  cudaStream_t s;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[PH_N];
+  int open = -1;
+  cudaEvent_t cur;
+  void begin(int ph) {
+    cudaEventCreate(&cur);
+    cudaEventRecord(cur, s);
+    open = ph;
+  }
+  void end() {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, s);
+    ev[open].push_back({cur, e});
+    open = -1;
+  }
+  void collect(sol_info* in) {
+    double t[PH_N] = {0};
+    for (int p = 0; p < PH_N; ++p)
+      for (auto& pr : ev[p]) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, pr.first, pr.second);
+        t[p] += ms * 1e-3;
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+      }
+    if (in) {
+      in->t_sap = t[PH_SAP]; in->t_dirac = t[PH_DIRAC]; in->t_project = t[PH_PROJECT];
+      in->t_little = t[PH_LITTLE]; in->t_orth = t[PH_ORTH]; in->t_restart = t[PH_RESTART];
+    }
+  }
+};
+
+int read_host(dw_ctx* c, const double* dev, int n, double* host, cudaStream_t s) {
+  DW_CUDA(cudaMemcpyAsync(c->h_red, dev, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  DW_CUDA(cudaStreamSynchronize(s));
+  for (int i = 0; i < n; ++i) host[i] = c->h_red[i];
+  return DW_OK;
+}
+
+template <typename T>
+struct Work {
+  std::vector<T*> xi, chi;
+  T *rho = nullptr, *w = nullptr, *t1 = nullptr, *lc = nullptr, *lv = nullptr;
+  double *eta = nullptr, *psi = nullptr, *r64 = nullptr, *t64 = nullptr, *c64 = nullptr, *v64 = nullptr;
+  std::vector<void*> owned;
+  int alloc(size_t bytes, void** p) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return dw_cuda_fail(e, "gcr_solve workspace");
+    owned.push_back(*p);
+    return DW_OK;
+  }
+  ~Work() {
+    for (void* p : owned) cudaFree(p);
+  }
+};
+
+template <typename T>
+int solve_one(dw_ctx* c, dfl_ctx* d, const sol_params* p, const double* eta_canon, double* psi_canon,
+              sol_info* info, cudaStream_t s) {
+  constexpr int P = prec_of<T>();
+  const size_t V = c->V;
+  const size_t n = V * 12;              // complex numbers per field
+  const size_t fbT = dw_field_bytes(c, P), fb64 = dw_field_bytes(c, DW_F64);
+  const int nkv = p->nkv;
+  const int Nl = d ? dfl_nlittle(d) : 0;
+  Work<T> W;
+  int rc;
+  W.xi.resize(nkv);
+  W.chi.resize(nkv);
+  for (int k = 0; k < nkv; ++k) {
+    if ((rc = W.alloc(fbT, (void**)&W.xi[k])) || (rc = W.alloc(fbT, (void**)&W.chi[k]))) return rc;
+  }
+  if ((rc = W.alloc(fbT, (void**)&W.rho)) || (rc = W.alloc(fbT, (void**)&W.w)) || (rc = W.alloc(fbT, (void**)&W.t1)) ||
+      (rc = W.alloc(fb64, (void**)&W.eta)) || (rc = W.alloc(fb64, (void**)&W.psi)) ||
+      (rc = W.alloc(fb64, (void**)&W.r64)) || (rc = W.alloc(fb64, (void**)&W.t64)))
+    return rc;
+  if (d) {
+    if ((rc = W.alloc((size_t)Nl * 2 * sizeof(T), (void**)&W.lc)) ||
+        (rc = W.alloc((size_t)Nl * 2 * sizeof(T), (void**)&W.lv)) ||
+        (rc = W.alloc((size_t)Nl * 2 * sizeof(double), (void**)&W.c64)) ||
+        (rc = W.alloc((size_t)Nl * 2 * sizeof(double), (void**)&W.v64)))
+      return rc;
+  }
+  Timers tm;
+  tm.s = s;
+  auto t_start = std::chrono::steady_clock::now();
+  double* dres = c->d_red + 65536 + 4096;
+  double h[2 * 64];
+  if ((rc = dw_pack(c, DW_F64, 1, eta_canon, W.eta, s))) return rc;
+  DW_CUDA(cudaMemsetAsync(W.psi, 0, fb64, s));
+  blas_dot<double>(c, W.eta, W.eta, n, dres, s);
+  if ((rc = read_host(c, dres, 3, h, s))) return rc;
+  const double en = sqrt(h[2]);
+  sol_info inf{};
+  inf.status = DW_ENOTCONV;
+  if (en == 0.0) {
+    inf.status = DW_OK;
+    DW_CUDA(cudaMemsetAsync(psi_canon, 0, V * 24 * sizeof(double), s));
+    if (info) *info = inf;
+    return DW_OK;
+  }
+  auto residual64 = [&]() -> int {   // r64 = eta - D psi, returns via h[2] = |r|^2
+    tm.begin(PH_RESTART);
+    dirac_full<double>(c, W.psi, W.t64, s);
+    DW_CUDA(cudaMemcpyAsync(W.r64, W.eta, fb64, cudaMemcpyDeviceToDevice, s));
+    blas_axpy<double>(W.t64, W.r64, -1.0, 0.0, n, s);
+    blas_dot<double>(c, W.r64, W.r64, n, dres, s);
+    tm.end();
+    return read_host(c, dres, 3, h, s);
+  };
+  std::vector<cd> a(nkv), cc(nkv), bb((size_t)nkv * nkv);
+  double relres = 1.0;
+  const int max_restarts = 10000;
+  for (int restart = 0; restart < max_restarts; ++restart) {
+    if ((rc = residual64())) return rc;
+    if (d) {
+      // deflation correction with the FP64 little solve (A.5: high precision outside the cycles)
+      tm.begin(PH_PROJECT);
+      restrict_(d, W.r64, W.c64, s);
+      tm.end();
+      int it = 0;
+      double rr = 0;
+      tm.begin(PH_LITTLE);
+      rc = lsolve_(d, W.c64, W.v64, p->little_tol_out, p->little_maxit, p->little_nkv, &it, &rr, s);
+      tm.end();
+      if (rc < 0) return rc;
+      inf.little_iterations += it;
+      inf.little_solves += 1;
+      tm.begin(PH_PROJECT);
+      prolong_(d, W.v64, W.psi, 1, s);
+      tm.end();
+      if ((rc = residual64())) return rc;
+    }
+    const double rn = sqrt(h[2]);
+    relres = rn / en;
+    if (rn <= p->tol * en) { inf.status = DW_OK; break; }
+    if (inf.iterations >= p->nmx) break;
+    // ---- one GCR cycle in precision T on rho / rn
+    blas_convert<double, T>(W.r64, W.rho, 1.0 / rn, n, s);
+    const double stop = std::max(p->tol * en / rn, p->mixed ? p->inner_rtol : 0.0);
+    int k = 0;
+    double rk = 1.0;
+    for (; k < nkv && inf.iterations < p->nmx; ++k) {
+      tm.begin(PH_SAP);
+      if ((rc = sap_apply<T>(c, p->ncy, p->nmr, W.rho, W.xi[k], s))) return rc;
+      tm.end();
+      tm.begin(PH_DIRAC);
+      dirac_full<T>(c, W.xi[k], W.chi[k], s);
+      tm.end();
+      if (d) {
+        // chi = P_L w = w - D Phi A^{-1} Phi^+ w, little tolerance adapted to |w| (A.5)
+        tm.begin(PH_PROJECT);
+        blas_dot<T>(c, W.chi[k], W.chi[k], n, dres, s);
+        restrict_(d, W.chi[k], W.lc, s);
+        tm.end();
+        if ((rc = read_host(c, dres, 3, h, s))) return rc;
+        double wn = sqrt(h[2]);
+        double ltol = std::min(p->little_tol_cap, p->little_tol_in / std::max(wn, 1e-300));
+        int it = 0;
+        double rr = 0;
+        tm.begin(PH_LITTLE);
+        rc = lsolve_(d, W.lc, W.lv, ltol, p->little_maxit, p->little_nkv, &it, &rr, s);
+        tm.end();
+        if (rc < 0) return rc;
+        inf.little_iterations += it;
+        inf.little_solves += 1;
+        tm.begin(PH_PROJECT);
+        prolong_(d, W.lv, W.t1, 0, s);
+        dirac_full<T>(c, W.t1, W.w, s);
+        blas_axpy<T>(W.w, W.chi[k], -1.0, 0.0, n, s);
+        tm.end();
+      }
+      tm.begin(PH_ORTH);
+      if (k > 0) {
+        std::vector<const T*> prev(W.chi.begin(), W.chi.begin() + k);
+        blas_multi_dot<T>(c, prev.data(), k, W.chi[k], n, dres, s);
+        if ((rc = read_host(c, dres, 2 * k, h, s))) return rc;
+        for (int j = 0; j < k; ++j) bb[(size_t)j * nkv + k] = cd(h[2 * j], h[2 * j + 1]);
+        blas_multi_axpy<T>(prev.data(), k, h, W.chi[k], n, s);
+      }
+      blas_dot<T>(c, W.chi[k], W.rho, n, dres, s);
+      if ((rc = read_host(c, dres, 3, h, s))) return rc;
+      double ck = sqrt(h[2]);
+      if (!(ck > 0)) { tm.end(); break; }
+      cc[k] = ck;
+      a[k] = cd(h[0], h[1]) / ck;
+      blas_scale<T>(W.chi[k], 1.0 / ck, 0.0, n, s);
+      blas_axpy<T>(W.chi[k], W.rho, -a[k].real(), -a[k].imag(), n, s);
+      blas_dot<T>(c, W.rho, W.rho, n, dres, s);
+      if ((rc = read_host(c, dres, 3, h, s))) return rc;
+      tm.end();
+      rk = sqrt(h[2]);
+      inf.iterations += 1;
+      if (rk <= stop) { ++k; break; }
+    }
+    if (k == 0) break;
+    std::vector<cd> beta(k);
+    for (int j = k - 1; j >= 0; --j) {
+      cd sacc = a[j];
+      for (int i = j + 1; i < k; ++i) sacc -= bb[(size_t)j * nkv + i] * beta[i];
+      beta[j] = sacc / cc[j];
+    }
+    std::vector<double> coef(2 * k);
+    for (int j = 0; j < k; ++j) { coef[2 * j] = beta[j].real(); coef[2 * j + 1] = beta[j].imag(); }
+    std::vector<const T*> xs(W.xi.begin(), W.xi.begin() + k);
+    tm.begin(PH_RESTART);
+    blas_lincomb<T>(xs.data(), k, coef.data(), W.w, n, s);
+    blas_convert<T, double>(W.w, W.t64, rn, n, s);
+    blas_axpy<double>(W.t64, W.psi, 1.0, 0.0, n, s);
+    tm.end();
+    inf.restarts += 1;
+  }
+  if ((rc = dw_unpack(c, DW_F64, 1, W.psi, psi_canon, s))) return rc;
+  DW_CUDA(cudaStreamSynchronize(s));
+  inf.relres = relres;
+  inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  tm.collect(&inf);
+  if (info) *info = inf;
+  return inf.status;
+}
+
+}  // namespace
+
+extern "C" int gcr_solve(dw_ctx* c, dfl_ctx* d, const sol_params* p, int nrhs, const double* eta, double* psi,
+                         sol_info* info, void* stream) {
+  if (!c || !p || !eta || !psi || nrhs < 1 || p->nkv < 1 || p->nkv > 64 || p->nmx < 1 || !(p->tol > 0) ||
+      p->ncy < 0 || p->nmr < 0 || (d && (p->little_nkv < 1 || p->little_maxit < 1))) {
+    dw_set_error("gcr_solve: bad argument");
+    return DW_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int worst = DW_OK;
+  const size_t n = (size_t)c->V * 24;
+  for (int r = 0; r < nrhs; ++r) {
+    int rc = p->mixed ? solve_one<float>(c, d, p, eta + r * n, psi + r * n, info ? info + r : nullptr, s)
+                      : solve_one<double>(c, d, p, eta + r * n, psi + r * n, info ? info + r : nullptr, s);
+    if (rc < 0) return rc;
+    if (rc > worst) worst = rc;
+  }
+  return worst;
+}
