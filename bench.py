@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Seconds per solve of D psi = eta to ||eta - D psi|| <= 1e-10 ||eta||.
+
+Workload (default "24^3x48"): 48 x 24^3 lattice, smeared random SU(3)
+field (U = exp(0.3 i X), 5 APE steps, alpha = 0.5), c_sw = 1, bare mass at
+the near-critical value fixed by the unpreconditioned CG count (> 2000
+iterations), one Gaussian source.  Solver: flexible GCR (restart 16) with
+FP64 restart residuals, right-preconditioned by M_sap (4^4 blocks, ncy = 4,
+nmr = 4, FP32), deflated by Ns = 20 block fields on 4^4 blocks stored in
+BF16 (11 inverse-iteration steps), little operator FP32 with FP64 assembly.
+One step = one solve from psi = 0 with eta and all operator data resident
+in HBM.  The same algorithm in plain FP64 is timed beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 run under torch.distributed.run: every rank solves its own
+right-hand sides (independent replicas, weak scaling, no collective in the
+data path); rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "24^3x48": dict(L=(48, 24, 24, 24), m0=-0.0, csw=1.0, sap_bs=(4, 4, 4, 4), dfl_bs=(4, 4, 4, 4), Ns=20,
+                    n_inv=11, ncy=4, nmr=4, nkv=16, tol=1e-10, gauge_seed=1, source_seed=2, start_seed=3),
+    "8^4": dict(L=(8, 8, 8, 8), m0=-0.2, csw=1.0, sap_bs=(4, 4, 4, 4), dfl_bs=(4, 4, 4, 4), Ns=8,
+                n_inv=11, ncy=4, nmr=4, nkv=16, tol=1e-10, gauge_seed=1, source_seed=2, start_seed=3),
+}
+# Mass of the 24^3x48 workload: near-critical value chosen with cgnr_solve so that the
+# unpreconditioned CG needs more than 2000 iterations (record in the design doc).
+MASS_FILE = os.path.join(ROOT, "paper_0706_2298_gb300", "workload_masses.json")
+
+
+def load_masses():
+    if os.path.exists(MASS_FILE):
+        with open(MASS_FILE) as f:
+            for k, v in json.load(f).items():
+                if k in WORKLOADS:
+                    WORKLOADS[k]["m0"] = v["m0"]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        dev = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"],
+                                 parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_d_time(U, L, m0, csw, reps=2):
+    """FP64 oracle D application time at the workload size (bounded CPU sample)."""
+    import numpy as np
+    from oracle.dirac import WilsonClover
+    from paper_0706_2298_gb300 import synth
+    D = WilsonClover(L, U, m0, csw)
+    psi = synth.gaussian_source(L, 99).numpy()
+    D.apply(psi)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        D.apply(psi)
+    return (time.perf_counter() - t0) / reps
+
+
+def d_equivalents(iterations, ncy, nmr):
+    """D-application equivalents of a DFL+SAP+GCR solve: per GCR step one M_sap
+    (ncy cycles, each colour pass nmr+2 half-lattice block operator applications
+    -> ncy*(nmr+2) full applications), D xi and the D Phi v of P_L."""
+    return iterations * (ncy * (nmr + 2) + 2)
+
+
+def run_reference(args, wl, rank):
+    import numpy as np
+    from paper_0706_2298_gb300 import synth
+    if rank != 0:
+        return
+    L = wl["L"]
+    U = synth.random_gauge(L, wl["gauge_seed"]).numpy()
+    n_it = wl.get("ref_iterations", 40)
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        pass
+    t_steps = []
+    from oracle.dirac import WilsonClover
+    D = WilsonClover(L, U, wl["m0"], wl["csw"])
+    psi = synth.gaussian_source(L, 99).numpy()
+    D.apply(psi)
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        D.apply(psi)
+        t_steps.append(time.perf_counter() - t0)
+    t_d = statistics.median(t_steps)
+    neq = d_equivalents(n_it, wl["ncy"], wl["nmr"])
+    val = t_d * neq
+    line = {"impl": "reference", "metric": "s/solve to rel. residual 1e-10 (DFL+SAP+GCR)", "value": val,
+            "unit": "s/solve", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_d, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "L": list(L), "m0": wl["m0"]},
+            "cpu_baseline": {"value": val, "unit": "s/solve", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} FP64 oracle D applications at {args.workload} "
+                                       f"({t_d:.3f} s each) x {neq} D-equivalents of a solve with "
+                                       f"{n_it} GCR steps"},
+            "e2e": {"value": val, "unit": "s/solve", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="24^3x48", choices=list(WORKLOADS))
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison solves")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    args = ap.parse_args()
+    load_masses()
+    wl = WORKLOADS[args.workload]
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, wl, rank)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    import __graft_entry__ as ge
+    if rank == 0:
+        ge.build()
+    if world > 1:
+        dist.barrier()
+    from paper_0706_2298_gb300 import dwsolve as dw
+    from paper_0706_2298_gb300 import synth
+
+    L = wl["L"]
+    V = synth.volume(L)
+    # ---- inputs (seeded, synthetic); the smearing runs on the GPU, draws are on the CPU generator
+    U = synth.random_gauge(L, wl["gauge_seed"], device="cuda").cpu()
+    ctx = dw.dw_create(L, wl["m0"], wl["csw"], U, wl["sap_bs"])
+    eta_h = synth.gaussian_source(L, wl["source_seed"] + 1000 * rank)
+    eta = eta_h.cuda()
+    start = synth.start_fields(L, wl["Ns"], wl["start_seed"]).cuda()
+    psi = torch.empty_like(eta)
+
+    t0 = time.perf_counter()
+    dfl = dw.deflation_build(ctx, wl["dfl_bs"], wl["Ns"], wl["n_inv"], wl["ncy"], wl["nmr"], start,
+                             basis_prec=dw.DW_BF16, iter_prec=dw.DW_F32)
+    t_build = time.perf_counter() - t0
+    p_mixed = dw.sol_params(tol=wl["tol"], nkv=wl["nkv"], ncy=wl["ncy"], nmr=wl["nmr"], mixed=1)
+
+    def solve():
+        rc, infos = dw.gcr_solve(ctx, dfl, p_mixed, 1, eta, psi)
+        if rc != dw.DW_OK:
+            raise RuntimeError(f"solve did not converge: {infos[0].as_dict()}")
+        return infos[0]
+
+    for _ in range(max(args.warmup, 0)):
+        solve()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_r{rank}.csv") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_r{rank}.csv")
+    clocks.start()
+    n0 = dw.dw_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    infos = [solve() for _ in range(args.steps)]
+    ev1.record()
+    torch.cuda.synchronize()
+    launches = dw.dw_launch_count() - n0
+    t_ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+        dist.barrier()
+    clk = clocks.stop()
+    ms_per_step = t_ms / args.steps
+    value = (t_ms / 1e3) / (args.steps * world)
+    iters = statistics.median([i.iterations for i in infos])
+
+    # ---- roofline of the dominant kernel (Schwarz block kernel): algorithmic bytes per launch / event time
+    hbm, peak_kind = peaks()
+    t_sap = sum(i.t_sap for i in infos)
+    n_sap_launch = sum(i.iterations for i in infos) * 2 * wl["ncy"]
+    sap_launch_s = t_sap / max(n_sap_launch, 1)
+    # per site processed (FP32): links 4 x 12 reals, clover (A or A^-1) 72 reals, r in/out, delta out, xi in/out
+    sap_bytes = (V // 2) * 4 * (48 + 72 + 24 * 5)
+    roof = {"kernel": "sap_block_kernel<float,128>", "bound": "hbm", "achieved": sap_bytes / sap_launch_s / 1e9,
+            "peak": hbm, "unit": "GB/s", "frac": sap_bytes / sap_launch_s / 1e9 / hbm, "traffic": None,
+            "peak_kind": peak_kind, "launch_us": sap_launch_s * 1e6, "algorithmic_bytes_per_launch": sap_bytes}
+
+    # ---- D_w bandwidth: FP32 and FP64 applications, L2 flushed before each timed launch
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    dirac = {}
+    for prec, name, rb in ((dw.DW_F32, "f32", 4), (dw.DW_F64, "f64", 8)):
+        x = ctx.empty_field(prec)
+        y = ctx.empty_field(prec)
+        dw.dw_pack(ctx, prec, 1, eta, x)
+        ts = []
+        for it in range(13):
+            flush.fill_(float(it))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            dw.dw_apply(ctx, prec, dw.DW_OP_FULL, 1, x, y)
+            b.record()
+            torch.cuda.synchronize()
+            if it >= 3:
+                ts.append(a.elapsed_time(b) / 1e3)
+        t = statistics.median(ts)
+        algo = V * rb * (24 + 24 + 4 * 18 + 72)      # psi in + out, 4 links (18 reals), clover 72 reals
+        dirac[name] = {"us": t * 1e6, "gbs": algo / t / 1e9, "frac_of_measured": algo / t / 1e9 / hbm,
+                       "frac_of_8tbs": algo / t / 8e12, "algorithmic_bytes": algo}
+        del x, y
+    del flush
+
+    # ---- plain FP64 path (same algorithm, FP64 everywhere, FP64 basis)
+    plain = None
+    if not args.no_plain:
+        dfl64 = dw.deflation_build(ctx, wl["dfl_bs"], wl["Ns"], wl["n_inv"], wl["ncy"], wl["nmr"], start,
+                                   basis_prec=dw.DW_F64, iter_prec=dw.DW_F64)
+        p64 = dw.sol_params(tol=wl["tol"], nkv=wl["nkv"], ncy=wl["ncy"], nmr=wl["nmr"], mixed=0)
+        psi64 = torch.empty_like(eta)
+        rc, inf64 = dw.gcr_solve(ctx, dfl64, p64, 1, eta, psi64)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        n_plain = max(1, min(args.steps, 3))
+        for _ in range(n_plain):
+            rc, inf64 = dw.gcr_solve(ctx, dfl64, p64, 1, eta, psi64)
+        b.record()
+        torch.cuda.synchronize()
+        plain = {"s_per_solve": a.elapsed_time(b) / 1e3 / n_plain, "iterations": inf64[0].iterations,
+                 "relres": inf64[0].relres, "converged": rc == dw.DW_OK}
+        del dfl64
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    eta_pin = eta_h.pin_memory()
+    psi_pin = torch.empty_like(eta_h).pin_memory()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        eta.copy_(eta_pin, non_blocking=True)
+        rc, _ = dw.gcr_solve(ctx, dfl, p_mixed, 1, eta, psi)
+        psi_pin.copy_(psi, non_blocking=True)
+    b.record()
+    torch.cuda.synchronize()
+    e2e = {"value": a.elapsed_time(b) / 1e3 / args.steps, "unit": "s/solve",
+           "h2d_bytes_per_step": eta_h.numel() * 16, "d2h_bytes_per_step": eta_h.numel() * 16}
+
+    # ---- CPU oracle sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import torch as _t
+        t_d = oracle_d_time(U.numpy(), L, wl["m0"], wl["csw"])
+        neq = d_equivalents(iters, wl["ncy"], wl["nmr"])
+        cpu = {"value": t_d * neq, "unit": "s/solve", "cores": 1, "kind": "oracle",
+               "sample": f"2 FP64 oracle D applications at {args.workload} ({t_d:.2f} s each, numpy, 1 thread) "
+                         f"x {neq} D-equivalents of this solve ({iters} GCR steps x (ncy*(nmr+2)+2))"}
+
+    if rank == 0:
+        line = {"metric": "s/solve to rel. residual 1e-10 (DFL+SAP+GCR, mixed precision) vs plain FP64 path",
+                "value": value, "unit": "s/solve", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+bf16 (FP64 restarts)", "data": "synthetic",
+                "config": {"workload": args.workload, "L": list(L), "m0": wl["m0"], "csw": wl["csw"],
+                           "sap_bs": list(wl["sap_bs"]), "dfl_bs": list(wl["dfl_bs"]), "Ns": wl["Ns"],
+                           "n_inv": wl["n_inv"], "nkv": wl["nkv"], "ncy": wl["ncy"], "nmr": wl["nmr"],
+                           "tol": wl["tol"], "l2": "inputs larger than L2 (solve working set > 2 GB)",
+                           "parallelism": f"replicas x{world}"},
+                "gcr_iterations": iters, "relres": max(i.relres for i in infos),
+                "little_iterations_per_solve": statistics.median([i.little_iterations for i in infos]),
+                "phase_s": {k: statistics.median([getattr(i, k) for i in infos])
+                            for k in ("t_sap", "t_dirac", "t_project", "t_little", "t_orth", "t_restart")},
+                "dfl_build_s": t_build, "plain_fp64": plain,
+                "speedup_vs_plain_fp64": (plain["s_per_solve"] / value) if plain else None,
+                "dirac": dirac, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -72,6 +72,10 @@ typedef struct {
 
 /* Last error message of the calling thread (static storage, never NULL). */
 const char* dw_last_error(void);
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all contexts); callers difference two readings to count the launches of
+ * a region. */
+long long dw_launch_count(void);
 
 /* Create an operator context from host links (canonical layout, FP64).
  * Builds the clover term F, A(x) = (4+m0) + c_sw (i/4) sigma F and its
@@ -184,6 +188,14 @@ typedef struct {
  * info: nrhs entries (may be NULL).  Synchronous. */
 int gcr_solve(dw_ctx* ctx, dfl_ctx* d, const sol_params* p, int nrhs, const double* eta_dev,
               double* psi_dev, sol_info* info, void* stream);
+
+/* Conjugate gradient on the normal equations D^+ D psi = D^+ eta, FP64,
+ * unpreconditioned (the plain iterative method against which the paper's
+ * near-critical masses are characterised).  Stops at
+ * ||eta - D psi|| <= tol ||eta|| or after maxit iterations (DW_ENOTCONV).
+ * eta, psi: canonical complex128[V][4][3] on the device.  Synchronous. */
+int cgnr_solve(dw_ctx* ctx, double tol, int maxit, const double* eta_dev, double* psi_dev, int* iters,
+               double* relres, void* stream);
 
 #ifdef __cplusplus
 }

@@ -114,6 +114,19 @@ __global__ void convert_kernel(const Tin* __restrict__ x, Tout* __restrict__ y, 
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x)
     y[i] = (Tout)((double)x[i] * s);
 }
+// packed-field precision change: the unit layout differs between FP32 (2 complex per
+// 16-byte unit) and FP64 (1 complex per unit), so convert site by site
+template <typename Tin, typename Tout>
+__global__ void field_convert_kernel(const Tin* __restrict__ x, Tout* __restrict__ y, double s, size_t V) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V; i += (size_t)gridDim.x * blockDim.x) {
+    cplx<Tin> a[12];
+    cplx<Tout> b[12];
+    load_site<Tin, 12>(x, V, i, a);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) b[k] = {(Tout)((double)a[k].re * s), (Tout)((double)a[k].im * s)};
+    store_site<Tout, 12>(y, V, i, b);
+  }
+}
 template <typename T>
 struct Coefs {
   double c[2 * MAXK];
@@ -144,13 +157,13 @@ inline unsigned ew_grid(size_t n) {
 template <typename T>
 int blas_dot(dw_ctx* c, const T* a, const T* b, size_t n, double* out3, cudaStream_t s) {
   // out3 (device): re, im of (a, b) and |a|^2
-  dot_kernel<T><<<RGRID, RB, 0, s>>>(a, b, n, c->d_red, c->d_count, out3);
+  dot_kernel<T><<<RGRID, RB, 0, s>>>(a, b, n, c->d_red, c->d_count, out3); dw_note_launch();
   return DW_OK;
 }
 
 template <typename T, int K>
 static void launch_md(dw_ctx* c, const Ptrs<T, MAXK>& p, const T* b, size_t n, double* out, cudaStream_t s) {
-  multi_dot_kernel<T, K><<<RGRID, RB, 0, s>>>(p, b, n, c->d_red, c->d_count, out);
+  multi_dot_kernel<T, K><<<RGRID, RB, 0, s>>>(p, b, n, c->d_red, c->d_count, out); dw_note_launch();
 }
 
 template <typename T>
@@ -171,24 +184,29 @@ int blas_multi_dot(dw_ctx* c, const T* const* vs, int k, const T* b, size_t n, d
 
 template <typename T>
 void blas_axpy(const T* x, T* y, double ar, double ai, size_t n, cudaStream_t s) {
-  axpy_kernel<T><<<ew_grid(n), 256, 0, s>>>(x, y, (T)ar, (T)ai, n);
+  axpy_kernel<T><<<ew_grid(n), 256, 0, s>>>(x, y, (T)ar, (T)ai, n); dw_note_launch();
 }
 template <typename T>
 void blas_xpby(const T* x, T* y, double br, double bi, size_t n, cudaStream_t s) {
-  xpby_kernel<T><<<ew_grid(n), 256, 0, s>>>(x, y, (T)br, (T)bi, n);
+  xpby_kernel<T><<<ew_grid(n), 256, 0, s>>>(x, y, (T)br, (T)bi, n); dw_note_launch();
 }
 template <typename T>
 void blas_scale(T* x, double ar, double ai, size_t n, cudaStream_t s) {
-  scale_kernel<T><<<ew_grid(n), 256, 0, s>>>(x, (T)ar, (T)ai, n);
+  scale_kernel<T><<<ew_grid(n), 256, 0, s>>>(x, (T)ar, (T)ai, n); dw_note_launch();
 }
 template <typename Tin, typename Tout>
 void blas_convert(const Tin* x, Tout* y, double scale, size_t n, cudaStream_t s) {
-  convert_kernel<Tin, Tout><<<ew_grid(2 * n), 256, 0, s>>>(x, y, scale, 2 * n);
+  convert_kernel<Tin, Tout><<<ew_grid(2 * n), 256, 0, s>>>(x, y, scale, 2 * n); dw_note_launch();
+}
+
+template <typename Tin, typename Tout>
+void field_convert(const Tin* x, Tout* y, double scale, size_t V, cudaStream_t s) {
+  field_convert_kernel<Tin, Tout><<<ew_grid(V), 256, 0, s>>>(x, y, scale, V); dw_note_launch();
 }
 
 template <typename T, int K>
 static void launch_ma(const Ptrs<T, MAXK>& p, const Coefs<T>& cf, T* y, size_t n, int mode, cudaStream_t s) {
-  multi_axpy_kernel<T, K><<<ew_grid(n), 256, 0, s>>>(p, cf, y, n, mode);
+  multi_axpy_kernel<T, K><<<ew_grid(n), 256, 0, s>>>(p, cf, y, n, mode); dw_note_launch();
 }
 template <typename T>
 static void multi_axpy_impl(const T* const* vs, int k, const double* coef, T* y, size_t n, int mode,
@@ -238,3 +256,7 @@ template void blas_convert<double, float>(const double*, float*, double, size_t,
 template void blas_convert<float, double>(const float*, double*, double, size_t, cudaStream_t);
 template void blas_convert<double, double>(const double*, double*, double, size_t, cudaStream_t);
 template void blas_convert<float, float>(const float*, float*, double, size_t, cudaStream_t);
+template void field_convert<double, float>(const double*, float*, double, size_t, cudaStream_t);
+template void field_convert<float, double>(const float*, double*, double, size_t, cudaStream_t);
+template void field_convert<double, double>(const double*, double*, double, size_t, cudaStream_t);
+template void field_convert<float, float>(const float*, float*, double, size_t, cudaStream_t);

@@ -272,6 +272,9 @@ struct dw_ctx {
   double* h_red = nullptr;                // pinned host mirror
 };
 
+// kernel launch counter (process-wide, all devices) ---------------------------
+void dw_note_launch();
+
 // error handling ------------------------------------------------------------
 void dw_set_error(const std::string& msg);
 int dw_cuda_fail(cudaError_t e, const char* what);
@@ -294,8 +297,12 @@ template <typename T> void blas_axpy(const T* x, T* y, double ar, double ai, siz
 // y = x + b*y  (complex b)
 template <typename T> void blas_xpby(const T* x, T* y, double br, double bi, size_t n_cplx, cudaStream_t s);
 template <typename T> void blas_scale(T* x, double ar, double ai, size_t n_cplx, cudaStream_t s);
+// flat complex arrays (little vectors, matrices) only -- not packed fields of mixed precision
 template <typename Tin, typename Tout> void blas_convert(const Tin* x, Tout* y, double scale, size_t n_cplx,
                                                         cudaStream_t s);
+// packed fields of V sites: y = scale * x with a change of precision (layouts differ per precision)
+template <typename Tin, typename Tout> void field_convert(const Tin* x, Tout* y, double scale, size_t V,
+                                                         cudaStream_t s);
 // y -= sum_j coef[j] * vs[j]  (coef: host array of k complex)
 template <typename T> void blas_multi_axpy(const T* const* vs, int k, const double* coef, T* y, size_t n_cplx,
                                            cudaStream_t s);

@@ -16,8 +16,11 @@
 #include <chrono>
 #include <cmath>
 #include <complex>
+#include <cooperative_groups.h>
 
 #include "dw_common.cuh"
+
+namespace cg = cooperative_groups;
 
 using cd = std::complex<double>;
 
@@ -38,6 +41,8 @@ struct dfl_ctx {
   uint4* basis16 = nullptr;
   // little operator
   double* B64 = nullptr;                 // [Nb][9][Ns][Ns] column-major complex
+  float* B32 = nullptr;                  // FP32 copy
+  void* fw[2] = {nullptr, nullptr};      // full-system fallback work (A.2)
   double* Binv64 = nullptr; float* Binv32 = nullptr;   // [Nb][Ns][Ns]
   double* M64 = nullptr; float* M32 = nullptr;         // [Nb][8][Ns][Ns]  B_LL^{-1} B_{L,nb(L,d)}
   bool illcond = false;
@@ -47,6 +52,10 @@ struct dfl_ctx {
   double* g64 = nullptr; float* g32 = nullptr;         // [Ns][Ne*Ns]
   double* Bg64 = nullptr; float* Bg32 = nullptr;       // B^ g
   std::vector<cd> Atil_inv;                            // Ns x Ns row-major
+  double* Ainv64 = nullptr; float* Ainv32 = nullptr;   // device copies of A~^{-1}
+  int coop_grid = 0;                                   // CTAs of the cooperative little solver (0: not possible)
+  double* coop_partial = nullptr;                      // [coop_grid][64]
+  double* coop_out = nullptr;                          // iterations, relative residual
   // work vectors (little GCR)
   void* lw[2] = {nullptr, nullptr};                    // per precision
   size_t lw_count = 0;
@@ -537,6 +546,308 @@ inline unsigned warps_grid(int n, int threads = 128) { return (unsigned)((n * 32
 
 }  // namespace
 
+// ------------------------------------------------------------------ cooperative little GCR (A.2-A.4)
+// The whole even-odd, globally deflated little GCR in one persistent kernel:
+// grid-wide barriers replace the host round trips of the host-driven loop.
+// Reductions: per-thread partials -> per-CTA sums in shared memory -> one
+// partial per CTA in global memory -> after the barrier every CTA adds the
+// partials in CTA order (identical, deterministic values in every CTA).
+constexpr int COOP_THREADS = 256;
+constexpr int COOP_NV = 64;
+constexpr int COOP_NKV = 24;
+
+template <typename T>
+struct CoopArgs {
+  int Ne, No, Ns, nkv, maxit, a3;
+  const int *list_e, *list_o, *lnb_e, *lnb_o;
+  const T *M, *g, *Bg, *Ainv, *b;
+  T* v;
+  T* work;            // (2 nkv + 4) vectors of Ne*Ns complex
+  double* partial;    // [2][gridDim][COOP_NV]
+  double* out;        // [0] iterations, [1] relative residual
+  double tol;
+};
+
+struct CoopShared {
+  double ws[COOP_THREADS / 32][COOP_NV];
+  double res[COOP_NV];
+  double a[2 * COOP_NKV], c[COOP_NKV], beta[2 * COOP_NKV];
+  double bb[COOP_NKV][2 * COOP_NKV];
+  double z[2 * 32];
+  int phase;
+};
+
+// sum nv per-thread values over the grid; result in sh.res (all CTAs)
+DW_D void coop_reduce(cg::grid_group& grid, CoopShared& sh, double* acc, int nv, double* partial_base) {
+  // two partial buffers used alternately: a CTA that runs ahead into the next reduction
+  // cannot overwrite partials another CTA is still adding up
+  double* partial = partial_base + (size_t)(sh.phase & 1) * gridDim.x * COOP_NV;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int j = 0; j < nv; ++j) {
+    double x = acc[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) sh.ws[w][j] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double x = 0;
+    for (int q = 0; q < COOP_THREADS / 32; ++q) x += sh.ws[q][threadIdx.x];
+    partial[blockIdx.x * COOP_NV + threadIdx.x] = x;
+  }
+  grid.sync();
+  if (threadIdx.x < nv) {
+    double x = 0;
+    for (unsigned q = 0; q < gridDim.x; ++q) x += partial[q * COOP_NV + threadIdx.x];
+    sh.res[threadIdx.x] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sh.phase += 1;
+  __syncthreads();
+}
+
+// out[r] = base[r] - sum_d M[list[r]][d] src[lnb[r][d]]  (warp per block row; base may be null)
+template <typename T>
+DW_D void coop_hop(int nrow, int Ns, const int* list, const int* lnb, const T* M, const cplx<T>* src,
+                   const cplx<T>* base, cplx<T>* out) {
+  const int lane = threadIdx.x & 31;
+  const int nw = gridDim.x * (COOP_THREADS / 32);
+  const cplx<T>* Mc = reinterpret_cast<const cplx<T>*>(M);
+  for (int r = blockIdx.x * (COOP_THREADS / 32) + (threadIdx.x >> 5); r < nrow; r += nw) {
+    const int L = list[r];
+    cplx<T> acc = {T(0), T(0)};
+    for (int d = 0; d < 8; ++d) {
+      const int j = lnb[r * 8 + d];
+      const cplx<T>* m = Mc + ((size_t)L * 8 + d) * Ns * Ns;
+      const cplx<T>* sv = src + (size_t)j * Ns;
+      for (int col = 0; col < Ns; ++col) {
+        cplx<T> x = sv[col];
+        if (lane < Ns) acc += m[(size_t)col * Ns + lane] * x;
+      }
+    }
+    if (lane < Ns) {
+      cplx<T> bse = base ? base[(size_t)r * Ns + lane] : cplx<T>{T(0), T(0)};
+      out[(size_t)r * Ns + lane] = bse - acc;
+    }
+  }
+}
+
+// y = B^ x = x - M_eo (M_oe x); ends with a grid barrier
+template <typename T>
+DW_D void coop_bhat(cg::grid_group& grid, const CoopArgs<T>& a, const cplx<T>* x, cplx<T>* tmpo, cplx<T>* y) {
+  // tmpo = -M_oe x ; y = x + M_eo tmpo... written as y = x - M_eo(M_oe x) via two signed hops
+  coop_hop<T>(a.No, a.Ns, a.list_o, a.lnb_o, a.M, x, nullptr, tmpo);     // tmpo = -M_oe x
+  grid.sync();
+  // y = x - M_eo (-tmpo) = x + M_eo tmpo : use base = x and negate inside by hopping on tmpo, then fix sign
+  {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (COOP_THREADS / 32);
+    const cplx<T>* Mc = reinterpret_cast<const cplx<T>*>(a.M);
+    for (int r = blockIdx.x * (COOP_THREADS / 32) + (threadIdx.x >> 5); r < a.Ne; r += nw) {
+      const int L = a.list_e[r];
+      cplx<T> acc = {T(0), T(0)};
+      for (int d = 0; d < 8; ++d) {
+        const int j = a.lnb_e[r * 8 + d];
+        const cplx<T>* m = Mc + ((size_t)L * 8 + d) * a.Ns * a.Ns;
+        const cplx<T>* sv = tmpo + (size_t)j * a.Ns;
+        for (int col = 0; col < a.Ns; ++col) {
+          cplx<T> xv = sv[col];
+          if (lane < a.Ns) acc += m[(size_t)col * a.Ns + lane] * xv;
+        }
+      }
+      if (lane < a.Ns) y[(size_t)r * a.Ns + lane] = x[(size_t)r * a.Ns + lane] + acc;
+    }
+  }
+  grid.sync();
+}
+
+// u -= Bg A~^{-1} g^+ u  (P~_L, in place; elementwise part by the owning thread, no trailing barrier)
+template <typename T>
+DW_D void coop_PL(cg::grid_group& grid, CoopShared& sh, const CoopArgs<T>& a, cplx<T>* u, double* acc,
+                  const cplx<T>* gsrc, const cplx<T>* bgsrc, bool subtract_from_u) {
+  const size_t n = (size_t)a.Ne * a.Ns;
+  const size_t tid = blockIdx.x * (size_t)COOP_THREADS + threadIdx.x, nth = (size_t)gridDim.x * COOP_THREADS;
+  const int Ns = a.Ns;
+  for (int j = 0; j < 2 * Ns; ++j) acc[j] = 0;
+  for (size_t i = tid; i < n; i += nth) {
+    cplx<T> x = u[i];
+    for (int l = 0; l < Ns; ++l) {
+      cplx<T> gl = gsrc[(size_t)l * n + i];
+      acc[2 * l] += (double)gl.re * x.re + (double)gl.im * x.im;
+      acc[2 * l + 1] += (double)gl.re * x.im - (double)gl.im * x.re;
+    }
+  }
+  coop_reduce(grid, sh, acc, 2 * Ns, a.partial);
+  if (threadIdx.x < Ns) {          // z = A~^{-1} y
+    const cplx<T>* Ai = reinterpret_cast<const cplx<T>*>(a.Ainv);
+    double zr = 0, zi = 0;
+    for (int q = 0; q < Ns; ++q) {
+      cplx<T> m = Ai[threadIdx.x * Ns + q];
+      double yr = sh.res[2 * q], yi = sh.res[2 * q + 1];
+      zr += (double)m.re * yr - (double)m.im * yi;
+      zi += (double)m.re * yi + (double)m.im * yr;
+    }
+    sh.z[2 * threadIdx.x] = zr;
+    sh.z[2 * threadIdx.x + 1] = zi;
+  }
+  __syncthreads();
+  for (size_t i = tid; i < n; i += nth) {
+    cplx<T> x = u[i];
+    for (int l = 0; l < Ns; ++l) {
+      cplx<T> zl = {(T)sh.z[2 * l], (T)sh.z[2 * l + 1]};
+      if (subtract_from_u) x -= zl * bgsrc[(size_t)l * n + i];
+      else x += zl * bgsrc[(size_t)l * n + i];
+    }
+    u[i] = x;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(COOP_THREADS) little_gcr_coop_kernel(CoopArgs<T> a) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ CoopShared sh;
+  if (threadIdx.x == 0) sh.phase = 0;
+  __syncthreads();
+  double acc[COOP_NV];
+  const size_t n = (size_t)a.Ne * a.Ns;
+  const size_t tid = blockIdx.x * (size_t)COOP_THREADS + threadIdx.x, nth = (size_t)gridDim.x * COOP_THREADS;
+  const int nkv = a.nkv;
+  cplx<T>* W = reinterpret_cast<cplx<T>*>(a.work);
+  cplx<T>* rho = W + (size_t)2 * nkv * n;
+  cplx<T>* tmpo = rho + n;
+  cplx<T>* t = tmpo + n;
+  cplx<T>* rhsd = t + n;
+  const cplx<T>* b = reinterpret_cast<const cplx<T>*>(a.b);
+  const cplx<T>* g = reinterpret_cast<const cplx<T>*>(a.g);
+  const cplx<T>* Bg = reinterpret_cast<const cplx<T>*>(a.Bg);
+  cplx<T>* v = reinterpret_cast<cplx<T>*>(a.v);
+  auto chi = [&](int k) { return W + (size_t)k * n; };
+  auto xi = [&](int k) { return W + (size_t)(nkv + k) * n; };
+
+  // rhsd = P~_L b, rho = rhsd, v = 0
+  for (size_t i = tid; i < n; i += nth) rhsd[i] = b[i];
+  if (a.a3) coop_PL<T>(grid, sh, a, rhsd, acc, g, Bg, true);
+  acc[0] = 0;
+  for (size_t i = tid; i < n; i += nth) {
+    cplx<T> x = rhsd[i];
+    rho[i] = x;
+    v[i] = {T(0), T(0)};
+    acc[0] += (double)x.re * x.re + (double)x.im * x.im;
+  }
+  coop_reduce(grid, sh, acc, 1, a.partial);
+  const double bn = sqrt(sh.res[0]);
+  double rn = bn;
+  int total = 0;
+  while (bn > 0 && rn > a.tol * bn && total < a.maxit) {
+    int k = 0;
+    for (; k < nkv && total < a.maxit; ++k) {
+      cplx<T>* ck = chi(k);
+      cplx<T>* xk = xi(k);
+      for (size_t i = tid; i < n; i += nth) xk[i] = rho[i];
+      grid.sync();
+      coop_bhat<T>(grid, a, xk, tmpo, ck);
+      if (a.a3) coop_PL<T>(grid, sh, a, ck, acc, g, Bg, true);
+      if (k > 0) {
+        for (int j = 0; j < 2 * k; ++j) acc[j] = 0;
+        for (size_t i = tid; i < n; i += nth) {
+          cplx<T> y = ck[i];
+          for (int j = 0; j < k; ++j) {
+            cplx<T> x = chi(j)[i];
+            acc[2 * j] += (double)x.re * y.re + (double)x.im * y.im;
+            acc[2 * j + 1] += (double)x.re * y.im - (double)x.im * y.re;
+          }
+        }
+        coop_reduce(grid, sh, acc, 2 * k, a.partial);
+        if (threadIdx.x < 2 * k) sh.bb[threadIdx.x >> 1][2 * k + (threadIdx.x & 1)] = sh.res[threadIdx.x];
+        __syncthreads();
+        for (size_t i = tid; i < n; i += nth) {
+          cplx<T> y = ck[i];
+          for (int j = 0; j < k; ++j) {
+            cplx<T> bj = {(T)sh.bb[j][2 * k], (T)sh.bb[j][2 * k + 1]};
+            y -= bj * chi(j)[i];
+          }
+          ck[i] = y;
+        }
+      }
+      acc[0] = acc[1] = acc[2] = 0;
+      for (size_t i = tid; i < n; i += nth) {
+        cplx<T> x = ck[i], y = rho[i];
+        acc[0] += (double)x.re * y.re + (double)x.im * y.im;
+        acc[1] += (double)x.re * y.im - (double)x.im * y.re;
+        acc[2] += (double)x.re * x.re + (double)x.im * x.im;
+      }
+      coop_reduce(grid, sh, acc, 3, a.partial);
+      const double cn = sqrt(sh.res[2]);
+      if (!(cn > 0)) break;
+      const double ar = sh.res[0] / cn, ai = sh.res[1] / cn;
+      if (threadIdx.x == 0) { sh.c[k] = cn; sh.a[2 * k] = ar; sh.a[2 * k + 1] = ai; }
+      acc[0] = 0;
+      const T inv = (T)(1.0 / cn);
+      const cplx<T> ak = {(T)ar, (T)ai};
+      for (size_t i = tid; i < n; i += nth) {
+        cplx<T> x = inv * ck[i];
+        ck[i] = x;
+        cplx<T> y = rho[i] - ak * x;
+        rho[i] = y;
+        acc[0] += (double)y.re * y.re + (double)y.im * y.im;
+      }
+      coop_reduce(grid, sh, acc, 1, a.partial);
+      rn = sqrt(sh.res[0]);
+      ++total;
+      if (rn <= a.tol * bn) { ++k; break; }
+    }
+    // back substitution (thread 0 of every CTA), v += sum beta_k xi_k
+    if (threadIdx.x == 0) {
+      for (int j = k - 1; j >= 0; --j) {
+        double sr = sh.a[2 * j], si = sh.a[2 * j + 1];
+        for (int i = j + 1; i < k; ++i) {
+          double br = sh.bb[j][2 * i], bi = sh.bb[j][2 * i + 1];
+          sr -= br * sh.beta[2 * i] - bi * sh.beta[2 * i + 1];
+          si -= br * sh.beta[2 * i + 1] + bi * sh.beta[2 * i];
+        }
+        sh.beta[2 * j] = sr / sh.c[j];
+        sh.beta[2 * j + 1] = si / sh.c[j];
+      }
+    }
+    __syncthreads();
+    for (size_t i = tid; i < n; i += nth) {
+      cplx<T> x = v[i];
+      for (int j = 0; j < k; ++j) x += cplx<T>{(T)sh.beta[2 * j], (T)sh.beta[2 * j + 1]} * xi(j)[i];
+      v[i] = x;
+    }
+    grid.sync();
+    if (k == 0) break;
+    // true residual of the deflated system
+    coop_bhat<T>(grid, a, v, tmpo, t);
+    if (a.a3) coop_PL<T>(grid, sh, a, t, acc, g, Bg, true);
+    acc[0] = 0;
+    for (size_t i = tid; i < n; i += nth) {
+      cplx<T> y = rhsd[i] - t[i];
+      rho[i] = y;
+      acc[0] += (double)y.re * y.re + (double)y.im * y.im;
+    }
+    coop_reduce(grid, sh, acc, 1, a.partial);
+    rn = sqrt(sh.res[0]);
+  }
+  if (a.a3) {
+    // v = chi + g A~^{-1} g^+ (b - B^ chi)
+    grid.sync();
+    coop_bhat<T>(grid, a, v, tmpo, t);
+    for (size_t i = tid; i < n; i += nth) t[i] = b[i] - t[i];
+    coop_PL<T>(grid, sh, a, t, acc, g, g, false);   // t += g z  (z from g^+ t); only z is used below
+    // coop_PL updated t, not v: redo the elementwise part on v with the same z
+    for (size_t i = tid; i < n; i += nth) {
+      cplx<T> x = v[i];
+      for (int l = 0; l < a.Ns; ++l) x += cplx<T>{(T)sh.z[2 * l], (T)sh.z[2 * l + 1]} * g[(size_t)l * n + i];
+      v[i] = x;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.out[0] = total;
+    a.out[1] = bn > 0 ? rn / bn : 0.0;
+  }
+}
+
 // ====================================================================== host side
 template <typename T>
 static const T* Mp(dfl_ctx* d);
@@ -559,10 +870,10 @@ template <> const double* Bgp<double>(dfl_ctx* d) { return d->Bg64; }
 template <typename T>
 static void apply_bhat(dfl_ctx* d, const T* ve, T* tmp_o, T* out, cudaStream_t s) {
   little_hop_kernel<T><<<warps_grid(d->No), 128, 0, s>>>(d->No, d->Ns, d->d_list[1], d->d_lnb[1], Mp<T>(d), ve,
-                                                        nullptr, tmp_o);
+                                                        nullptr, tmp_o); dw_note_launch();
   // tmp_o = -M_oe v_e; out = v_e - M_eo(M_oe v_e) = v_e + M_eo tmp_o  ->  use base = v_e and src = -tmp
   little_hop_kernel<T><<<warps_grid(d->Ne), 128, 0, s>>>(d->Ne, d->Ns, d->d_list[0], d->d_lnb[0], Mp<T>(d), tmp_o,
-                                                        nullptr, out);
+                                                        nullptr, out); dw_note_launch();
   // out = -M_eo tmp_o = M_eo M_oe v_e ; final = v_e - out
   blas_xpby<T>(ve, out, -1.0, 0.0, (size_t)d->Ne * d->Ns, s);
 }
@@ -578,7 +889,8 @@ extern "C" void dfl_destroy(dfl_ctx* d) {
   if (!d) return;
   void* ptrs[] = {d->d_sub, d->d_sap2dfl, d->d_bnb, d->d_list[0], d->d_list[1], d->d_lnb[0], d->d_lnb[1],
                   d->basis64, d->basis16, d->B64, d->Binv64, d->Binv32, d->M64, d->M32, d->g64, d->g32,
-                  d->Bg64, d->Bg32, d->lw[0], d->lw[1]};
+                  d->Bg64, d->Bg32, d->lw[0], d->lw[1], d->B32, d->fw[0], d->fw[1], d->Ainv64, d->Ainv32,
+                  d->coop_partial, d->coop_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete d;
@@ -587,14 +899,14 @@ extern "C" void dfl_destroy(dfl_ctx* d) {
 template <typename T>
 static int restrict_t(dfl_ctx* d, const T* psi, T* c, cudaStream_t s) {
   restrict_kernel<T><<<d->Nb, 128, 0, s>>>(d->c->g, d->d_sub, d->nsub, d->Ns, d->basis16 ? nullptr : d->basis64,
-                                            d->basis16, psi, c);
+                                            d->basis16, psi, c); dw_note_launch();
   return DW_OK;
 }
 template <typename T>
 static int prolong_t(dfl_ctx* d, const T* c, T* psi, int mode, cudaStream_t s) {
   unsigned blocks = (unsigned)((d->c->V + 127) / 128);
   prolong_kernel<T><<<blocks, 128, 0, s>>>(d->c->g, d->d_sap2dfl, d->Ns, d->basis16 ? nullptr : d->basis64,
-                                            d->basis16, c, psi, mode);
+                                            d->basis16, c, psi, mode); dw_note_launch();
   return DW_OK;
 }
 int dfl_restrict_f32(dfl_ctx* d, const float* psi, float* c, cudaStream_t s) { return restrict_t(d, psi, c, s); }
@@ -628,7 +940,7 @@ extern "C" int dfl_basis_export(dfl_ctx* d, double* canon, void* stream) {
 }
 extern "C" int little_apply(dfl_ctx* d, const double* v, double* w, void* stream) {
   if (!d || !v || !w || v == w) { dw_set_error("little_apply: bad argument"); return DW_EINVAL; }
-  little_full_kernel<<<warps_grid(d->Nb), 128, 0, (cudaStream_t)stream>>>(d->Nb, d->Ns, d->d_bnb, d->B64, v, w);
+  little_full_kernel<<<warps_grid(d->Nb), 128, 0, (cudaStream_t)stream>>>(d->Nb, d->Ns, d->d_bnb, d->B64, v, w); dw_note_launch();
   DW_CUDA(cudaGetLastError());
   return DW_OK;
 }
@@ -696,36 +1008,27 @@ static int little_coarse_add(dfl_ctx* d, const T* r, T* v, cudaStream_t s) {
   return DW_OK;
 }
 
-// Solve B^ v_e = b_e (deflated by A.3 when available) by restarted GCR.  Returns iterations.
-template <typename T>
-static int little_gcr(dfl_ctx* d, const T* b, T* v, double tol, int maxit, int nkv, int* iters, double* relres,
-                      cudaStream_t s) {
-  const int Ns = d->Ns;
-  const size_t n = (size_t)d->Ne * Ns;
-  T* chi0 = lwork<T>(d, 0);
-  T* xi0 = lwork<T>(d, nkv);
-  T* rho = lwork<T>(d, 2 * nkv);
-  T* tmpo = lwork<T>(d, 2 * nkv + 1);
-  T* rhs = lwork<T>(d, 2 * nkv + 2);
-  T* t = lwork<T>(d, 2 * nkv + 3);
+// Restarted GCR for op(v) = rhs on small (little) vectors of n complex numbers.
+// work: 2*nkv + 3 vectors of n complex.  Stops at ||rhs - op v|| <= tol ||rhs||.
+template <typename T, typename Op>
+static int gcr_small(dw_ctx* c, Op op, const T* rhs, T* v, size_t n, T* work, double tol, int maxit, int nkv,
+                     int* iters, double* relres, cudaStream_t s) {
+  T* chi0 = work;
+  T* xi0 = work + (size_t)nkv * 2 * n;
+  T* rho = work + (size_t)2 * nkv * 2 * n;
+  T* t = rho + 2 * n;
   auto chi = [&](int k) { return chi0 + (size_t)k * 2 * n; };
   auto xi = [&](int k) { return xi0 + (size_t)k * 2 * n; };
-  double* dres = d->c->d_red + 65536;
+  double* dres = c->d_red + 65536;
   std::vector<double> hbuf(2 * (nkv + 2));
-  // rhs = P~_L b
-  DW_CUDA(cudaMemcpyAsync(rhs, b, n * 2 * sizeof(T), cudaMemcpyDeviceToDevice, s));
   int rc;
-  if (d->a3 && (rc = little_PL<T>(d, rhs, s))) return rc;
-  blas_dot<T>(d->c, rhs, rhs, n, dres, s);
-  if ((rc = sync_read(d->c, dres, 3, hbuf.data(), s))) return rc;
+  blas_dot<T>(c, rhs, rhs, n, dres, s);
+  if ((rc = sync_read(c, dres, 3, hbuf.data(), s))) return rc;
   const double bn = sqrt(hbuf[2]);
   DW_CUDA(cudaMemsetAsync(v, 0, n * 2 * sizeof(T), s));
   *iters = 0;
   *relres = 0;
-  if (bn == 0.0) {
-    if (d->a3) little_coarse_add<T>(d, b, v, s);
-    return DW_OK;
-  }
+  if (bn == 0.0) return DW_OK;
   DW_CUDA(cudaMemcpyAsync(rho, rhs, n * 2 * sizeof(T), cudaMemcpyDeviceToDevice, s));
   double rn = bn;
   int total = 0;
@@ -735,35 +1038,28 @@ static int little_gcr(dfl_ctx* d, const T* b, T* v, double tol, int maxit, int n
     int k = 0;
     for (; k < nkv && total < maxit; ++k, ++total) {
       DW_CUDA(cudaMemcpyAsync(xi(k), rho, n * 2 * sizeof(T), cudaMemcpyDeviceToDevice, s));
-      apply_bhat<T>(d, xi(k), tmpo, chi(k), s);
-      if (d->a3 && (rc = little_PL<T>(d, chi(k), s))) return rc;
+      if ((rc = op(xi(k), chi(k)))) return rc;
       if (k > 0) {
         std::vector<const T*> prev(k);
         for (int j = 0; j < k; ++j) prev[j] = chi(j);
-        blas_multi_dot<T>(d->c, prev.data(), k, chi(k), n, dres, s);
-        if ((rc = sync_read(d->c, dres, 2 * k, hbuf.data(), s))) return rc;
-        std::vector<double> coef(2 * k);
-        for (int j = 0; j < k; ++j) {
-          bb[(size_t)j * nkv + k] = cd(hbuf[2 * j], hbuf[2 * j + 1]);
-          coef[2 * j] = hbuf[2 * j];
-          coef[2 * j + 1] = hbuf[2 * j + 1];
-        }
-        blas_multi_axpy<T>(prev.data(), k, coef.data(), chi(k), n, s);
+        blas_multi_dot<T>(c, prev.data(), k, chi(k), n, dres, s);
+        if ((rc = sync_read(c, dres, 2 * k, hbuf.data(), s))) return rc;
+        for (int j = 0; j < k; ++j) bb[(size_t)j * nkv + k] = cd(hbuf[2 * j], hbuf[2 * j + 1]);
+        blas_multi_axpy<T>(prev.data(), k, hbuf.data(), chi(k), n, s);
       }
-      blas_dot<T>(d->c, chi(k), rho, n, dres, s);
-      if ((rc = sync_read(d->c, dres, 3, hbuf.data(), s))) return rc;
+      blas_dot<T>(c, chi(k), rho, n, dres, s);
+      if ((rc = sync_read(c, dres, 3, hbuf.data(), s))) return rc;
       double ck = sqrt(hbuf[2]);
       if (!(ck > 0)) break;
       cc[k] = ck;
       a[k] = cd(hbuf[0], hbuf[1]) / ck;
       blas_scale<T>(chi(k), 1.0 / ck, 0.0, n, s);
       blas_axpy<T>(chi(k), rho, -a[k].real(), -a[k].imag(), n, s);
-      blas_dot<T>(d->c, rho, rho, n, dres, s);
-      if ((rc = sync_read(d->c, dres, 3, hbuf.data(), s))) return rc;
+      blas_dot<T>(c, rho, rho, n, dres, s);
+      if ((rc = sync_read(c, dres, 3, hbuf.data(), s))) return rc;
       rn = sqrt(hbuf[2]);
       if (rn <= tol * bn) { ++k; ++total; break; }
     }
-    // back substitution and update v += sum beta_k xi_k
     std::vector<cd> beta(k);
     for (int j = k - 1; j >= 0; --j) {
       cd sacc = a[j];
@@ -774,30 +1070,88 @@ static int little_gcr(dfl_ctx* d, const T* b, T* v, double tol, int maxit, int n
     std::vector<double> coef(2 * k);
     for (int j = 0; j < k; ++j) { xs[j] = xi(j); coef[2 * j] = -beta[j].real(); coef[2 * j + 1] = -beta[j].imag(); }
     if (k > 0) blas_multi_axpy<T>(xs.data(), k, coef.data(), v, n, s);
-    // true residual of the deflated system: rho = rhs - P~_L B^ v
-    apply_bhat<T>(d, v, tmpo, t, s);
-    if (d->a3 && (rc = little_PL<T>(d, t, s))) return rc;
+    if (k == 0) break;
+    // true residual rho = rhs - op v
+    if ((rc = op(v, t))) return rc;
     DW_CUDA(cudaMemcpyAsync(rho, rhs, n * 2 * sizeof(T), cudaMemcpyDeviceToDevice, s));
     blas_axpy<T>(t, rho, -1.0, 0.0, n, s);
-    blas_dot<T>(d->c, rho, rho, n, dres, s);
-    if ((rc = sync_read(d->c, dres, 3, hbuf.data(), s))) return rc;
+    blas_dot<T>(c, rho, rho, n, dres, s);
+    if ((rc = sync_read(c, dres, 3, hbuf.data(), s))) return rc;
     rn = sqrt(hbuf[2]);
-    if (k == 0) break;
   }
   *iters = total;
   *relres = rn / bn;
-  if (d->a3) {
-    // v = P~_R chi + g A~^{-1} g^+ b = chi + g A~^{-1} g^+ (b - B^ chi)
-    apply_bhat<T>(d, v, tmpo, t, s);
-    DW_CUDA(cudaMemcpyAsync(rho, b, n * 2 * sizeof(T), cudaMemcpyDeviceToDevice, s));
-    blas_axpy<T>(t, rho, -1.0, 0.0, n, s);
-    if ((rc = little_coarse_add<T>(d, rho, v, s))) return rc;
-  }
   return rn <= tol * bn ? DW_OK : DW_ENOTCONV;
 }
 
+template <typename T>
+static const T* Ainvp(dfl_ctx* d);
+template <> const float* Ainvp<float>(dfl_ctx* d) { return d->Ainv32; }
+template <> const double* Ainvp<double>(dfl_ctx* d) { return d->Ainv64; }
+
+static bool coop_enabled() {
+  const char* e = getenv("DW_LITTLE_COOP");
+  return !(e && e[0] == '0');
+}
+
+// the cooperative solver: same algorithm as little_gcr below (GCR on P~_L B^, then the A.3 correction)
+template <typename T>
+static int little_gcr_coop(dfl_ctx* d, const T* b, T* v, double tol, int maxit, int nkv, int* iters,
+                           double* relres, cudaStream_t s) {
+  CoopArgs<T> a;
+  a.Ne = d->Ne; a.No = d->No; a.Ns = d->Ns; a.nkv = nkv; a.maxit = maxit; a.a3 = d->a3 ? 1 : 0;
+  a.list_e = d->d_list[0]; a.list_o = d->d_list[1]; a.lnb_e = d->d_lnb[0]; a.lnb_o = d->d_lnb[1];
+  a.M = Mp<T>(d); a.g = d->a3 ? gp<T>(d) : nullptr; a.Bg = d->a3 ? Bgp<T>(d) : nullptr;
+  a.Ainv = d->a3 ? Ainvp<T>(d) : nullptr; a.b = b; a.v = v;
+  a.work = lwork<T>(d, 0);
+  a.partial = d->coop_partial;
+  a.out = d->coop_out;
+  a.tol = tol;
+  void* args[] = {&a};
+  DW_CUDA(cudaLaunchCooperativeKernel((void*)little_gcr_coop_kernel<T>, d->coop_grid, COOP_THREADS, args, 0, s));
+  dw_note_launch();
+  double h[2];
+  int rc = sync_read(d->c, d->coop_out, 2, h, s);
+  if (rc) return rc;
+  *iters = (int)h[0];
+  *relres = h[1];
+  return h[1] <= tol ? DW_OK : DW_ENOTCONV;
+}
+
+// Solve B^ v_e = b_e, deflated by the global modes (A.3) when available.
+// work: 2*nkv + 4 vectors of Ne*Ns complex.
+template <typename T>
+static int little_gcr(dfl_ctx* d, const T* b, T* v, double tol, int maxit, int nkv, int* iters, double* relres,
+                      cudaStream_t s) {
+  if (d->coop_grid > 0 && nkv <= COOP_NKV && coop_enabled())
+    return little_gcr_coop<T>(d, b, v, tol, maxit, nkv, iters, relres, s);
+  const size_t n = (size_t)d->Ne * d->Ns;
+  T* work = lwork<T>(d, 0);
+  T* tmpo = lwork<T>(d, 2 * nkv + 3);
+  T* rhs = lwork<T>(d, 2 * nkv + 4);
+  T* t = lwork<T>(d, 2 * nkv + 2);     // the generic GCR's scratch slot, free after it returns
+  cudaStream_t st = s;
+  int rc;
+  DW_CUDA(cudaMemcpyAsync(rhs, b, n * 2 * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  if (d->a3 && (rc = little_PL<T>(d, rhs, s))) return rc;
+  auto op = [&](const T* x, T* y) -> int {
+    apply_bhat<T>(d, x, tmpo, y, st);
+    return d->a3 ? little_PL<T>(d, y, st) : DW_OK;
+  };
+  int grc = gcr_small<T>(d->c, op, rhs, v, n, work, tol, maxit, nkv, iters, relres, s);
+  if (grc < 0) return grc;
+  if (d->a3) {
+    // v = P~_R chi + g A~^{-1} g^+ b = chi + g A~^{-1} g^+ (b - B^ chi)
+    apply_bhat<T>(d, v, tmpo, t, s);
+    DW_CUDA(cudaMemcpyAsync(rhs, b, n * 2 * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    blas_axpy<T>(t, rhs, -1.0, 0.0, n, s);
+    if ((rc = little_coarse_add<T>(d, rhs, v, s))) return rc;
+  }
+  return grc;
+}
+
 static int ensure_little_work(dfl_ctx* d, int prec, int nkv) {
-  size_t count = (size_t)2 * nkv + 8;
+  size_t count = (size_t)2 * nkv + 10;
   size_t n = (size_t)d->Ne * d->Ns * 2;
   if (d->lw[prec] && d->lw_count >= count) return DW_OK;
   for (int p = 0; p < 2; ++p)
@@ -808,6 +1162,45 @@ static int ensure_little_work(dfl_ctx* d, int prec, int nkv) {
   return DW_OK;
 }
 
+// Appendix A.2 fallback: an ill-conditioned diagonal block -> GCR on the full little system
+template <typename T>
+static const T* Bp(dfl_ctx* d);
+template <> const float* Bp<float>(dfl_ctx* d) { return d->B32; }
+template <> const double* Bp<double>(dfl_ctx* d) { return d->B64; }
+
+template <typename T>
+__global__ void little_full_t_kernel(int Nb, int Ns, const int* __restrict__ bnb, const T* __restrict__ B,
+                                     const T* __restrict__ v, T* w) {
+  int L = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (L >= Nb) return;
+  const cplx<T>* Bc = reinterpret_cast<const cplx<T>*>(B);
+  const cplx<T>* vc = reinterpret_cast<const cplx<T>*>(v);
+  cplx<T> acc = {T(0), T(0)};
+  for (int part = 0; part < 9; ++part) {
+    int src = part == 0 ? L : bnb[L * 8 + part - 1];
+    const cplx<T>* m = Bc + ((size_t)L * 9 + part) * Ns * Ns;
+    for (int col = 0; col < Ns; ++col) {
+      cplx<T> x = vc[(size_t)src * Ns + col];
+      if (lane < Ns) acc += m[(size_t)col * Ns + lane] * x;
+    }
+  }
+  if (lane < Ns) reinterpret_cast<cplx<T>*>(w)[(size_t)L * Ns + lane] = acc;
+}
+
+template <typename T>
+static int little_full_solve(dfl_ctx* d, const T* w, T* v, double tol, int maxit, int nkv, int* iters,
+                             double* relres, cudaStream_t s) {
+  constexpr int P = prec_of<T>();
+  const size_t n = (size_t)d->N;
+  if (!d->fw[P]) DW_CUDA(cudaMalloc(&d->fw[P], (size_t)(2 * nkv + 3) * n * 2 * sizeof(T)));
+  auto op = [&](const T* x, T* y) -> int {
+    little_full_t_kernel<T><<<warps_grid(d->Nb), 128, 0, s>>>(d->Nb, d->Ns, d->d_bnb, Bp<T>(d), x, y); dw_note_launch();
+    return DW_OK;
+  };
+  return gcr_small<T>(d->c, op, w, v, n, (T*)d->fw[P], tol, maxit, nkv, iters, relres, s);
+}
+
 // Full little solve A v = w (prec T; w, v: [Nb][Ns] complex of T)
 template <typename T>
 static int little_solve_t(dfl_ctx* d, const T* w, T* v, double tol, int maxit, int nkv, int* iters, double* relres,
@@ -816,24 +1209,25 @@ static int little_solve_t(dfl_ctx* d, const T* w, T* v, double tol, int maxit, i
   if (rc) return rc;
   const int Ns = d->Ns;
   size_t n_e = (size_t)d->Ne * Ns, n_o = (size_t)d->No * Ns;
-  T* we = lwork<T>(d, 2 * nkv + 4);
-  T* wo = lwork<T>(d, 2 * nkv + 5);
-  T* yo = lwork<T>(d, 2 * nkv + 6);
-  T* wt = lwork<T>(d, 2 * nkv + 7);
+  if (d->illcond) return little_full_solve<T>(d, w, v, tol, maxit, nkv, iters, relres, s);
+  T* we = lwork<T>(d, 2 * nkv + 5);
+  T* wo = lwork<T>(d, 2 * nkv + 6);
+  T* yo = lwork<T>(d, 2 * nkv + 7);
+  T* wt = lwork<T>(d, 2 * nkv + 8);
   unsigned ge = (unsigned)((n_e + 255) / 256), go = (unsigned)((n_o + 255) / 256);
-  little_gather_kernel<T, T><<<ge, 256, 0, s>>>(d->Ne, Ns, d->d_list[0], w, we);
-  little_gather_kernel<T, T><<<go, 256, 0, s>>>(d->No, Ns, d->d_list[1], w, wo);
+  little_gather_kernel<T, T><<<ge, 256, 0, s>>>(d->Ne, Ns, d->d_list[0], w, we); dw_note_launch();
+  little_gather_kernel<T, T><<<go, 256, 0, s>>>(d->No, Ns, d->d_list[1], w, wo); dw_note_launch();
   // yo = B_oo^{-1} w_o ; wt = B_ee^{-1} w_e - M_eo yo
-  little_bdiag_kernel<T><<<warps_grid(d->No), 128, 0, s>>>(d->No, Ns, d->d_list[1], Binvp<T>(d), wo, yo);
-  little_bdiag_kernel<T><<<warps_grid(d->Ne), 128, 0, s>>>(d->Ne, Ns, d->d_list[0], Binvp<T>(d), we, wt);
-  little_hop_kernel<T><<<warps_grid(d->Ne), 128, 0, s>>>(d->Ne, Ns, d->d_list[0], d->d_lnb[0], Mp<T>(d), yo, wt, we);
+  little_bdiag_kernel<T><<<warps_grid(d->No), 128, 0, s>>>(d->No, Ns, d->d_list[1], Binvp<T>(d), wo, yo); dw_note_launch();
+  little_bdiag_kernel<T><<<warps_grid(d->Ne), 128, 0, s>>>(d->Ne, Ns, d->d_list[0], Binvp<T>(d), we, wt); dw_note_launch();
+  little_hop_kernel<T><<<warps_grid(d->Ne), 128, 0, s>>>(d->Ne, Ns, d->d_list[0], d->d_lnb[0], Mp<T>(d), yo, wt, we); dw_note_launch();
   // we now holds w~_e ; solve B^ v_e = w~_e into wt
   rc = little_gcr<T>(d, we, wt, tol, maxit, nkv, iters, relres, s);
   if (rc < 0) return rc;
   // v_o = yo - M_oe v_e  -> into wo
-  little_hop_kernel<T><<<warps_grid(d->No), 128, 0, s>>>(d->No, Ns, d->d_list[1], d->d_lnb[1], Mp<T>(d), wt, yo, wo);
-  little_scatter_kernel<T, T><<<ge, 256, 0, s>>>(d->Ne, Ns, d->d_list[0], wt, v);
-  little_scatter_kernel<T, T><<<go, 256, 0, s>>>(d->No, Ns, d->d_list[1], wo, v);
+  little_hop_kernel<T><<<warps_grid(d->No), 128, 0, s>>>(d->No, Ns, d->d_list[1], d->d_lnb[1], Mp<T>(d), wt, yo, wo); dw_note_launch();
+  little_scatter_kernel<T, T><<<ge, 256, 0, s>>>(d->Ne, Ns, d->d_list[0], wt, v); dw_note_launch();
+  little_scatter_kernel<T, T><<<go, 256, 0, s>>>(d->No, Ns, d->d_list[1], wo, v); dw_note_launch();
   DW_CUDA(cudaGetLastError());
   return rc;
 }
@@ -950,10 +1344,13 @@ static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_c
   // ---- block Gram-Schmidt in FP64
   DW_CUDA(cudaMalloc(&d->basis64, (size_t)Ns * 24 * V * sizeof(double)));
   if (ip == DW_F64) DW_CUDA(cudaMemcpyAsync(d->basis64, work, fb * Ns, cudaMemcpyDeviceToDevice, s));
-  else blas_convert<float, double>((const float*)work, d->basis64, 1.0, n * Ns, s);
+  else
+    for (int l = 0; l < Ns; ++l)
+      field_convert<float, double>((const float*)work + (size_t)l * 24 * V, d->basis64 + (size_t)l * 24 * V, 1.0,
+                                   V, s);
   int* d_flag = (int*)(c->d_count + 40);
   DW_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), s));
-  block_gs_kernel<<<d->Nb, 256, 0, s>>>(g, d->d_sub, d->nsub, Ns, d->basis64, d_flag);
+  block_gs_kernel<<<d->Nb, 256, 0, s>>>(g, d->d_sub, d->nsub, Ns, d->basis64, d_flag); dw_note_launch();
   int flag = 0;
   DW_CUDA(cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
   DW_CUDA(cudaStreamSynchronize(s));
@@ -961,7 +1358,7 @@ static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_c
   if (p->basis_prec == DW_BF16) {
     DW_CUDA(cudaMalloc(&d->basis16, (size_t)Ns * 3 * V * sizeof(uint4)));
     size_t tot = V * Ns;
-    quantize_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(V, Ns, d->basis64, d->basis16);
+    quantize_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(V, Ns, d->basis64, d->basis16); dw_note_launch();
   }
   auto t1 = std::chrono::steady_clock::now();
   // ---- little operator (A.1) from the stored basis, FP64
@@ -969,18 +1366,20 @@ static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_c
   DW_CUDA(cudaMalloc(&d->B64, d->Nb * 9 * mat * sizeof(double)));
   assemble_kernel<<<(unsigned)(d->Nb * 9 * Ns), 128, 0, s>>>(g, d->d_sub, d->nsub, d->d_sap2dfl, Ns,
                                                             (const double*)c->links[DW_F64],
-                                                            (const double*)c->clov[DW_F64], d->basis64, d->B64);
+                                                            (const double*)c->clov[DW_F64], d->basis64, d->B64); dw_note_launch();
   DW_CUDA(cudaGetLastError());
+  DW_CUDA(cudaMalloc(&d->B32, d->Nb * 9 * mat * sizeof(float)));
+  blas_convert<double, float>(d->B64, d->B32, 1.0, (size_t)d->Nb * 9 * Ns * Ns, s);
   DW_CUDA(cudaMalloc(&d->Binv64, d->Nb * mat * sizeof(double)));
   DW_CUDA(cudaMalloc(&d->Binv32, d->Nb * mat * sizeof(float)));
   DW_CUDA(cudaMalloc(&d->M64, d->Nb * 8 * mat * sizeof(double)));
   DW_CUDA(cudaMalloc(&d->M32, d->Nb * 8 * mat * sizeof(float)));
   double* d_cond;
   DW_CUDA(cudaMalloc(&d_cond, d->Nb * sizeof(double)));
-  block_inverse_kernel<<<d->Nb, 32, 0, s>>>(Ns, d->B64, d->Binv64, d->Binv32, d_cond);
+  block_inverse_kernel<<<d->Nb, 32, 0, s>>>(Ns, d->B64, d->Binv64, d->Binv32, d_cond); dw_note_launch();
   size_t tot = (size_t)d->Nb * 8 * Ns * Ns;
   neighbour_products_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d->Nb, Ns, d->B64, d->Binv64, d->M64,
-                                                                          d->M32);
+                                                                          d->M32); dw_note_launch();
   std::vector<double> cond(d->Nb);
   DW_CUDA(cudaMemcpyAsync(cond.data(), d_cond, d->Nb * sizeof(double), cudaMemcpyDeviceToHost, s));
   DW_CUDA(cudaStreamSynchronize(s));
@@ -1003,10 +1402,10 @@ static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_c
       const double* src;
       if (ip == DW_F64) src = (const double*)work + (size_t)l * 24 * V;
       else {
-        blas_convert<float, double>((const float*)work + (size_t)l * 24 * V, f64, 1.0, n, s);
+        field_convert<float, double>((const float*)work + (size_t)l * 24 * V, f64, 1.0, V, s);
         src = f64;
       }
-      restrict_kernel<double><<<d->Nb, 128, 0, s>>>(g, d->d_sub, d->nsub, Ns, d->basis64, nullptr, src, cfull);
+      restrict_kernel<double><<<d->Nb, 128, 0, s>>>(g, d->d_sub, d->nsub, Ns, d->basis64, nullptr, src, cfull); dw_note_launch();
       DW_CUDA(cudaMemcpyAsync(hc.data(), cfull, hc.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
       DW_CUDA(cudaStreamSynchronize(s));
       for (int i = 0; i < d->Ne; ++i)
@@ -1074,8 +1473,30 @@ static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_c
           for (int b = 0; b < Ns; ++b) { At[r * Ns + b] -= f * At[col * Ns + b]; X[r * Ns + b] -= f * X[col * Ns + b]; }
         }
       }
-      if (ok) { d->Atil_inv = X; d->a3 = true; }
+      if (ok) {
+        d->Atil_inv = X;
+        d->a3 = true;
+        DW_CUDA(cudaMalloc(&d->Ainv64, (size_t)Ns * Ns * sizeof(cd)));
+        DW_CUDA(cudaMalloc(&d->Ainv32, (size_t)Ns * Ns * 2 * sizeof(float)));
+        DW_CUDA(cudaMemcpy(d->Ainv64, X.data(), (size_t)Ns * Ns * sizeof(cd), cudaMemcpyHostToDevice));
+        blas_convert<double, float>(d->Ainv64, d->Ainv32, 1.0, (size_t)Ns * Ns, s);
+      }
     }
+  }
+  // cooperative little solver: one CTA per SM when all of them can be resident
+  {
+    int dev = 0, sms = 0, coop = 0, b32 = 0, b64 = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, little_gcr_coop_kernel<float>, COOP_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, little_gcr_coop_kernel<double>, COOP_THREADS, 0);
+    d->coop_grid = (coop && b32 > 0 && b64 > 0 && Ns <= 32) ? sms : 0;
+    if (d->coop_grid) {
+      DW_CUDA(cudaMalloc(&d->coop_partial, (size_t)2 * d->coop_grid * COOP_NV * sizeof(double)));
+      DW_CUDA(cudaMalloc(&d->coop_out, 4 * sizeof(double)));
+    }
+    if ((rc = ensure_little_work(d, DW_F64, COOP_NKV))) return rc;
   }
   auto t2 = std::chrono::steady_clock::now();
   if (info) {

@@ -82,7 +82,7 @@ template <typename T>
 void dirac_full(dw_ctx* c, const T* in, T* out, cudaStream_t st) {
   constexpr int P = prec_of<T>();
   unsigned blocks = (unsigned)((c->V + 127) / 128);
-  dirac_full_kernel<T><<<blocks, 128, 0, st>>>(c->g, (const T*)c->links[P], (const T*)c->clov[P], in, out);
+  dirac_full_kernel<T><<<blocks, 128, 0, st>>>(c->g, (const T*)c->links[P], (const T*)c->clov[P], in, out); dw_note_launch();
 }
 template void dirac_full<float>(dw_ctx*, const float*, float*, cudaStream_t);
 template void dirac_full<double>(dw_ctx*, const double*, double*, cudaStream_t);
@@ -93,8 +93,8 @@ static int dirac_schur(dw_ctx* c, const T* in, T* out, cudaStream_t st) {
   if (!c->sap_d[P]) DW_CUDA(cudaMalloc(&c->sap_d[P], dw_field_bytes(c, P)));
   T* t = (T*)c->sap_d[P];
   unsigned blocks = (unsigned)((c->V / 2 + 127) / 128);
-  schur_odd_kernel<T><<<blocks, 128, 0, st>>>(c->g, (const T*)c->links[P], (const T*)c->clovinv[P], in, t);
-  schur_even_kernel<T><<<blocks, 128, 0, st>>>(c->g, (const T*)c->links[P], (const T*)c->clov[P], in, t, out);
+  schur_odd_kernel<T><<<blocks, 128, 0, st>>>(c->g, (const T*)c->links[P], (const T*)c->clovinv[P], in, t); dw_note_launch();
+  schur_even_kernel<T><<<blocks, 128, 0, st>>>(c->g, (const T*)c->links[P], (const T*)c->clov[P], in, t, out); dw_note_launch();
   return DW_OK;
 }
 

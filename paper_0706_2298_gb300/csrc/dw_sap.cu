@@ -231,7 +231,7 @@ void launch_sap(dw_ctx* c, int colour, const T* rsrc, T* rdst, const T* dprev, T
   }
   sap_block_kernel<T, SHV><<<c->ncolour[colour], SHV, smem, st>>>(c->g, (const T*)c->links[P], (const T*)c->clov[P],
                                                               (const T*)c->clovinv[P], list, rsrc, rdst, dprev,
-                                                              dout, xi, first, nmr);
+                                                              dout, xi, first, nmr); dw_note_launch();
 }
 
 }  // namespace

@@ -5,6 +5,7 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 
 #include "dw_common.cuh"
@@ -18,6 +19,10 @@ int dw_cuda_fail(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? DW_ENOMEM : DW_ECUDA;
 }
 extern "C" const char* dw_last_error(void) { return g_err.c_str(); }
+
+static std::atomic<long long> g_launches{0};
+void dw_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+extern "C" long long dw_launch_count(void) { return g_launches.load(); }
 
 // ------------------------------------------------------------------ clover kernel
 // sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu] restricted to the two chiral blocks,
@@ -441,7 +446,7 @@ extern "C" int dw_create(const dw_params* p, const double* links_host, dw_ctx** 
   long long blocks = (V + threads - 1) / threads;
   clover_build_kernel<<<(unsigned)blocks, threads>>>(g, (const double*)c->links[DW_F64], sig, 4.0 + p->m0, p->csw,
                                                      (double*)c->clov[DW_F64], (double*)c->clovinv[DW_F64],
-                                                     (float*)c->clov[DW_F32], (float*)c->clovinv[DW_F32], d_bad);
+                                                     (float*)c->clov[DW_F32], (float*)c->clovinv[DW_F32], d_bad); dw_note_launch();
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   int bad = 0;
@@ -460,8 +465,8 @@ extern "C" int dw_pack(dw_ctx* c, int prec, int nrhs, const double* in, void* ou
   }
   cudaStream_t s = (cudaStream_t)stream;
   unsigned blocks = (unsigned)((c->V + 127) / 128);
-  if (prec == DW_F64) pack_kernel64<<<blocks, 128, 0, s>>>(c->V, c->d_canon_of, nrhs, in, (double*)out);
-  else pack_kernel32<<<blocks, 128, 0, s>>>(c->V, c->d_canon_of, nrhs, in, (float*)out);
+  if (prec == DW_F64) { pack_kernel64<<<blocks, 128, 0, s>>>(c->V, c->d_canon_of, nrhs, in, (double*)out); dw_note_launch(); }
+  else { pack_kernel32<<<blocks, 128, 0, s>>>(c->V, c->d_canon_of, nrhs, in, (float*)out); dw_note_launch(); }
   DW_CUDA(cudaGetLastError());
   return DW_OK;
 }
@@ -473,8 +478,8 @@ extern "C" int dw_unpack(dw_ctx* c, int prec, int nrhs, const void* in, double* 
   }
   cudaStream_t s = (cudaStream_t)stream;
   unsigned blocks = (unsigned)((c->V + 127) / 128);
-  if (prec == DW_F64) unpack_kernel<double><<<blocks, 128, 0, s>>>(c->V, c->d_canon_of, nrhs, (const double*)in, out);
-  else unpack_kernel<float><<<blocks, 128, 0, s>>>(c->V, c->d_canon_of, nrhs, (const float*)in, out);
+  if (prec == DW_F64) { unpack_kernel<double><<<blocks, 128, 0, s>>>(c->V, c->d_canon_of, nrhs, (const double*)in, out); dw_note_launch(); }
+  else { unpack_kernel<float><<<blocks, 128, 0, s>>>(c->V, c->d_canon_of, nrhs, (const float*)in, out); dw_note_launch(); }
   DW_CUDA(cudaGetLastError());
   return DW_OK;
 }

@@ -18,6 +18,8 @@
 #include <chrono>
 #include <cmath>
 #include <complex>
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "dw_common.cuh"
@@ -145,6 +147,7 @@ int solve_one(dw_ctx* c, dfl_ctx* d, const sol_params* p, const double* eta_cano
   blas_dot<double>(c, W.eta, W.eta, n, dres, s);
   if ((rc = read_host(c, dres, 3, h, s))) return rc;
   const double en = sqrt(h[2]);
+  const bool verbose = getenv("DW_VERBOSE") && atoi(getenv("DW_VERBOSE")) > 0;
   sol_info inf{};
   inf.status = DW_ENOTCONV;
   if (en == 0.0) {
@@ -187,10 +190,13 @@ int solve_one(dw_ctx* c, dfl_ctx* d, const sol_params* p, const double* eta_cano
     }
     const double rn = sqrt(h[2]);
     relres = rn / en;
+    if (verbose)
+      fprintf(stderr, "[dwsolve] restart %d: |rho|/|eta| = %.3e  gcr steps %d  little its %d (%d solves)\n",
+              restart, relres, inf.iterations, inf.little_iterations, inf.little_solves);
     if (rn <= p->tol * en) { inf.status = DW_OK; break; }
     if (inf.iterations >= p->nmx) break;
     // ---- one GCR cycle in precision T on rho / rn
-    blas_convert<double, T>(W.r64, W.rho, 1.0 / rn, n, s);
+    field_convert<double, T>(W.r64, W.rho, 1.0 / rn, V, s);
     const double stop = std::max(p->tol * en / rn, p->mixed ? p->inner_rtol : 0.0);
     int k = 0;
     double rk = 1.0;
@@ -245,6 +251,8 @@ int solve_one(dw_ctx* c, dfl_ctx* d, const sol_params* p, const double* eta_cano
       tm.end();
       rk = sqrt(h[2]);
       inf.iterations += 1;
+      if (verbose > 0 && getenv("DW_VERBOSE")[0] == '2')
+        fprintf(stderr, "[dwsolve]   step %d: |rho_k| = %.3e  c_k = %.3e\n", k, rk, ck);
       if (rk <= stop) { ++k; break; }
     }
     if (k == 0) break;
@@ -259,7 +267,7 @@ int solve_one(dw_ctx* c, dfl_ctx* d, const sol_params* p, const double* eta_cano
     std::vector<const T*> xs(W.xi.begin(), W.xi.begin() + k);
     tm.begin(PH_RESTART);
     blas_lincomb<T>(xs.data(), k, coef.data(), W.w, n, s);
-    blas_convert<T, double>(W.w, W.t64, rn, n, s);
+    field_convert<T, double>(W.w, W.t64, rn, V, s);
     blas_axpy<double>(W.t64, W.psi, 1.0, 0.0, n, s);
     tm.end();
     inf.restarts += 1;
@@ -292,4 +300,70 @@ extern "C" int gcr_solve(dw_ctx* c, dfl_ctx* d, const sol_params* p, int nrhs, c
     if (rc > worst) worst = rc;
   }
   return worst;
+}
+
+// ------------------------------------------------------------------------- CGNR
+// Conjugate gradient on the normal equations D^+ D psi = D^+ eta (CGLS form,
+// recursively updated residual r = eta - D psi), FP64.  Used to measure the
+// unpreconditioned CG iteration count that fixes the bare mass of a workload
+// and as the plain comparison solver.  D^+ = gamma_5 D gamma_5; in the packed
+// layout gamma_5 flips the sign of the second half of a field (spins 2, 3).
+extern "C" int cgnr_solve(dw_ctx* c, double tol, int maxit, const double* eta_canon, double* psi_canon, int* iters,
+                          double* relres, void* stream) {
+  if (!c || !eta_canon || !psi_canon || maxit < 1 || !(tol > 0)) {
+    dw_set_error("cgnr_solve: bad argument");
+    return DW_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t V = c->V, n = V * 12, fb = dw_field_bytes(c, DW_F64);
+  Work<double> W;
+  double *b, *x, *r, *p, *q, *t;
+  int rc;
+  if ((rc = W.alloc(fb, (void**)&b)) || (rc = W.alloc(fb, (void**)&x)) || (rc = W.alloc(fb, (void**)&r)) ||
+      (rc = W.alloc(fb, (void**)&p)) || (rc = W.alloc(fb, (void**)&q)) || (rc = W.alloc(fb, (void**)&t)))
+    return rc;
+  double* dres = c->d_red + 65536 + 8192;
+  double h[3];
+  auto gdag = [&](const double* in, double* out) -> int {   // out = gamma_5 D gamma_5 in
+    DW_CUDA(cudaMemcpyAsync(t, in, fb, cudaMemcpyDeviceToDevice, s));
+    blas_scale<double>(t + n, -1.0, 0.0, n / 2, s);
+    dirac_full<double>(c, t, out, s);
+    blas_scale<double>(out + n, -1.0, 0.0, n / 2, s);
+    return DW_OK;
+  };
+  if ((rc = dw_pack(c, DW_F64, 1, eta_canon, b, s))) return rc;
+  DW_CUDA(cudaMemsetAsync(x, 0, fb, s));
+  DW_CUDA(cudaMemcpyAsync(r, b, fb, cudaMemcpyDeviceToDevice, s));
+  blas_dot<double>(c, b, b, n, dres, s);
+  if ((rc = read_host(c, dres, 3, h, s))) return rc;
+  const double bn = sqrt(h[2]);
+  if ((rc = gdag(r, p))) return rc;        // p = s = D^+ r
+  blas_dot<double>(c, p, p, n, dres, s);
+  if ((rc = read_host(c, dres, 3, h, s))) return rc;
+  double gam = h[2], rn = bn;
+  int it = 0;
+  while (rn > tol * bn && it < maxit && gam > 0) {
+    dirac_full<double>(c, p, q, s);
+    blas_dot<double>(c, q, q, n, dres, s);
+    if ((rc = read_host(c, dres, 3, h, s))) return rc;
+    double alpha = gam / h[2];
+    blas_axpy<double>(p, x, alpha, 0.0, n, s);
+    blas_axpy<double>(q, r, -alpha, 0.0, n, s);
+    if ((rc = gdag(r, q))) return rc;      // q = s = D^+ r
+    blas_dot<double>(c, q, q, n, dres, s);
+    double h2[3];
+    if ((rc = read_host(c, dres, 3, h2, s))) return rc;
+    blas_dot<double>(c, r, r, n, dres, s);
+    if ((rc = read_host(c, dres, 3, h, s))) return rc;
+    rn = sqrt(h[2]);
+    double beta = h2[2] / gam;
+    gam = h2[2];
+    blas_xpby<double>(q, p, beta, 0.0, n, s);   // p = s + beta p
+    ++it;
+  }
+  if ((rc = dw_unpack(c, DW_F64, 1, x, psi_canon, s))) return rc;
+  DW_CUDA(cudaStreamSynchronize(s));
+  if (iters) *iters = it;
+  if (relres) *relres = rn / bn;
+  return rn <= tol * bn ? DW_OK : DW_ENOTCONV;
 }

@@ -62,6 +62,7 @@ class SolInfo(C.Structure):
 _P = C.c_void_p
 _SIGNATURES = {
     "dw_last_error": (C.c_char_p, []),
+    "dw_launch_count": (C.c_longlong, []),
     "dw_create": (C.c_int, [C.POINTER(DwParams), _P, C.POINTER(_P)]),
     "dw_destroy": (None, [_P]),
     "dw_field_bytes": (C.c_size_t, [_P, C.c_int]),
@@ -80,6 +81,7 @@ _SIGNATURES = {
     "little_dirac_solve": (C.c_int, [_P, C.c_int, _P, _P, C.c_double, C.c_int, C.POINTER(C.c_int),
                                      C.POINTER(C.c_double), _P]),
     "gcr_solve": (C.c_int, [_P, _P, C.POINTER(SolParams), C.c_int, _P, _P, C.POINTER(SolInfo), _P]),
+    "cgnr_solve": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.POINTER(C.c_int), C.POINTER(C.c_double), _P]),
 }
 
 _lib = None
@@ -101,6 +103,10 @@ def lib():
             f.argtypes = args
         _lib = L
     return _lib
+
+
+def dw_launch_count() -> int:
+    return int(lib().dw_launch_count())
 
 
 def exported_symbols():
@@ -259,3 +265,10 @@ def gcr_solve(ctx: Ctx, d, params: SolParams, nrhs, eta_dev, psi_dev, stream=Non
                                 _ptr(_as_f64(eta_dev)), _ptr(_as_f64(psi_dev)), infos, _stream(stream)),
                 ok=(DW_OK, DW_ENOTCONV))
     return rc, [infos[i] for i in range(nrhs)]
+
+
+def cgnr_solve(ctx: Ctx, tol, maxit, eta_dev, psi_dev, stream=None):
+    it, rr = C.c_int(), C.c_double()
+    rc = _check(lib().cgnr_solve(ctx.handle, float(tol), int(maxit), _ptr(_as_f64(eta_dev)), _ptr(_as_f64(psi_dev)),
+                                 C.byref(it), C.byref(rr), _stream(stream)), ok=(DW_OK, DW_ENOTCONV))
+    return rc, it.value, rr.value

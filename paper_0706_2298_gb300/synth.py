@@ -112,8 +112,9 @@ def random_gauge(L: Sequence[int], seed: int, eps: float = 0.3, ape_steps: int =
                  alpha: float = 0.5, device: str | torch.device = "cpu") -> torch.Tensor:
     """Smeared random SU(3) field, complex128[V, 4, 3, 3] on ``device``."""
     V = volume(L)
-    X = _traceless_hermitian(V * 4, seed, "gauge").to(device)
-    U = _exp_i_hermitian(X, eps).reshape(V, 4, 3, 3)
+    X = _traceless_hermitian(V * 4, seed, "gauge")
+    # the eigendecomposition runs on the CPU (batched 3x3 eigh on CUDA asks for huge workspaces)
+    U = _exp_i_hermitian(X, eps).reshape(V, 4, 3, 3).to(device)
     if ape_steps > 0:
         U = ape_smear(U, L, ape_steps, alpha)
     return U.contiguous()

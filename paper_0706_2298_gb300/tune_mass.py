@@ -1,0 +1,78 @@
+"""Bare-mass tuning for a benchmark workload.
+
+The 48 x 24^3 workload is defined at a near-critical bare mass: the lightest
+mass (approached from the heavy side) at which the unpreconditioned conjugate
+gradient on the normal equations needs more than ``target`` iterations to
+reach ||eta - D psi|| <= 1e-10 ||eta||.  This script scans m0 downwards,
+then bisects between the last easy and the first hard mass, using the
+library's FP64 CGNR on the GPU, and records the result in
+``workload_masses.json``.
+
+    python -m paper_0706_2298_gb300.tune_mass [--target 2000]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(HERE))
+
+
+def main():
+    import torch
+    from paper_0706_2298_gb300 import dwsolve as dw
+    from paper_0706_2298_gb300 import synth
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--L", default="48,24,24,24")
+    ap.add_argument("--target", type=int, default=2000)
+    ap.add_argument("--maxit", type=int, default=6000)
+    ap.add_argument("--bisect", type=int, default=7)
+    ap.add_argument("--name", default="24^3x48")
+    args = ap.parse_args()
+    L = tuple(int(v) for v in args.L.split(","))
+    U = synth.random_gauge(L, 1, device="cuda").cpu()
+    eta = synth.gaussian_source(L, 2).cuda()
+    psi = torch.empty_like(eta)
+    log = []
+
+    def count(m0):
+        ctx = dw.dw_create(L, m0, 1.0, U, (4, 4, 4, 4))
+        rc, it, rr = dw.cgnr_solve(ctx, 1e-10, args.maxit, eta, psi)
+        log.append({"m0": m0, "cg_iterations": it, "relres": rr, "converged": rc == dw.DW_OK})
+        print(f"m0 = {m0:+.5f}: CGNR iterations {it} (relres {rr:.2e})", flush=True)
+        return it if rc == dw.DW_OK else args.maxit + 1
+
+    easy, hard = None, None
+    m = 0.2
+    while m > -0.6:
+        c = count(m)
+        if c > args.target:
+            hard = (m, c)
+            break
+        easy = (m, c)
+        m -= 0.05
+    if hard is None or easy is None:
+        raise SystemExit("no mass with more than target iterations found")
+    lo, hi = hard[0], easy[0]
+    for _ in range(args.bisect):
+        mid = 0.5 * (lo + hi)
+        c = count(mid)
+        if c > args.target:
+            lo, hard = mid, (mid, c)
+        else:
+            hi = mid
+    out_path = os.path.join(HERE, "workload_masses.json")
+    data = json.load(open(out_path)) if os.path.exists(out_path) else {}
+    data[args.name] = {"m0": round(hard[0], 6), "cg_iterations": hard[1], "target": args.target,
+                       "rule": "heaviest scanned/bisected mass with CGNR iterations > target", "scan": log}
+    with open(out_path, "w") as f:
+        json.dump(data, f, indent=1)
+    print(json.dumps(data[args.name]))
+
+
+if __name__ == "__main__":
+    main()

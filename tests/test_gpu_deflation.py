@@ -1,0 +1,209 @@
+"""GPU parity of the deflation subspace, the little Dirac operator, the little
+solver and the full DFL+SAP+GCR solve against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle.deflation import BlockSubspace, block_gram_schmidt, inverse_iteration, round_bf16
+from oracle.dirac import WilsonClover
+from oracle.sap import Blocking, SchwarzOracle
+from oracle.solver import solve_plain
+from paper_0706_2298_gb300 import dwsolve as dw
+from paper_0706_2298_gb300 import synth
+
+from .gpu_util import from_packed, rel, to_packed
+
+pytestmark = pytest.mark.gpu
+
+# (lattice, Schwarz block, deflation block, Ns)
+CASES = [
+    ((8, 8, 8, 8), (4, 4, 4, 4), (4, 4, 4, 4), 6),     # two blocks per direction: +mu and -mu neighbours coincide
+    ((8, 8, 8, 8), (2, 2, 2, 2), (4, 4, 4, 4), 5),     # 16 Schwarz blocks per deflation block
+    ((16, 8, 8, 8), (4, 4, 4, 4), (4, 4, 4, 4), 4),    # four blocks in time
+]
+
+
+def basis_fields(sub: BlockSubspace):
+    """The oracle's block basis as Ns global fields (field l = sum_L phi^L_l)."""
+    out = np.zeros((sub.Ns, sub.D.V, 12), dtype=np.complex128)
+    for L in range(sub.Nb):
+        out[:, sub.blk.sites[L], :] = sub.phi[L].reshape(sub.Ns, -1, 12)
+    return out.reshape(sub.Ns, sub.D.V, 4, 3)
+
+
+@pytest.fixture(scope="module", params=CASES, ids=lambda c: "x".join(map(str, c[0])) + f"_s{c[1][0]}_d{c[2][0]}")
+def case(request):
+    L, sb, db, Ns = request.param
+    U = synth.random_gauge(L, 4)
+    m0, csw = -0.2, 1.0
+    ctx = dw.dw_create(L, m0, csw, U, sb)
+    D = WilsonClover(L, U.numpy(), m0, csw)
+    start = synth.start_fields(L, Ns, 3)
+    return L, sb, db, Ns, ctx, D, start
+
+
+def _build(case, basis_prec, n_inv=0, iter_prec=dw.DW_F64, cond_max=1e8):
+    L, sb, db, Ns, ctx, D, start = case
+    return dw.deflation_build(ctx, db, Ns, n_inv, 4, 4, start.cuda(), basis_prec=basis_prec, iter_prec=iter_prec,
+                              cond_max=cond_max)
+
+
+def _export(case, d):
+    L, sb, db, Ns, ctx, D, start = case
+    out = torch.empty((Ns, ctx.V, 4, 3), dtype=torch.complex128, device="cuda")
+    dw.dfl_basis_export(d, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def test_block_gram_schmidt_fp64(case):
+    L, sb, db, Ns, ctx, D, start = case
+    d = _build(case, dw.DW_F64)
+    sub = BlockSubspace(D, db, block_gram_schmidt(Blocking(L, db), start.numpy()))
+    assert rel(_export(case, d), basis_fields(sub)) <= 1e-13
+
+
+def test_basis_bf16_rounding(case):
+    """The stored BF16 basis is the FP64 Gram-Schmidt result rounded to bfloat16 through FP32."""
+    L, sb, db, Ns, ctx, D, start = case
+    d = _build(case, dw.DW_BF16)
+    phi = round_bf16(block_gram_schmidt(Blocking(L, db), start.numpy()))
+    sub = BlockSubspace(D, db, phi)
+    got, want = _export(case, d), basis_fields(sub)
+    # identical except where the two FP64 Gram-Schmidt results straddle a rounding boundary
+    mismatch = np.mean(got != want)
+    assert mismatch < 1e-6 and rel(got, want) <= 1e-5
+
+
+@pytest.mark.parametrize("basis_prec,prec,tol", [(dw.DW_F64, dw.DW_F64, 1e-13), (dw.DW_BF16, dw.DW_F32, 1e-5),
+                                                 (dw.DW_BF16, dw.DW_F64, 1e-12)])
+def test_restrict_prolong(case, basis_prec, prec, tol):
+    L, sb, db, Ns, ctx, D, start = case
+    d = _build(case, basis_prec)
+    phi = block_gram_schmidt(Blocking(L, db), start.numpy())
+    if basis_prec == dw.DW_BF16:
+        phi = round_bf16(phi)
+    sub = BlockSubspace(D, db, phi)
+    psi = synth.gaussian_source(L, 11).numpy()
+    x = to_packed(ctx, prec, psi)
+    dt = torch.float64 if prec == dw.DW_F64 else torch.float32
+    c = torch.empty(d.Nb * d.Ns * 2, dtype=dt, device="cuda")
+    dw.dfl_restrict(d, prec, x, c)
+    torch.cuda.synchronize()
+    cg = c.double().cpu().numpy().view(np.complex128).reshape(d.Nb, d.Ns)
+    c_or = sub.restrict(psi)
+    assert rel(cg, c_or) <= tol
+    cin = synth.complex_gaussian((d.Nb, d.Ns), 12).numpy()
+    ct = torch.from_numpy(cin.view(np.float64).reshape(-1).copy()).to(dt).cuda()
+    y = ctx.empty_field(prec)
+    dw.dfl_prolong(d, prec, ct, y)
+    assert rel(from_packed(ctx, prec, y), sub.prolong(cin.astype(np.complex64 if prec == dw.DW_F32 else np.complex128)
+                                                      .astype(np.complex128))) <= tol
+
+
+def test_little_operator_assembly(case):
+    """(A.1): the assembled little operator equals (phi_k, D phi_l) on the same basis."""
+    L, sb, db, Ns, ctx, D, start = case
+    d = _build(case, dw.DW_F64)
+    sub = BlockSubspace(D, db, block_gram_schmidt(Blocking(L, db), start.numpy()))
+    v = synth.complex_gaussian((d.Nb * d.Ns,), 13).numpy()
+    w = torch.empty(d.Nb * d.Ns, dtype=torch.complex128, device="cuda")
+    dw.little_apply(d, torch.from_numpy(v).cuda(), w)
+    torch.cuda.synchronize()
+    assert rel(w.cpu().numpy(), sub.A @ v) <= 1e-13
+
+
+@pytest.mark.parametrize("prec,tol,cmp", [(dw.DW_F64, 1e-12, 1e-9), (dw.DW_F32, 1e-5, 1e-4)])
+def test_little_solve(case, prec, tol, cmp):
+    L, sb, db, Ns, ctx, D, start = case
+    d = _build(case, dw.DW_F64 if prec == dw.DW_F64 else dw.DW_BF16)
+    phi = block_gram_schmidt(Blocking(L, db), start.numpy())
+    if prec == dw.DW_F32:
+        phi = round_bf16(phi)
+    sub = BlockSubspace(D, db, phi)
+    wv = synth.complex_gaussian((d.Nb * d.Ns,), 14).numpy()
+    dt = torch.float64 if prec == dw.DW_F64 else torch.float32
+    wt = torch.from_numpy(wv.view(np.float64).copy()).to(dt).cuda()
+    vt = torch.empty_like(wt)
+    rc, it, rr = dw.little_dirac_solve(d, prec, wt, vt, tol, 2000)
+    assert rc == dw.DW_OK and rr <= tol
+    v = vt.double().cpu().numpy().view(np.complex128)
+    assert rel(v, np.linalg.solve(sub.A, wv)) <= cmp
+
+
+def test_little_solve_fallback(case):
+    """A.2: with every diagonal block declared ill-conditioned the full little system is solved."""
+    L, sb, db, Ns, ctx, D, start = case
+    d = _build(case, dw.DW_F64, cond_max=1.0)
+    assert d.status == dw.DW_ILLCOND
+    sub = BlockSubspace(D, db, block_gram_schmidt(Blocking(L, db), start.numpy()))
+    wv = synth.complex_gaussian((d.Nb * d.Ns,), 15).numpy()
+    wt = torch.from_numpy(wv).cuda()
+    vt = torch.empty_like(wt)
+    rc, it, rr = dw.little_dirac_solve(d, dw.DW_F64, wt, vt, 1e-12, 4000)
+    assert rc == dw.DW_OK
+    assert rel(vt.cpu().numpy(), np.linalg.solve(sub.A, wv)) <= 1e-9
+
+
+def test_inverse_iteration_fp64(case):
+    """(5.1) with M_sap: FP64 GPU subspace generation equals the oracle's."""
+    L, sb, db, Ns, ctx, D, start = case
+    d = _build(case, dw.DW_F64, n_inv=2)
+    fields = inverse_iteration(SchwarzOracle(D, sb), start.numpy(), 2, 4, 4)
+    sub = BlockSubspace(D, db, block_gram_schmidt(Blocking(L, db), fields))
+    assert rel(_export(case, d), basis_fields(sub)) <= 1e-11
+
+
+def test_global_mode_deflation_helps(case):
+    """A.3 lowers the little GCR count: compare with the same system after A.2 fallback."""
+    L, sb, db, Ns, ctx, D, start = case
+    d = _build(case, dw.DW_F64, n_inv=2)
+    wv = synth.complex_gaussian((d.Nb * d.Ns,), 16).numpy()
+    wt = torch.from_numpy(wv).cuda()
+    vt = torch.empty_like(wt)
+    rc, it_eo, rr = dw.little_dirac_solve(d, dw.DW_F64, wt, vt, 1e-10, 4000)
+    d2 = _build(case, dw.DW_F64, n_inv=2, cond_max=1.0)
+    rc2, it_full, rr2 = dw.little_dirac_solve(d2, dw.DW_F64, wt, vt, 1e-10, 4000)
+    assert rc == dw.DW_OK and rc2 == dw.DW_OK
+    assert it_eo < it_full
+
+
+# ----------------------------------------------------------------------------- full solver
+@pytest.fixture(scope="module")
+def solve_case():
+    L = (8, 8, 8, 8)
+    U = synth.random_gauge(L, 1)
+    ctx = dw.dw_create(L, -0.2, 1.0, U, (4, 4, 4, 4))
+    D = WilsonClover(L, U.numpy(), -0.2, 1.0)
+    eta = synth.gaussian_source(L, 2)
+    x, info = solve_plain(D, eta.numpy(), tol=1e-12)
+    assert info.converged
+    return L, ctx, D, eta, x
+
+
+@pytest.mark.parametrize("mixed,dfl", [(1, True), (0, True), (1, False), (0, False)])
+def test_gcr_solve(solve_case, mixed, dfl):
+    L, ctx, D, eta, x = solve_case
+    d = None
+    if dfl:
+        d = dw.deflation_build(ctx, (4, 4, 4, 4), 8, 4, 4, 4, synth.start_fields(L, 8, 3).cuda(),
+                               basis_prec=dw.DW_BF16 if mixed else dw.DW_F64,
+                               iter_prec=dw.DW_F32 if mixed else dw.DW_F64)
+    p = dw.sol_params(tol=1e-10, nkv=16, mixed=mixed)
+    psi = torch.empty_like(eta, device="cuda")
+    rc, infos = dw.gcr_solve(ctx, d, p, 1, eta.cuda(), psi)
+    assert rc == dw.DW_OK
+    psi = psi.cpu().numpy()
+    r = np.linalg.norm(eta.numpy() - D.apply(psi)) / np.linalg.norm(eta.numpy())
+    assert r <= 1.05e-10
+    assert rel(psi, x) <= 1e-8
+    assert infos[0].relres <= 1e-10 and infos[0].iterations > 0
+
+
+def test_inverse_iteration_fp32(case):
+    """FP32 subspace generation (the mixed path) tracks the FP64 oracle to FP32 accuracy."""
+    L, sb, db, Ns, ctx, D, start = case
+    d = _build(case, dw.DW_F64, n_inv=2, iter_prec=dw.DW_F32)
+    fields = inverse_iteration(SchwarzOracle(D, sb), start.numpy(), 2, 4, 4)
+    sub = BlockSubspace(D, db, block_gram_schmidt(Blocking(L, db), fields))
+    assert rel(_export(case, d), basis_fields(sub)) <= 1e-4
