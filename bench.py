@@ -170,6 +170,7 @@ def main():
     ap.add_argument("--workload", default="24^3x48", choices=list(WORKLOADS))
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 12 point-source batched solve")
     args = ap.parse_args()
     load_masses()
     wl = WORKLOADS[args.workload]
@@ -231,7 +232,9 @@ def main():
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     ev0.record()
+    torch.cuda.nvtx.range_push("timed_solve")
     infos = [solve() for _ in range(args.steps)]
+    torch.cuda.nvtx.range_pop()
     ev1.record()
     torch.cuda.synchronize()
     launches = dw.dw_launch_count() - n0
@@ -316,6 +319,34 @@ def main():
     e2e = {"value": a.elapsed_time(b) / 1e3 / args.steps, "unit": "s/solve",
            "h2d_bytes_per_step": eta_h.numel() * 16, "d2h_bytes_per_step": eta_h.numel() * 16}
 
+    # ---- 12 spin-colour point sources: one lockstep batch (captured M_sap graphs) vs one at a time
+    batch = None
+    if not args.no_batch:
+        tune = dw.dw_autotune(ctx, 12)
+        eta12 = synth.point_sources(L).cuda()
+        psi12 = torch.empty_like(eta12)
+        res = {}
+        for mode in ("batched", "sequential"):
+            if mode == "sequential":
+                os.environ["DW_BATCH"] = "0"
+            rc, inf12 = dw.gcr_solve(ctx, dfl, p_mixed, 12, eta12, psi12)      # warm-up (captures graphs)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            n0b = dw.dw_launch_count()
+            a.record()
+            rc, inf12 = dw.gcr_solve(ctx, dfl, p_mixed, 12, eta12, psi12)
+            b.record()
+            torch.cuda.synchronize()
+            os.environ.pop("DW_BATCH", None)
+            res[mode] = {"s_per_rhs": a.elapsed_time(b) / 1e3 / 12, "s_total": a.elapsed_time(b) / 1e3,
+                         "converged": rc == dw.DW_OK, "max_relres": max(i.relres for i in inf12),
+                         "gcr_iterations_max": max(i.iterations for i in inf12),
+                         "launches": dw.dw_launch_count() - n0b}
+        batch = {"workload": f"{args.workload}, 12 point sources (spin-colour unit vectors at the origin)",
+                 **res, "speedup_batched": res["sequential"]["s_total"] / res["batched"]["s_total"],
+                 "autotune": tune}
+        del eta12, psi12
+
     # ---- CPU oracle sample (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -343,7 +374,7 @@ def main():
                 "dfl_build_s": t_build, "plain_fp64": plain,
                 "speedup_vs_plain_fp64": (plain["s_per_solve"] / value) if plain else None,
                 "dirac": dirac, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clk}
+                "gpu_launches": launches, "clocks": clk, "batch12": batch}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

@@ -7,7 +7,7 @@
 namespace {
 
 constexpr int RB = 256;            // reduction CTA size
-constexpr int RGRID = 304;         // 2 CTAs per SM on 152 SMs
+constexpr int RGRID = 608;         // 4 CTAs per SM on 152 SMs
 constexpr int MAXK = 16;           // vectors per multi-dot launch
 
 template <typename T, int K>
@@ -52,37 +52,64 @@ __device__ void grid_reduce(double* v, double* partial, unsigned* count, double*
   if (threadIdx.x == 0) *count = 0;
 }
 
+// Per-thread partial sums in the field's own precision (FP32 fields: FP32, a few dozen terms per
+// thread), combined across threads in FP64.  vec: 16-byte loads when both pointers allow them.
 template <typename T>
 __global__ void __launch_bounds__(RB) dot_kernel(const T* __restrict__ a, const T* __restrict__ b, size_t n,
-                                                 double* partial, unsigned* count, double* out) {
-  double v[3] = {0, 0, 0};   // re, im, |a|^2 (norm comes for free)
+                                                 int vec, double* partial, unsigned* count, double* out) {
+  T r0 = 0, r1 = 0, r2 = 0;   // re, im of (a, b), |a|^2
+  const size_t tid = blockIdx.x * (size_t)RB + threadIdx.x, nth = (size_t)gridDim.x * RB;
   const cplx<T>* A = reinterpret_cast<const cplx<T>*>(a);
   const cplx<T>* B = reinterpret_cast<const cplx<T>*>(b);
-  for (size_t i = blockIdx.x * (size_t)RB + threadIdx.x; i < n; i += (size_t)gridDim.x * RB) {
-    cplx<T> x = A[i], y = B[i];
-    v[0] += (double)x.re * y.re + (double)x.im * y.im;
-    v[1] += (double)x.re * y.im - (double)x.im * y.re;
-    v[2] += (double)x.re * x.re + (double)x.im * x.im;
+  size_t done = 0;
+  if (vec) {
+    using U = typename Unit<T>::t;
+    constexpr int C = Unit<T>::C;
+    const U* AU = reinterpret_cast<const U*>(a);
+    const U* BU = reinterpret_cast<const U*>(b);
+    const size_t nu = n / C;
+    for (size_t i = tid; i < nu; i += nth) {
+      cplx<T> x[C], y[C];
+      unpack_unit(AU[i], x);
+      unpack_unit(BU[i], y);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        r0 += x[c].re * y[c].re + x[c].im * y[c].im;
+        r1 += x[c].re * y[c].im - x[c].im * y[c].re;
+        r2 += x[c].re * x[c].re + x[c].im * x[c].im;
+      }
+    }
+    done = nu * C;
   }
+  for (size_t i = done + tid; i < n; i += nth) {
+    cplx<T> x = A[i], y = B[i];
+    r0 += x.re * y.re + x.im * y.im;
+    r1 += x.re * y.im - x.im * y.re;
+    r2 += x.re * x.re + x.im * x.im;
+  }
+  double v[3] = {(double)r0, (double)r1, (double)r2};
   grid_reduce<3>(v, partial, count, out);
 }
 
 template <typename T, int K>
 __global__ void __launch_bounds__(RB) multi_dot_kernel(Ptrs<T, MAXK> vs, const T* __restrict__ b, size_t n,
                                                        double* partial, unsigned* count, double* out) {
-  double v[2 * K];
+  T r[2 * K];
 #pragma unroll
-  for (int k = 0; k < 2 * K; ++k) v[k] = 0;
+  for (int k = 0; k < 2 * K; ++k) r[k] = 0;
   const cplx<T>* B = reinterpret_cast<const cplx<T>*>(b);
   for (size_t i = blockIdx.x * (size_t)RB + threadIdx.x; i < n; i += (size_t)gridDim.x * RB) {
     cplx<T> y = B[i];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       cplx<T> x = reinterpret_cast<const cplx<T>*>(vs.p[k])[i];
-      v[2 * k] += (double)x.re * y.re + (double)x.im * y.im;
-      v[2 * k + 1] += (double)x.re * y.im - (double)x.im * y.re;
+      r[2 * k] += x.re * y.re + x.im * y.im;
+      r[2 * k + 1] += x.re * y.im - x.im * y.re;
     }
   }
+  double v[2 * K];
+#pragma unroll
+  for (int k = 0; k < 2 * K; ++k) v[k] = (double)r[k];
   grid_reduce<2 * K>(v, partial, count, out);
 }
 
@@ -157,7 +184,8 @@ inline unsigned ew_grid(size_t n) {
 template <typename T>
 int blas_dot(dw_ctx* c, const T* a, const T* b, size_t n, double* out3, cudaStream_t s) {
   // out3 (device): re, im of (a, b) and |a|^2
-  dot_kernel<T><<<RGRID, RB, 0, s>>>(a, b, n, c->d_red, c->d_count, out3); dw_note_launch();
+  const int vec = ((((uintptr_t)a) | ((uintptr_t)b)) % 16) == 0;
+  dot_kernel<T><<<RGRID, RB, 0, s>>>(a, b, n, vec, c->d_red, c->d_count, out3); dw_note_launch();
   return DW_OK;
 }
 

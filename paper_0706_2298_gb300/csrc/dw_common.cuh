@@ -267,6 +267,11 @@ struct dw_ctx {
   void* clovinv[2] = {nullptr, nullptr};
   void* sap_r[2] = {nullptr, nullptr};    // SAP residual workspace
   void* sap_d[2] = {nullptr, nullptr};    // SAP last-correction workspace
+  int sap_cap = 1;                        // right-hand sides the FP32 SAP workspace holds
+  int tune_rgroup = 3;                    // right-hand sides per pass of the multi-RHS D (autotuned)
+  int tune_sap_staged = 1;                // 1: staged FP32 Schwarz kernel, 0: generic kernel (autotuned)
+  void* graph_cache = nullptr;            // captured M_sap launch sequences (dw_sap.cu)
+  cudaStream_t cap_stream = nullptr;      // stream used only for graph capture
   double* d_red = nullptr;                // reduction scratch
   unsigned* d_count = nullptr;
   double* h_red = nullptr;                // pinned host mirror
@@ -312,7 +317,13 @@ template <typename T> void blas_lincomb(const T* const* vs, int k, const double*
 
 // dirac / sap entry points used by the solver ---------------------------------------
 template <typename T> void dirac_full(dw_ctx* c, const T* in, T* out, cudaStream_t s);
+// nrhs fields stored consecutively; rgroup right-hand sides share one pass over the links
+template <typename T> void dirac_mrhs(dw_ctx* c, const T* in, T* out, int nrhs, int rgroup, cudaStream_t s);
 template <typename T> int sap_apply(dw_ctx* c, int ncy, int nmr, const T* rho, T* xi, cudaStream_t s);
+int sap_apply_mrhs(dw_ctx* c, int ncy, int nmr, const float* rho, float* xi, int nrhs, cudaStream_t s);
+// same, replayed from a captured CUDA graph after the first call for a (rho, xi, nrhs, ncy, nmr) key
+int sap_apply_mrhs_graph(dw_ctx* c, int ncy, int nmr, const float* rho, float* xi, int nrhs, cudaStream_t s);
+void sap_graphs_free(dw_ctx* c);
 
 // ---------------------------------------------------------------- hopping term
 // acc += sign * (1 - gamma_mu) U_mu(x) psi(x+mu) + sign * (1 + gamma_mu) U_mu(x-mu)^+ psi(x-mu)

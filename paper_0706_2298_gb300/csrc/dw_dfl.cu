@@ -54,6 +54,9 @@ struct dfl_ctx {
   std::vector<cd> Atil_inv;                            // Ns x Ns row-major
   double* Ainv64 = nullptr; float* Ainv32 = nullptr;   // device copies of A~^{-1}
   int coop_grid = 0;                                   // CTAs of the cooperative little solver (0: not possible)
+  int defer_slot = -1;                                 // >= 0: write results to coop_out[2*slot], no host sync
+  double* ref64 = nullptr;                             // refinement work: 3 FP64 little vectors
+  float* ref32 = nullptr;                              //                  2 FP32 little vectors
   double* coop_partial = nullptr;                      // [coop_grid][64]
   double* coop_out = nullptr;                          // iterations, relative residual
   // work vectors (little GCR)
@@ -205,11 +208,16 @@ __global__ void quantize_kernel(size_t V, int Ns, double* b64, uint4* b16) {
 template <typename T>
 __global__ void __launch_bounds__(128) restrict_kernel(Geom g, const int* __restrict__ sub, int nsub, int Ns,
                                                        const double* b64, const uint4* b16,
-                                                       const T* __restrict__ psi, T* __restrict__ c) {
+                                                       const T* __restrict__ psi0, T* __restrict__ c0, int nrhs,
+                                                       size_t fstride, size_t cstride) {
   __shared__ double sh[2][NSMAX][4];
   const int L = blockIdx.x;
   const size_t V = g.V;
   const int nsite = nsub * g.svol;
+  // the right-hand sides of a batch are handled by the same CTA so the block's basis stays in L2
+  for (int rhs = 0; rhs < nrhs; ++rhs) {
+  const T* psi = psi0 + (size_t)rhs * fstride;
+  T* c = c0 + (size_t)rhs * cstride;
   cplx<T> acc[NSMAX];
 #pragma unroll
   for (int k = 0; k < NSMAX; ++k) acc[k] = {T(0), T(0)};
@@ -247,17 +255,23 @@ __global__ void __launch_bounds__(128) restrict_kernel(Geom g, const int* __rest
     c[2 * ((size_t)L * Ns + k)] = (T)re;
     c[2 * ((size_t)L * Ns + k) + 1] = (T)im;
   }
+  __syncthreads();
+  }
 }
 
 // psi = mode 0: Phi c ; 1: psi + Phi c ; 2: psi - Phi c
 template <typename T>
 __global__ void __launch_bounds__(128) prolong_kernel(Geom g, const int* __restrict__ sap2dfl, int Ns,
                                                       const double* b64, const uint4* b16,
-                                                      const T* __restrict__ c, T* psi, int mode) {
+                                                      const T* __restrict__ c0, T* psi0, int mode, int nrhs,
+                                                      size_t fstride, size_t cstride) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= g.V) return;
   const size_t V = g.V;
   const int L = __ldg(sap2dfl + (int)(i >> g.lsvol));
+  for (int rhs = 0; rhs < nrhs; ++rhs) {
+  const T* c = c0 + (size_t)rhs * cstride;
+  T* psi = psi0 + (size_t)rhs * fstride;
   cplx<T> out[12], f[12];
   if (mode == 0) {
 #pragma unroll
@@ -274,6 +288,7 @@ __global__ void __launch_bounds__(128) prolong_kernel(Geom g, const int* __restr
     for (int j = 0; j < 12; ++j) out[j] += ck * f[j];
   }
   store_site<T, 12>(psi, V, i, out);
+  }
 }
 
 // ------------------------------------------------------------------ little operator assembly (A.1), FP64
@@ -454,51 +469,80 @@ __global__ void neighbour_products_kernel(int Nb, int Ns, const double* __restri
 }
 
 // ------------------------------------------------------------------ little vector kernels
-// out[i] = base_coef * base[i] - sum_d M[blk_i][d] src[lnb[i][d]]   (one warp per block, lane = row)
-// base may be null (then the first term is absent).  M column-major: M[((L*8+d)*Ns + col)*Ns + row].
-template <typename T>
+// acc(lane) += sum_col m[col*Ns + lane] * sv[col] for lane < Ns.  The source vector is read
+// once (one element per lane) and broadcast by warp shuffles; with NS fixed at compile time the
+// column loop is unrolled so the coalesced matrix loads are all in flight together.
+template <typename T, int NS>
+DW_D cplx<T> warp_mv(const cplx<T>* __restrict__ m, const cplx<T>* __restrict__ sv, int Ns, int lane,
+                     cplx<T> acc) {
+  const int n = NS ? NS : Ns;
+  const cplx<T> x = lane < n ? sv[lane] : cplx<T>{T(0), T(0)};
+  if (NS) {
+#pragma unroll
+    for (int col = 0; col < (NS ? NS : 1); ++col) {
+      cplx<T> xc = {__shfl_sync(0xffffffffu, x.re, col), __shfl_sync(0xffffffffu, x.im, col)};
+      if (lane < NS) acc += m[(size_t)col * NS + lane] * xc;
+    }
+  } else {
+    for (int col = 0; col < n; ++col) {
+      cplx<T> xc = {__shfl_sync(0xffffffffu, x.re, col), __shfl_sync(0xffffffffu, x.im, col)};
+      if (lane < n) acc += m[(size_t)col * n + lane] * xc;
+    }
+  }
+  return acc;
+}
+
+// out[i] = base[i] - sum_d M[blk_i][d] src[lnb[i][d]]   (one warp per block row, lane = row;
+// base may be null).  M column-major: M[((L*8+d)*Ns + col)*Ns + row].
+template <typename T, int NS>
 __global__ void little_hop_kernel(int n, int Ns, const int* __restrict__ list, const int* __restrict__ lnb,
                                   const T* __restrict__ M, const T* __restrict__ src, const T* base, T* out) {
-  int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (wid >= n) return;
+  const int ns = NS ? NS : Ns;
   const int L = __ldg(list + wid);
   const cplx<T>* Mc = reinterpret_cast<const cplx<T>*>(M);
   const cplx<T>* S = reinterpret_cast<const cplx<T>*>(src);
   cplx<T> acc = {T(0), T(0)};
+#pragma unroll 2
   for (int d = 0; d < 8; ++d) {
-    int j = __ldg(lnb + wid * 8 + d);
-    const cplx<T>* m = Mc + ((size_t)L * 8 + d) * Ns * Ns;
-    const cplx<T>* sv = S + (size_t)j * Ns;
-    for (int col = 0; col < Ns; ++col) {
-      cplx<T> v = sv[col];
-      if (lane < Ns) acc += m[(size_t)col * Ns + lane] * v;
-    }
+    const int j = __ldg(lnb + wid * 8 + d);
+    acc = warp_mv<T, NS>(Mc + ((size_t)L * 8 + d) * ns * ns, S + (size_t)j * ns, ns, lane, acc);
   }
-  if (lane < Ns) {
+  if (lane < ns) {
     cplx<T>* O = reinterpret_cast<cplx<T>*>(out);
-    cplx<T> b = base ? reinterpret_cast<const cplx<T>*>(base)[(size_t)wid * Ns + lane] : cplx<T>{T(0), T(0)};
-    O[(size_t)wid * Ns + lane] = b - acc;
+    cplx<T> b = base ? reinterpret_cast<const cplx<T>*>(base)[(size_t)wid * ns + lane] : cplx<T>{T(0), T(0)};
+    O[(size_t)wid * ns + lane] = b - acc;
   }
 }
 
 // out[i] = Binv[blk_i] * src[i]  (compact parity list vectors)
-template <typename T>
+template <typename T, int NS>
 __global__ void little_bdiag_kernel(int n, int Ns, const int* __restrict__ list, const T* __restrict__ Binv,
                                     const T* __restrict__ src, T* out) {
-  int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (wid >= n) return;
+  const int ns = NS ? NS : Ns;
   const int L = __ldg(list + wid);
-  const cplx<T>* m = reinterpret_cast<const cplx<T>*>(Binv) + (size_t)L * Ns * Ns;
-  const cplx<T>* sv = reinterpret_cast<const cplx<T>*>(src) + (size_t)wid * Ns;
-  cplx<T> acc = {T(0), T(0)};
-  for (int col = 0; col < Ns; ++col) {
-    cplx<T> v = sv[col];
-    if (lane < Ns) acc += m[(size_t)col * Ns + lane] * v;
-  }
-  if (lane < Ns) reinterpret_cast<cplx<T>*>(out)[(size_t)wid * Ns + lane] = acc;
+  cplx<T> acc = warp_mv<T, NS>(reinterpret_cast<const cplx<T>*>(Binv) + (size_t)L * ns * ns,
+                               reinterpret_cast<const cplx<T>*>(src) + (size_t)wid * ns, ns, lane,
+                               cplx<T>{T(0), T(0)});
+  if (lane < ns) reinterpret_cast<cplx<T>*>(out)[(size_t)wid * ns + lane] = acc;
 }
+
+// run CALL with a compile-time NSV for the common subspace sizes (0 = runtime size)
+#define NS_DISPATCH(NSRT, CALL)                                   \
+  switch (NSRT) {                                                 \
+    case 8: { constexpr int NSV = 8; CALL; } break;               \
+    case 12: { constexpr int NSV = 12; CALL; } break;             \
+    case 16: { constexpr int NSV = 16; CALL; } break;             \
+    case 20: { constexpr int NSV = 20; CALL; } break;             \
+    case 24: { constexpr int NSV = 24; CALL; } break;             \
+    case 32: { constexpr int NSV = 32; CALL; } break;             \
+    default: { constexpr int NSV = 0; CALL; } break;              \
+  }
 
 // gather a parity part of a full little vector ([Nb][Ns]) into compact order / scatter back
 template <typename Tin, typename Tout>
@@ -577,8 +621,11 @@ struct CoopShared {
   int phase;
 };
 
-// sum nv per-thread values over the grid; result in sh.res (all CTAs)
-DW_D void coop_reduce(cg::grid_group& grid, CoopShared& sh, double* acc, int nv, double* partial_base) {
+// sum nv per-thread values over the grid; result in sh.res (all CTAs).  After the barrier each CTA
+// copies the partials into shared memory with all threads loading in parallel, then warp w adds the
+// partials of values j = w, w + 8, ... in a fixed tree: identical, deterministic sums in every CTA.
+DW_D void coop_reduce(cg::grid_group& grid, CoopShared& sh, double* acc, int nv, double* partial_base,
+                      double* stage) {
   // two partial buffers used alternately: a CTA that runs ahead into the next reduction
   // cannot overwrite partials another CTA is still adding up
   double* partial = partial_base + (size_t)(sh.phase & 1) * gridDim.x * COOP_NV;
@@ -596,10 +643,18 @@ DW_D void coop_reduce(cg::grid_group& grid, CoopShared& sh, double* acc, int nv,
     partial[blockIdx.x * COOP_NV + threadIdx.x] = x;
   }
   grid.sync();
-  if (threadIdx.x < nv) {
+  const int G = gridDim.x;
+  for (int idx = threadIdx.x; idx < G * nv; idx += COOP_THREADS) {
+    const int q = idx / nv, j = idx - q * nv;
+    stage[j * G + q] = __ldcg(partial + q * COOP_NV + j);
+  }
+  __syncthreads();
+  for (int j = w; j < nv; j += COOP_THREADS / 32) {
     double x = 0;
-    for (unsigned q = 0; q < gridDim.x; ++q) x += partial[q * COOP_NV + threadIdx.x];
-    sh.res[threadIdx.x] = x;
+    for (int q = lane; q < G; q += 32) x += stage[j * G + q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) sh.res[j] = x;
   }
   __syncthreads();
   if (threadIdx.x == 0) sh.phase += 1;
@@ -607,67 +662,44 @@ DW_D void coop_reduce(cg::grid_group& grid, CoopShared& sh, double* acc, int nv,
 }
 
 // out[r] = base[r] - sum_d M[list[r]][d] src[lnb[r][d]]  (warp per block row; base may be null)
-template <typename T>
+template <typename T, int NS>
 DW_D void coop_hop(int nrow, int Ns, const int* list, const int* lnb, const T* M, const cplx<T>* src,
-                   const cplx<T>* base, cplx<T>* out) {
+                   const cplx<T>* base, cplx<T>* out, T out_sign) {
   const int lane = threadIdx.x & 31;
   const int nw = gridDim.x * (COOP_THREADS / 32);
+  const int ns = NS ? NS : Ns;
   const cplx<T>* Mc = reinterpret_cast<const cplx<T>*>(M);
   for (int r = blockIdx.x * (COOP_THREADS / 32) + (threadIdx.x >> 5); r < nrow; r += nw) {
     const int L = list[r];
     cplx<T> acc = {T(0), T(0)};
+#pragma unroll 2
     for (int d = 0; d < 8; ++d) {
       const int j = lnb[r * 8 + d];
-      const cplx<T>* m = Mc + ((size_t)L * 8 + d) * Ns * Ns;
-      const cplx<T>* sv = src + (size_t)j * Ns;
-      for (int col = 0; col < Ns; ++col) {
-        cplx<T> x = sv[col];
-        if (lane < Ns) acc += m[(size_t)col * Ns + lane] * x;
-      }
+      acc = warp_mv<T, NS>(Mc + ((size_t)L * 8 + d) * ns * ns, src + (size_t)j * ns, ns, lane, acc);
     }
-    if (lane < Ns) {
-      cplx<T> bse = base ? base[(size_t)r * Ns + lane] : cplx<T>{T(0), T(0)};
-      out[(size_t)r * Ns + lane] = bse - acc;
+    if (lane < ns) {
+      cplx<T> bse = base ? base[(size_t)r * ns + lane] : cplx<T>{T(0), T(0)};
+      out[(size_t)r * ns + lane] = bse + out_sign * acc;
     }
   }
 }
 
 // y = B^ x = x - M_eo (M_oe x); ends with a grid barrier
-template <typename T>
+template <typename T, int NS>
 DW_D void coop_bhat(cg::grid_group& grid, const CoopArgs<T>& a, const cplx<T>* x, cplx<T>* tmpo, cplx<T>* y) {
-  // tmpo = -M_oe x ; y = x + M_eo tmpo... written as y = x - M_eo(M_oe x) via two signed hops
-  coop_hop<T>(a.No, a.Ns, a.list_o, a.lnb_o, a.M, x, nullptr, tmpo);     // tmpo = -M_oe x
+  coop_hop<T, NS>(a.No, a.Ns, a.list_o, a.lnb_o, a.M, x, nullptr, tmpo, T(1));    // tmpo = M_oe x
   grid.sync();
-  // y = x - M_eo (-tmpo) = x + M_eo tmpo : use base = x and negate inside by hopping on tmpo, then fix sign
-  {
-    const int lane = threadIdx.x & 31;
-    const int nw = gridDim.x * (COOP_THREADS / 32);
-    const cplx<T>* Mc = reinterpret_cast<const cplx<T>*>(a.M);
-    for (int r = blockIdx.x * (COOP_THREADS / 32) + (threadIdx.x >> 5); r < a.Ne; r += nw) {
-      const int L = a.list_e[r];
-      cplx<T> acc = {T(0), T(0)};
-      for (int d = 0; d < 8; ++d) {
-        const int j = a.lnb_e[r * 8 + d];
-        const cplx<T>* m = Mc + ((size_t)L * 8 + d) * a.Ns * a.Ns;
-        const cplx<T>* sv = tmpo + (size_t)j * a.Ns;
-        for (int col = 0; col < a.Ns; ++col) {
-          cplx<T> xv = sv[col];
-          if (lane < a.Ns) acc += m[(size_t)col * a.Ns + lane] * xv;
-        }
-      }
-      if (lane < a.Ns) y[(size_t)r * a.Ns + lane] = x[(size_t)r * a.Ns + lane] + acc;
-    }
-  }
+  coop_hop<T, NS>(a.Ne, a.Ns, a.list_e, a.lnb_e, a.M, tmpo, x, y, T(-1));        // y = x - M_eo tmpo
   grid.sync();
 }
 
 // u -= Bg A~^{-1} g^+ u  (P~_L, in place; elementwise part by the owning thread, no trailing barrier)
-template <typename T>
+template <typename T, int NS>
 DW_D void coop_PL(cg::grid_group& grid, CoopShared& sh, const CoopArgs<T>& a, cplx<T>* u, double* acc,
-                  const cplx<T>* gsrc, const cplx<T>* bgsrc, bool subtract_from_u) {
+                  const cplx<T>* gsrc, const cplx<T>* bgsrc, bool subtract_from_u, double* stage) {
   const size_t n = (size_t)a.Ne * a.Ns;
   const size_t tid = blockIdx.x * (size_t)COOP_THREADS + threadIdx.x, nth = (size_t)gridDim.x * COOP_THREADS;
-  const int Ns = a.Ns;
+  const int Ns = NS ? NS : a.Ns;
   for (int j = 0; j < 2 * Ns; ++j) acc[j] = 0;
   for (size_t i = tid; i < n; i += nth) {
     cplx<T> x = u[i];
@@ -677,7 +709,7 @@ DW_D void coop_PL(cg::grid_group& grid, CoopShared& sh, const CoopArgs<T>& a, cp
       acc[2 * l + 1] += (double)gl.re * x.im - (double)gl.im * x.re;
     }
   }
-  coop_reduce(grid, sh, acc, 2 * Ns, a.partial);
+  coop_reduce(grid, sh, acc, 2 * Ns, a.partial, stage);
   if (threadIdx.x < Ns) {          // z = A~^{-1} y
     const cplx<T>* Ai = reinterpret_cast<const cplx<T>*>(a.Ainv);
     double zr = 0, zi = 0;
@@ -702,10 +734,11 @@ DW_D void coop_PL(cg::grid_group& grid, CoopShared& sh, const CoopArgs<T>& a, cp
   }
 }
 
-template <typename T>
+template <typename T, int NS>
 __global__ void __launch_bounds__(COOP_THREADS) little_gcr_coop_kernel(CoopArgs<T> a) {
   cg::grid_group grid = cg::this_grid();
   __shared__ CoopShared sh;
+  extern __shared__ double stage[];     // [COOP_NV][gridDim]
   if (threadIdx.x == 0) sh.phase = 0;
   __syncthreads();
   double acc[COOP_NV];
@@ -726,7 +759,7 @@ __global__ void __launch_bounds__(COOP_THREADS) little_gcr_coop_kernel(CoopArgs<
 
   // rhsd = P~_L b, rho = rhsd, v = 0
   for (size_t i = tid; i < n; i += nth) rhsd[i] = b[i];
-  if (a.a3) coop_PL<T>(grid, sh, a, rhsd, acc, g, Bg, true);
+  if (a.a3) coop_PL<T, NS>(grid, sh, a, rhsd, acc, g, Bg, true, stage);
   acc[0] = 0;
   for (size_t i = tid; i < n; i += nth) {
     cplx<T> x = rhsd[i];
@@ -734,7 +767,7 @@ __global__ void __launch_bounds__(COOP_THREADS) little_gcr_coop_kernel(CoopArgs<
     v[i] = {T(0), T(0)};
     acc[0] += (double)x.re * x.re + (double)x.im * x.im;
   }
-  coop_reduce(grid, sh, acc, 1, a.partial);
+  coop_reduce(grid, sh, acc, 1, a.partial, stage);
   const double bn = sqrt(sh.res[0]);
   double rn = bn;
   int total = 0;
@@ -745,8 +778,8 @@ __global__ void __launch_bounds__(COOP_THREADS) little_gcr_coop_kernel(CoopArgs<
       cplx<T>* xk = xi(k);
       for (size_t i = tid; i < n; i += nth) xk[i] = rho[i];
       grid.sync();
-      coop_bhat<T>(grid, a, xk, tmpo, ck);
-      if (a.a3) coop_PL<T>(grid, sh, a, ck, acc, g, Bg, true);
+      coop_bhat<T, NS>(grid, a, xk, tmpo, ck);
+      if (a.a3) coop_PL<T, NS>(grid, sh, a, ck, acc, g, Bg, true, stage);
       if (k > 0) {
         for (int j = 0; j < 2 * k; ++j) acc[j] = 0;
         for (size_t i = tid; i < n; i += nth) {
@@ -757,7 +790,7 @@ __global__ void __launch_bounds__(COOP_THREADS) little_gcr_coop_kernel(CoopArgs<
             acc[2 * j + 1] += (double)x.re * y.im - (double)x.im * y.re;
           }
         }
-        coop_reduce(grid, sh, acc, 2 * k, a.partial);
+        coop_reduce(grid, sh, acc, 2 * k, a.partial, stage);
         if (threadIdx.x < 2 * k) sh.bb[threadIdx.x >> 1][2 * k + (threadIdx.x & 1)] = sh.res[threadIdx.x];
         __syncthreads();
         for (size_t i = tid; i < n; i += nth) {
@@ -776,7 +809,7 @@ __global__ void __launch_bounds__(COOP_THREADS) little_gcr_coop_kernel(CoopArgs<
         acc[1] += (double)x.re * y.im - (double)x.im * y.re;
         acc[2] += (double)x.re * x.re + (double)x.im * x.im;
       }
-      coop_reduce(grid, sh, acc, 3, a.partial);
+      coop_reduce(grid, sh, acc, 3, a.partial, stage);
       const double cn = sqrt(sh.res[2]);
       if (!(cn > 0)) break;
       const double ar = sh.res[0] / cn, ai = sh.res[1] / cn;
@@ -791,7 +824,7 @@ __global__ void __launch_bounds__(COOP_THREADS) little_gcr_coop_kernel(CoopArgs<
         rho[i] = y;
         acc[0] += (double)y.re * y.re + (double)y.im * y.im;
       }
-      coop_reduce(grid, sh, acc, 1, a.partial);
+      coop_reduce(grid, sh, acc, 1, a.partial, stage);
       rn = sqrt(sh.res[0]);
       ++total;
       if (rn <= a.tol * bn) { ++k; break; }
@@ -818,23 +851,23 @@ __global__ void __launch_bounds__(COOP_THREADS) little_gcr_coop_kernel(CoopArgs<
     grid.sync();
     if (k == 0) break;
     // true residual of the deflated system
-    coop_bhat<T>(grid, a, v, tmpo, t);
-    if (a.a3) coop_PL<T>(grid, sh, a, t, acc, g, Bg, true);
+    coop_bhat<T, NS>(grid, a, v, tmpo, t);
+    if (a.a3) coop_PL<T, NS>(grid, sh, a, t, acc, g, Bg, true, stage);
     acc[0] = 0;
     for (size_t i = tid; i < n; i += nth) {
       cplx<T> y = rhsd[i] - t[i];
       rho[i] = y;
       acc[0] += (double)y.re * y.re + (double)y.im * y.im;
     }
-    coop_reduce(grid, sh, acc, 1, a.partial);
+    coop_reduce(grid, sh, acc, 1, a.partial, stage);
     rn = sqrt(sh.res[0]);
   }
   if (a.a3) {
     // v = chi + g A~^{-1} g^+ (b - B^ chi)
     grid.sync();
-    coop_bhat<T>(grid, a, v, tmpo, t);
+    coop_bhat<T, NS>(grid, a, v, tmpo, t);
     for (size_t i = tid; i < n; i += nth) t[i] = b[i] - t[i];
-    coop_PL<T>(grid, sh, a, t, acc, g, g, false);   // t += g z  (z from g^+ t); only z is used below
+    coop_PL<T, NS>(grid, sh, a, t, acc, g, g, false, stage);   // t += g z  (z from g^+ t); only z is used below
     // coop_PL updated t, not v: redo the elementwise part on v with the same z
     for (size_t i = tid; i < n; i += nth) {
       cplx<T> x = v[i];
@@ -869,11 +902,13 @@ template <> const double* Bgp<double>(dfl_ctx* d) { return d->Bg64; }
 // B^ v_e = v_e - M_eo (M_oe v_e);  tmp_o: No*Ns complex
 template <typename T>
 static void apply_bhat(dfl_ctx* d, const T* ve, T* tmp_o, T* out, cudaStream_t s) {
-  little_hop_kernel<T><<<warps_grid(d->No), 128, 0, s>>>(d->No, d->Ns, d->d_list[1], d->d_lnb[1], Mp<T>(d), ve,
-                                                        nullptr, tmp_o); dw_note_launch();
+  NS_DISPATCH(d->Ns, (little_hop_kernel<T, NSV><<<warps_grid(d->No), 128, 0, s>>>(
+                                d->No, d->Ns, d->d_list[1], d->d_lnb[1], Mp<T>(d), ve, nullptr, tmp_o)));
+  dw_note_launch();
   // tmp_o = -M_oe v_e; out = v_e - M_eo(M_oe v_e) = v_e + M_eo tmp_o  ->  use base = v_e and src = -tmp
-  little_hop_kernel<T><<<warps_grid(d->Ne), 128, 0, s>>>(d->Ne, d->Ns, d->d_list[0], d->d_lnb[0], Mp<T>(d), tmp_o,
-                                                        nullptr, out); dw_note_launch();
+  NS_DISPATCH(d->Ns, (little_hop_kernel<T, NSV><<<warps_grid(d->Ne), 128, 0, s>>>(
+                                d->Ne, d->Ns, d->d_list[0], d->d_lnb[0], Mp<T>(d), tmp_o, nullptr, out)));
+  dw_note_launch();
   // out = -M_eo tmp_o = M_eo M_oe v_e ; final = v_e - out
   blas_xpby<T>(ve, out, -1.0, 0.0, (size_t)d->Ne * d->Ns, s);
 }
@@ -890,24 +925,38 @@ extern "C" void dfl_destroy(dfl_ctx* d) {
   void* ptrs[] = {d->d_sub, d->d_sap2dfl, d->d_bnb, d->d_list[0], d->d_list[1], d->d_lnb[0], d->d_lnb[1],
                   d->basis64, d->basis16, d->B64, d->Binv64, d->Binv32, d->M64, d->M32, d->g64, d->g32,
                   d->Bg64, d->Bg32, d->lw[0], d->lw[1], d->B32, d->fw[0], d->fw[1], d->Ainv64, d->Ainv32,
-                  d->coop_partial, d->coop_out};
+                  d->coop_partial, d->coop_out, d->ref64, d->ref32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete d;
 }
 
 template <typename T>
-static int restrict_t(dfl_ctx* d, const T* psi, T* c, cudaStream_t s) {
+static int restrict_t(dfl_ctx* d, const T* psi, T* c, cudaStream_t s, int nrhs = 1) {
   restrict_kernel<T><<<d->Nb, 128, 0, s>>>(d->c->g, d->d_sub, d->nsub, d->Ns, d->basis16 ? nullptr : d->basis64,
-                                            d->basis16, psi, c); dw_note_launch();
+                                            d->basis16, psi, c, nrhs, (size_t)d->c->V * 24,
+                                            (size_t)d->N * 2); dw_note_launch();
   return DW_OK;
 }
 template <typename T>
-static int prolong_t(dfl_ctx* d, const T* c, T* psi, int mode, cudaStream_t s) {
+static int prolong_t(dfl_ctx* d, const T* c, T* psi, int mode, cudaStream_t s, int nrhs = 1) {
   unsigned blocks = (unsigned)((d->c->V + 127) / 128);
   prolong_kernel<T><<<blocks, 128, 0, s>>>(d->c->g, d->d_sap2dfl, d->Ns, d->basis16 ? nullptr : d->basis64,
-                                            d->basis16, c, psi, mode); dw_note_launch();
+                                            d->basis16, c, psi, mode, nrhs, (size_t)d->c->V * 24,
+                                            (size_t)d->N * 2); dw_note_launch();
   return DW_OK;
+}
+int dfl_restrict_mrhs_f32(dfl_ctx* d, const float* psi, float* c, int nrhs, cudaStream_t s) {
+  return restrict_t(d, psi, c, s, nrhs);
+}
+int dfl_prolong_mrhs_f32(dfl_ctx* d, const float* c, float* psi, int mode, int nrhs, cudaStream_t s) {
+  return prolong_t(d, c, psi, mode, s, nrhs);
+}
+int dfl_restrict_mrhs_f64(dfl_ctx* d, const double* psi, double* c, int nrhs, cudaStream_t s) {
+  return restrict_t(d, psi, c, s, nrhs);
+}
+int dfl_prolong_mrhs_f64(dfl_ctx* d, const double* c, double* psi, int mode, int nrhs, cudaStream_t s) {
+  return prolong_t(d, c, psi, mode, s, nrhs);
 }
 int dfl_restrict_f32(dfl_ctx* d, const float* psi, float* c, cudaStream_t s) { return restrict_t(d, psi, c, s); }
 int dfl_restrict_f64(dfl_ctx* d, const double* psi, double* c, cudaStream_t s) { return restrict_t(d, psi, c, s); }
@@ -1105,11 +1154,20 @@ static int little_gcr_coop(dfl_ctx* d, const T* b, T* v, double tol, int maxit, 
   a.Ainv = d->a3 ? Ainvp<T>(d) : nullptr; a.b = b; a.v = v;
   a.work = lwork<T>(d, 0);
   a.partial = d->coop_partial;
-  a.out = d->coop_out;
+  a.out = d->coop_out + (d->defer_slot >= 0 ? 2 * d->defer_slot : 0);
   a.tol = tol;
   void* args[] = {&a};
-  DW_CUDA(cudaLaunchCooperativeKernel((void*)little_gcr_coop_kernel<T>, d->coop_grid, COOP_THREADS, args, 0, s));
+  cudaError_t le = cudaSuccess;
+  const size_t dsm = (size_t)COOP_NV * d->coop_grid * sizeof(double);
+  NS_DISPATCH(d->Ns, (le = cudaLaunchCooperativeKernel((void*)little_gcr_coop_kernel<T, NSV>, d->coop_grid,
+                                                       COOP_THREADS, args, dsm, s)));
+  DW_CUDA(le);
   dw_note_launch();
+  if (d->defer_slot >= 0) {   // results collected later by little_collect
+    *iters = 0;
+    *relres = 0;
+    return DW_OK;
+  }
   double h[2];
   int rc = sync_read(d->c, d->coop_out, 2, h, s);
   if (rc) return rc;
@@ -1168,24 +1226,21 @@ static const T* Bp(dfl_ctx* d);
 template <> const float* Bp<float>(dfl_ctx* d) { return d->B32; }
 template <> const double* Bp<double>(dfl_ctx* d) { return d->B64; }
 
-template <typename T>
+template <typename T, int NS>
 __global__ void little_full_t_kernel(int Nb, int Ns, const int* __restrict__ bnb, const T* __restrict__ B,
                                      const T* __restrict__ v, T* w) {
-  int L = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
+  const int L = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (L >= Nb) return;
+  const int ns = NS ? NS : Ns;
   const cplx<T>* Bc = reinterpret_cast<const cplx<T>*>(B);
   const cplx<T>* vc = reinterpret_cast<const cplx<T>*>(v);
   cplx<T> acc = {T(0), T(0)};
   for (int part = 0; part < 9; ++part) {
-    int src = part == 0 ? L : bnb[L * 8 + part - 1];
-    const cplx<T>* m = Bc + ((size_t)L * 9 + part) * Ns * Ns;
-    for (int col = 0; col < Ns; ++col) {
-      cplx<T> x = vc[(size_t)src * Ns + col];
-      if (lane < Ns) acc += m[(size_t)col * Ns + lane] * x;
-    }
+    const int src = part == 0 ? L : bnb[L * 8 + part - 1];
+    acc = warp_mv<T, NS>(Bc + ((size_t)L * 9 + part) * ns * ns, vc + (size_t)src * ns, ns, lane, acc);
   }
-  if (lane < Ns) reinterpret_cast<cplx<T>*>(w)[(size_t)L * Ns + lane] = acc;
+  if (lane < ns) reinterpret_cast<cplx<T>*>(w)[(size_t)L * ns + lane] = acc;
 }
 
 template <typename T>
@@ -1195,7 +1250,9 @@ static int little_full_solve(dfl_ctx* d, const T* w, T* v, double tol, int maxit
   const size_t n = (size_t)d->N;
   if (!d->fw[P]) DW_CUDA(cudaMalloc(&d->fw[P], (size_t)(2 * nkv + 3) * n * 2 * sizeof(T)));
   auto op = [&](const T* x, T* y) -> int {
-    little_full_t_kernel<T><<<warps_grid(d->Nb), 128, 0, s>>>(d->Nb, d->Ns, d->d_bnb, Bp<T>(d), x, y); dw_note_launch();
+    NS_DISPATCH(d->Ns, (little_full_t_kernel<T, NSV><<<warps_grid(d->Nb), 128, 0, s>>>(d->Nb, d->Ns, d->d_bnb,
+                                                                                      Bp<T>(d), x, y)));
+    dw_note_launch();
     return DW_OK;
   };
   return gcr_small<T>(d->c, op, w, v, n, (T*)d->fw[P], tol, maxit, nkv, iters, relres, s);
@@ -1218,14 +1275,20 @@ static int little_solve_t(dfl_ctx* d, const T* w, T* v, double tol, int maxit, i
   little_gather_kernel<T, T><<<ge, 256, 0, s>>>(d->Ne, Ns, d->d_list[0], w, we); dw_note_launch();
   little_gather_kernel<T, T><<<go, 256, 0, s>>>(d->No, Ns, d->d_list[1], w, wo); dw_note_launch();
   // yo = B_oo^{-1} w_o ; wt = B_ee^{-1} w_e - M_eo yo
-  little_bdiag_kernel<T><<<warps_grid(d->No), 128, 0, s>>>(d->No, Ns, d->d_list[1], Binvp<T>(d), wo, yo); dw_note_launch();
-  little_bdiag_kernel<T><<<warps_grid(d->Ne), 128, 0, s>>>(d->Ne, Ns, d->d_list[0], Binvp<T>(d), we, wt); dw_note_launch();
-  little_hop_kernel<T><<<warps_grid(d->Ne), 128, 0, s>>>(d->Ne, Ns, d->d_list[0], d->d_lnb[0], Mp<T>(d), yo, wt, we); dw_note_launch();
+  NS_DISPATCH(Ns, (little_bdiag_kernel<T, NSV><<<warps_grid(d->No), 128, 0, s>>>(d->No, Ns, d->d_list[1],
+                                                                             Binvp<T>(d), wo, yo)));
+  NS_DISPATCH(Ns, (little_bdiag_kernel<T, NSV><<<warps_grid(d->Ne), 128, 0, s>>>(d->Ne, Ns, d->d_list[0],
+                                                                             Binvp<T>(d), we, wt)));
+  NS_DISPATCH(Ns, (little_hop_kernel<T, NSV><<<warps_grid(d->Ne), 128, 0, s>>>(d->Ne, Ns, d->d_list[0],
+                                                                           d->d_lnb[0], Mp<T>(d), yo, wt, we)));
+  dw_note_launch(); dw_note_launch(); dw_note_launch();
   // we now holds w~_e ; solve B^ v_e = w~_e into wt
   rc = little_gcr<T>(d, we, wt, tol, maxit, nkv, iters, relres, s);
   if (rc < 0) return rc;
   // v_o = yo - M_oe v_e  -> into wo
-  little_hop_kernel<T><<<warps_grid(d->No), 128, 0, s>>>(d->No, Ns, d->d_list[1], d->d_lnb[1], Mp<T>(d), wt, yo, wo); dw_note_launch();
+  NS_DISPATCH(Ns, (little_hop_kernel<T, NSV><<<warps_grid(d->No), 128, 0, s>>>(d->No, Ns, d->d_list[1],
+                                                                           d->d_lnb[1], Mp<T>(d), wt, yo, wo)));
+  dw_note_launch();
   little_scatter_kernel<T, T><<<ge, 256, 0, s>>>(d->Ne, Ns, d->d_list[0], wt, v); dw_note_launch();
   little_scatter_kernel<T, T><<<go, 256, 0, s>>>(d->No, Ns, d->d_list[1], wo, v); dw_note_launch();
   DW_CUDA(cudaGetLastError());
@@ -1240,6 +1303,78 @@ int little_solve_f64(dfl_ctx* d, const double* w, double* v, double tol, int max
   return little_solve_t(d, w, v, tol, maxit, nkv, it, rr, s);
 }
 int dfl_nlittle(const dfl_ctx* d) { return d->N; }
+// FP64-accurate solution of A v = w (little operator (3.2)/(A.1)) by mixed-precision iterative
+// refinement: FP32 even-odd deflated GCR solves for the corrections, FP64 residuals w - A v with the
+// FP64 operator.  Used for the restart corrections of the mixed-precision solver, so every little
+// GCR iteration runs in FP32 while the correction reaches the outer tolerance.
+int little_solve_refined(dfl_ctx* d, const double* w, double* v, double tol, int maxit, int nkv, int* iters,
+                         double* relres, cudaStream_t s) {
+  const size_t N = d->N;
+  if (!d->ref64) DW_CUDA(cudaMalloc(&d->ref64, 3 * N * 2 * sizeof(double)));
+  if (!d->ref32) DW_CUDA(cudaMalloc(&d->ref32, 2 * N * 2 * sizeof(float)));
+  double* r = d->ref64;
+  double* t = r + 2 * N;
+  float* w32 = d->ref32;
+  float* v32 = w32 + 2 * N;
+  double* dres = d->c->d_red + 65536 + 2048;
+  double h[3];
+  int rc;
+  DW_CUDA(cudaMemsetAsync(v, 0, N * 2 * sizeof(double), s));
+  DW_CUDA(cudaMemcpyAsync(r, w, N * 2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  blas_dot<double>(d->c, w, w, N, dres, s);
+  if ((rc = sync_read(d->c, dres, 3, h, s))) return rc;
+  const double wn = sqrt(h[2]);
+  *iters = 0;
+  *relres = 0;
+  if (wn == 0.0) return DW_OK;
+  double rn = wn;
+  for (int step = 0; step < 8 && rn > tol * wn && *iters < maxit; ++step) {
+    blas_convert<double, float>(r, w32, 1.0 / rn, N, s);
+    int it = 0;
+    double rr = 0;
+    rc = little_solve_t<float>(d, w32, v32, 1e-6, maxit - *iters, nkv, &it, &rr, s);
+    if (rc < 0) return rc;
+    *iters += it;
+    blas_convert<float, double>(v32, t, rn, N, s);
+    blas_axpy<double>(t, v, 1.0, 0.0, N, s);
+    NS_DISPATCH(d->Ns, (little_full_t_kernel<double, NSV><<<warps_grid(d->Nb), 128, 0, s>>>(
+                            d->Nb, d->Ns, d->d_bnb, d->B64, v, t)));
+    dw_note_launch();
+    DW_CUDA(cudaMemcpyAsync(r, w, N * 2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    blas_axpy<double>(t, r, -1.0, 0.0, N, s);
+    blas_dot<double>(d->c, r, r, N, dres, s);
+    if ((rc = sync_read(d->c, dres, 3, h, s))) return rc;
+    rn = sqrt(h[2]);
+  }
+  *relres = rn / wn;
+  return rn <= tol * wn ? DW_OK : DW_ENOTCONV;
+}
+
+// nrhs FP32 little solves queued back to back; one host synchronisation collects the counts.
+// Uses the cooperative solver when available (otherwise each solve synchronises on its own).
+int little_solve_batch_f32(dfl_ctx* d, const float* w, float* v, const double* tol, const int* use, int maxit,
+                           int nkv, int nrhs, int* iters, double* relres, cudaStream_t s) {
+  const size_t N2 = (size_t)d->N * 2;
+  const bool coop = d->coop_grid > 0 && nkv <= COOP_NKV && coop_enabled() && !d->illcond && nrhs <= 64;
+  for (int r = 0; r < nrhs; ++r) {
+    iters[r] = 0;
+    relres[r] = 0;
+    if (!use[r]) continue;
+    d->defer_slot = coop ? r : -1;
+    int rc = little_solve_t<float>(d, w + r * N2, v + r * N2, tol[r], maxit, nkv, iters + r, relres + r, s);
+    d->defer_slot = -1;
+    if (rc < 0) return rc;
+  }
+  if (coop) {
+    std::vector<double> h(2 * nrhs);
+    int rc = sync_read(d->c, d->coop_out, 2 * nrhs, h.data(), s);
+    if (rc) return rc;
+    for (int r = 0; r < nrhs; ++r)
+      if (use[r]) { iters[r] = (int)h[2 * r]; relres[r] = h[2 * r + 1]; }
+  }
+  return DW_OK;
+}
+
 
 extern "C" int little_dirac_solve(dfl_ctx* d, int prec, const void* w, void* v, double tol, int maxit, int* iters,
                                   double* relres, void* stream) {
@@ -1405,7 +1540,8 @@ static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_c
         field_convert<float, double>((const float*)work + (size_t)l * 24 * V, f64, 1.0, V, s);
         src = f64;
       }
-      restrict_kernel<double><<<d->Nb, 128, 0, s>>>(g, d->d_sub, d->nsub, Ns, d->basis64, nullptr, src, cfull); dw_note_launch();
+      restrict_kernel<double><<<d->Nb, 128, 0, s>>>(g, d->d_sub, d->nsub, Ns, d->basis64, nullptr, src, cfull, 1,
+                                                    0, 0); dw_note_launch();
       DW_CUDA(cudaMemcpyAsync(hc.data(), cfull, hc.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
       DW_CUDA(cudaStreamSynchronize(s));
       for (int i = 0; i < d->Ne; ++i)
@@ -1489,12 +1625,19 @@ static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_c
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, little_gcr_coop_kernel<float>, COOP_THREADS, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, little_gcr_coop_kernel<double>, COOP_THREADS, 0);
+    const size_t dsm = (size_t)COOP_NV * sms * sizeof(double);
+    NS_DISPATCH(Ns, (cudaFuncSetAttribute(little_gcr_coop_kernel<float, NSV>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm)));
+    NS_DISPATCH(Ns, (cudaFuncSetAttribute(little_gcr_coop_kernel<double, NSV>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm)));
+    NS_DISPATCH(Ns, (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, little_gcr_coop_kernel<float, NSV>,
+                                                                   COOP_THREADS, dsm)));
+    NS_DISPATCH(Ns, (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, little_gcr_coop_kernel<double, NSV>,
+                                                                   COOP_THREADS, dsm)));
     d->coop_grid = (coop && b32 > 0 && b64 > 0 && Ns <= 32) ? sms : 0;
     if (d->coop_grid) {
       DW_CUDA(cudaMalloc(&d->coop_partial, (size_t)2 * d->coop_grid * COOP_NV * sizeof(double)));
-      DW_CUDA(cudaMalloc(&d->coop_out, 4 * sizeof(double)));
+      DW_CUDA(cudaMalloc(&d->coop_out, 2 * 64 * sizeof(double)));
     }
     if ((rc = ensure_little_work(d, DW_F64, COOP_NKV))) return rc;
   }

@@ -10,7 +10,7 @@
 #include "dw_common.cuh"
 
 template <typename T>
-__global__ void __launch_bounds__(128) dirac_full_kernel(Geom g, const T* __restrict__ links,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) dirac_full_kernel(Geom g, const T* __restrict__ links,
                                                          const T* __restrict__ clov, const T* __restrict__ in,
                                                          T* __restrict__ out) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -78,6 +78,78 @@ __global__ void __launch_bounds__(128) schur_even_kernel(Geom g, const T* __rest
   store_site<T, 12>(out, V, site_index(g, s.b, 1, s.h), y);
 }
 
+// Multi-RHS D: one thread per site applies D to all right-hand sides (fields stored one after the
+// other, stride fstride reals).  RHS are processed R at a time; the links and clover of the site are
+// loaded for each group but come from L1/L2 after the first, so HBM sees them once per site.
+template <typename T, int R>
+__global__ void __launch_bounds__(128) dirac_mrhs_kernel(Geom g, const T* __restrict__ links,
+                                                         const T* __restrict__ clov, const T* __restrict__ in,
+                                                         T* __restrict__ out, int nrhs, size_t fstride) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= g.V) return;
+  const size_t V = g.V;
+  SiteRef s = decode(g, i);
+  for (int r0 = 0; r0 < nrhs; r0 += R) {
+    const int nr = nrhs - r0 < R ? nrhs - r0 : R;
+    cplx<T> acc[R][12];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc[r][k] = {T(0), T(0)};
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      const int mu = d >> 1;
+      bool cr;
+      const long long j = neighbour(g, s, d, &cr);
+      const T sg = time_wrap(g, s, d) ? T(-1) : T(1);
+      SU3<T> U;
+      load_link(links, V, mu, (d & 1) ? j : i, U);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (r < nr) {
+          cplx<T> p[12];
+          load_site<T, 12>(in + (size_t)(r0 + r) * fstride, V, j, p);
+          switch (d) {
+            case 0: hop_acc<0, -1, false>(acc[r], p, U, sg); break;
+            case 1: hop_acc<0, +1, true>(acc[r], p, U, sg); break;
+            case 2: hop_acc<1, -1, false>(acc[r], p, U, sg); break;
+            case 3: hop_acc<1, +1, true>(acc[r], p, U, sg); break;
+            case 4: hop_acc<2, -1, false>(acc[r], p, U, sg); break;
+            case 5: hop_acc<2, +1, true>(acc[r], p, U, sg); break;
+            case 6: hop_acc<3, -1, false>(acc[r], p, U, sg); break;
+            default: hop_acc<3, +1, true>(acc[r], p, U, sg); break;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (r < nr) {
+        cplx<T> psi[12], y[12];
+        load_site<T, 12>(in + (size_t)(r0 + r) * fstride, V, i, psi);
+        clover_apply(clov, V, i, psi, y);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) y[k] -= T(0.5) * acc[r][k];
+        store_site<T, 12>(out + (size_t)(r0 + r) * fstride, V, i, y);
+      }
+    }
+  }
+}
+
+template <typename T>
+void dirac_mrhs(dw_ctx* c, const T* in, T* out, int nrhs, int rgroup, cudaStream_t st) {
+  constexpr int P = prec_of<T>();
+  unsigned blocks = (unsigned)((c->V + 127) / 128);
+  const size_t fs = (size_t)c->V * 24;
+  const T* L = (const T*)c->links[P];
+  const T* K = (const T*)c->clov[P];
+  if (rgroup >= 3) { dirac_mrhs_kernel<T, 3><<<blocks, 128, 0, st>>>(c->g, L, K, in, out, nrhs, fs); dw_note_launch(); }
+  else if (rgroup == 2) { dirac_mrhs_kernel<T, 2><<<blocks, 128, 0, st>>>(c->g, L, K, in, out, nrhs, fs); dw_note_launch(); }
+  else { dirac_mrhs_kernel<T, 1><<<blocks, 128, 0, st>>>(c->g, L, K, in, out, nrhs, fs); dw_note_launch(); }
+}
+template void dirac_mrhs<float>(dw_ctx*, const float*, float*, int, int, cudaStream_t);
+template void dirac_mrhs<double>(dw_ctx*, const double*, double*, int, int, cudaStream_t);
+
 template <typename T>
 void dirac_full(dw_ctx* c, const T* in, T* out, cudaStream_t st) {
   constexpr int P = prec_of<T>();
@@ -106,6 +178,12 @@ extern "C" int dw_apply(dw_ctx* c, int prec, int op, int nrhs, const void* in, v
   }
   cudaStream_t st = (cudaStream_t)stream;
   size_t n = (size_t)c->V * 24;
+  if (nrhs > 1 && op == DW_OP_FULL) {   // multi-RHS kernel: links and clover read once per site
+    if (prec == DW_F64) dirac_mrhs(c, (const double*)in, (double*)out, nrhs, c->tune_rgroup, st);
+    else dirac_mrhs(c, (const float*)in, (float*)out, nrhs, c->tune_rgroup, st);
+    DW_CUDA(cudaGetLastError());
+    return DW_OK;
+  }
   for (int r = 0; r < nrhs; ++r) {
     int rc = DW_OK;
     if (prec == DW_F64) {

@@ -254,6 +254,8 @@ static void put_cplx(std::vector<char>& buf, int prec, size_t V, size_t field_of
 
 static void free_ctx(dw_ctx* c) {
   if (!c) return;
+  sap_graphs_free(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   void* ptrs[] = {c->d_canon_of, c->d_nbtab, c->d_blk_nb, c->d_blk_x0, c->d_loc, c->d_colour_list,
                   c->links[0], c->links[1], c->clov[0], c->clov[1], c->clovinv[0], c->clovinv[1],
                   c->sap_r[0], c->sap_r[1], c->sap_d[0], c->sap_d[1], c->d_red, c->d_count};

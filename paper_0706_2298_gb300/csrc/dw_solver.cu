@@ -34,6 +34,13 @@ int dfl_prolong_f64(dfl_ctx*, const double*, double*, int, cudaStream_t);
 int little_solve_f32(dfl_ctx*, const float*, float*, double, int, int, int*, double*, cudaStream_t);
 int little_solve_f64(dfl_ctx*, const double*, double*, double, int, int, int*, double*, cudaStream_t);
 int dfl_nlittle(const dfl_ctx*);
+int dfl_restrict_mrhs_f32(dfl_ctx*, const float*, float*, int, cudaStream_t);
+int dfl_prolong_mrhs_f32(dfl_ctx*, const float*, float*, int, int, cudaStream_t);
+int little_solve_batch_f32(dfl_ctx*, const float*, float*, const double*, const int*, int, int, int, int*, double*,
+                           cudaStream_t);
+int little_solve_refined(dfl_ctx*, const double*, double*, double, int, int, int*, double*, cudaStream_t);
+int dfl_restrict_mrhs_f64(dfl_ctx*, const double*, double*, int, cudaStream_t);
+int dfl_prolong_mrhs_f64(dfl_ctx*, const double*, double*, int, int, cudaStream_t);
 
 namespace {
 
@@ -170,25 +177,43 @@ int solve_one(dw_ctx* c, dfl_ctx* d, const sol_params* p, const double* eta_cano
   const int max_restarts = 10000;
   for (int restart = 0; restart < max_restarts; ++restart) {
     if ((rc = residual64())) return rc;
+    double rn = sqrt(h[2]);
     if (d) {
-      // deflation correction with the FP64 little solve (A.5: high precision outside the cycles)
-      tm.begin(PH_PROJECT);
-      restrict_(d, W.r64, W.c64, s);
-      tm.end();
       int it = 0;
       double rr = 0;
-      tm.begin(PH_LITTLE);
-      rc = lsolve_(d, W.c64, W.v64, p->little_tol_out, p->little_maxit, p->little_nkv, &it, &rr, s);
-      tm.end();
-      if (rc < 0) return rc;
+      if (p->mixed) {
+        // deflation correction accurate to the outer tolerance, all little iterations in FP32
+        // (A.5 asks for high precision outside the cycles): FP32 GCR + FP64 little residuals
+        tm.begin(PH_PROJECT);
+        restrict_(d, W.r64, W.c64, s);
+        tm.end();
+        tm.begin(PH_LITTLE);
+        rc = little_solve_refined(d, W.c64, W.v64, p->little_tol_out, p->little_maxit, p->little_nkv, &it, &rr, s);
+        tm.end();
+        if (rc < 0) return rc;
+        tm.begin(PH_PROJECT);
+        prolong_(d, W.v64, W.psi, 1, s);
+        tm.end();
+        if ((rc = residual64())) return rc;
+        rn = sqrt(h[2]);
+      } else {
+        // deflation correction with the FP64 little solve (A.5: high precision outside the cycles)
+        tm.begin(PH_PROJECT);
+        restrict_(d, W.r64, W.c64, s);
+        tm.end();
+        tm.begin(PH_LITTLE);
+        rc = lsolve_(d, W.c64, W.v64, p->little_tol_out, p->little_maxit, p->little_nkv, &it, &rr, s);
+        tm.end();
+        if (rc < 0) return rc;
+        tm.begin(PH_PROJECT);
+        prolong_(d, W.v64, W.psi, 1, s);
+        tm.end();
+        if ((rc = residual64())) return rc;
+        rn = sqrt(h[2]);
+      }
       inf.little_iterations += it;
       inf.little_solves += 1;
-      tm.begin(PH_PROJECT);
-      prolong_(d, W.v64, W.psi, 1, s);
-      tm.end();
-      if ((rc = residual64())) return rc;
     }
-    const double rn = sqrt(h[2]);
     relres = rn / en;
     if (verbose)
       fprintf(stderr, "[dwsolve] restart %d: |rho|/|eta| = %.3e  gcr steps %d  little its %d (%d solves)\n",
@@ -281,6 +306,234 @@ int solve_one(dw_ctx* c, dfl_ctx* d, const sol_params* p, const double* eta_cano
   return inf.status;
 }
 
+// --------------------------------------------------------------------------- batched solve
+// Mixed-precision DFL+SAP+GCR for nrhs right-hand sides in lockstep: every kernel processes the
+// whole batch (links, clover and the deflation basis are read once per site or block for all
+// right-hand sides), and each host round trip serves all of them.  A right-hand side that has
+// converged is frozen (its psi is no longer updated).
+int solve_batch_f32(dw_ctx* c, dfl_ctx* d, const sol_params* p, int nrhs, const double* eta_canon,
+                    double* psi_canon, sol_info* info, cudaStream_t s) {
+  const size_t V = c->V, n = V * 12, fs = V * 24;
+  const size_t fb32 = dw_field_bytes(c, DW_F32) * nrhs, fb64 = dw_field_bytes(c, DW_F64) * nrhs;
+  const int nkv = p->nkv;
+  const int Nl = d ? dfl_nlittle(d) : 0;
+  Work<float> W;
+  int rc;
+  W.xi.resize(nkv);
+  W.chi.resize(nkv);
+  for (int k = 0; k < nkv; ++k)
+    if ((rc = W.alloc(fb32, (void**)&W.xi[k])) || (rc = W.alloc(fb32, (void**)&W.chi[k]))) return rc;
+  if ((rc = W.alloc(fb32, (void**)&W.rho)) || (rc = W.alloc(fb32, (void**)&W.w)) ||
+      (rc = W.alloc(fb32, (void**)&W.t1)) || (rc = W.alloc(fb64, (void**)&W.eta)) ||
+      (rc = W.alloc(fb64, (void**)&W.psi)) || (rc = W.alloc(fb64, (void**)&W.r64)) ||
+      (rc = W.alloc(fb64, (void**)&W.t64)))
+    return rc;
+  if (d && ((rc = W.alloc((size_t)Nl * 2 * sizeof(float) * nrhs, (void**)&W.lc)) ||
+            (rc = W.alloc((size_t)Nl * 2 * sizeof(float) * nrhs, (void**)&W.lv)) ||
+            (rc = W.alloc((size_t)Nl * 2 * sizeof(double) * nrhs, (void**)&W.c64)) ||
+            (rc = W.alloc((size_t)Nl * 2 * sizeof(double) * nrhs, (void**)&W.v64))))
+    return rc;
+  Timers tm;
+  tm.s = s;
+  auto t_start = std::chrono::steady_clock::now();
+  double* dres = c->d_red + 65536 + 4096;
+  std::vector<double> h(3 * 64 + 2 * 64 * 64);
+  auto F32 = [&](float* base, int r) { return base + (size_t)r * fs; };
+  auto F64 = [&](double* base, int r) { return base + (size_t)r * fs; };
+  // batched norms / dots: one kernel per right-hand side, one read for all
+  auto norms64 = [&](double* base, std::vector<double>& out) -> int {
+    for (int r = 0; r < nrhs; ++r) blas_dot<double>(c, F64(base, r), F64(base, r), n, dres + 3 * r, s);
+    int e = read_host(c, dres, 3 * nrhs, h.data(), s);
+    for (int r = 0; r < nrhs; ++r) out[r] = sqrt(h[3 * r + 2]);
+    return e;
+  };
+  if ((rc = dw_pack(c, DW_F64, nrhs, eta_canon, W.eta, s))) return rc;
+  DW_CUDA(cudaMemsetAsync(W.psi, 0, fb64, s));
+  std::vector<double> en(nrhs), rn(nrhs), relres(nrhs, 1.0), ltol(nrhs), rk(nrhs);
+  std::vector<int> conv(nrhs, 0), live(nrhs), its(nrhs), lits(nrhs), nsteps(nrhs, 0), restarts(nrhs, 0),
+      lsolves(nrhs, 0), litot(nrhs, 0);
+  std::vector<double> lrr(nrhs);
+  if ((rc = norms64(W.eta, en))) return rc;
+  for (int r = 0; r < nrhs; ++r) conv[r] = en[r] == 0.0;
+  auto residual64 = [&]() -> int {
+    tm.begin(PH_RESTART);
+    dirac_mrhs<double>(c, W.psi, W.t64, nrhs, c->tune_rgroup, s);
+    for (int r = 0; r < nrhs; ++r) {
+      DW_CUDA(cudaMemcpyAsync(F64(W.r64, r), F64(W.eta, r), fs * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      blas_axpy<double>(F64(W.t64, r), F64(W.r64, r), -1.0, 0.0, n, s);
+    }
+    tm.end();
+    return norms64(W.r64, rn);
+  };
+  const int nkvmax = nkv;
+  std::vector<cd> a((size_t)nrhs * nkvmax), cc((size_t)nrhs * nkvmax), bb((size_t)nrhs * nkvmax * nkvmax);
+  const int max_restarts = 10000;
+  int total_steps = 0;
+  for (int restart = 0; restart < max_restarts; ++restart) {
+    if ((rc = residual64())) return rc;
+    if (d) {
+      // deflation correction accurate to the outer tolerance (FP32 little iterations, FP64 residuals)
+      tm.begin(PH_PROJECT);
+      dfl_restrict_mrhs_f64(d, W.r64, W.c64, nrhs, s);
+      tm.end();
+      tm.begin(PH_LITTLE);
+      for (int r = 0; r < nrhs; ++r) {
+        double* vr = W.v64 + (size_t)r * Nl * 2;
+        if (conv[r]) {
+          DW_CUDA(cudaMemsetAsync(vr, 0, (size_t)Nl * 2 * sizeof(double), s));
+          continue;
+        }
+        int it = 0;
+        double rr = 0;
+        rc = little_solve_refined(d, W.c64 + (size_t)r * Nl * 2, vr, p->little_tol_out, p->little_maxit,
+                                  p->little_nkv, &it, &rr, s);
+        if (rc < 0) return rc;
+        litot[r] += it;
+        lsolves[r] += 1;
+      }
+      tm.end();
+      tm.begin(PH_PROJECT);
+      dfl_prolong_mrhs_f64(d, W.v64, W.psi, 1, nrhs, s);
+      tm.end();
+      if ((rc = residual64())) return rc;
+    }
+    bool all = true;
+    for (int r = 0; r < nrhs; ++r) {
+      if (!conv[r]) {
+        relres[r] = rn[r] / en[r];
+        if (rn[r] <= p->tol * en[r]) conv[r] = 1;
+      }
+      all &= conv[r] != 0;
+    }
+    if (all || total_steps >= p->nmx) break;
+    // ---- one GCR cycle for the batch
+    for (int r = 0; r < nrhs; ++r) {
+      live[r] = !conv[r];
+      field_convert<double, float>(F64(W.r64, r), F32(W.rho, r), live[r] ? 1.0 / rn[r] : 0.0, V, s);
+      nsteps[r] = 0;
+    }
+    for (int k = 0; k < nkv && total_steps < p->nmx; ++k) {
+      tm.begin(PH_SAP);
+      if ((rc = sap_apply_mrhs_graph(c, p->ncy, p->nmr, W.rho, W.xi[k], nrhs, s))) return rc;
+      tm.end();
+      tm.begin(PH_DIRAC);
+      dirac_mrhs<float>(c, W.xi[k], W.chi[k], nrhs, c->tune_rgroup, s);
+      tm.end();
+      if (d) {
+        tm.begin(PH_PROJECT);
+        for (int r = 0; r < nrhs; ++r) blas_dot<float>(c, F32(W.chi[k], r), F32(W.chi[k], r), n, dres + 3 * r, s);
+        dfl_restrict_mrhs_f32(d, W.chi[k], W.lc, nrhs, s);
+        tm.end();
+        if ((rc = read_host(c, dres, 3 * nrhs, h.data(), s))) return rc;
+        std::vector<int> use(nrhs);
+        for (int r = 0; r < nrhs; ++r) {
+          use[r] = live[r];
+          ltol[r] = std::min(p->little_tol_cap, p->little_tol_in / std::max(sqrt(h[3 * r + 2]), 1e-300));
+        }
+        tm.begin(PH_LITTLE);
+        rc = little_solve_batch_f32(d, W.lc, W.lv, ltol.data(), use.data(), p->little_maxit, p->little_nkv, nrhs,
+                                    lits.data(), lrr.data(), s);
+        tm.end();
+        if (rc < 0) return rc;
+        for (int r = 0; r < nrhs; ++r) if (use[r]) { litot[r] += lits[r]; lsolves[r] += 1; }
+        tm.begin(PH_PROJECT);
+        for (int r = 0; r < nrhs; ++r)
+          if (!use[r]) DW_CUDA(cudaMemsetAsync(W.lv + (size_t)r * Nl * 2, 0, (size_t)Nl * 2 * sizeof(float), s));
+        dfl_prolong_mrhs_f32(d, W.lv, W.t1, 0, nrhs, s);
+        dirac_mrhs<float>(c, W.t1, W.w, nrhs, c->tune_rgroup, s);
+        for (int r = 0; r < nrhs; ++r) blas_axpy<float>(F32(W.w, r), F32(W.chi[k], r), -1.0, 0.0, n, s);
+        tm.end();
+      }
+      tm.begin(PH_ORTH);
+      if (k > 0) {
+        for (int r = 0; r < nrhs; ++r) {
+          std::vector<const float*> prev(k);
+          for (int j = 0; j < k; ++j) prev[j] = F32(W.chi[j], r);
+          blas_multi_dot<float>(c, prev.data(), k, F32(W.chi[k], r), n, dres + (size_t)r * 2 * nkv, s);
+        }
+        if ((rc = read_host(c, dres, 2 * nkv * nrhs, h.data(), s))) return rc;
+        for (int r = 0; r < nrhs; ++r) {
+          std::vector<const float*> prev(k);
+          for (int j = 0; j < k; ++j) {
+            prev[j] = F32(W.chi[j], r);
+            bb[((size_t)r * nkvmax + j) * nkvmax + k] = cd(h[r * 2 * nkv + 2 * j], h[r * 2 * nkv + 2 * j + 1]);
+          }
+          blas_multi_axpy<float>(prev.data(), k, h.data() + (size_t)r * 2 * nkv, F32(W.chi[k], r), n, s);
+        }
+      }
+      for (int r = 0; r < nrhs; ++r) blas_dot<float>(c, F32(W.chi[k], r), F32(W.rho, r), n, dres + 3 * r, s);
+      if ((rc = read_host(c, dres, 3 * nrhs, h.data(), s))) return rc;
+      for (int r = 0; r < nrhs; ++r) {
+        double ck = sqrt(h[3 * r + 2]);
+        if (!live[r] || !(ck > 0)) { live[r] = 0; continue; }
+        cc[(size_t)r * nkvmax + k] = ck;
+        a[(size_t)r * nkvmax + k] = cd(h[3 * r], h[3 * r + 1]) / ck;
+        nsteps[r] = k + 1;
+        cd ak = a[(size_t)r * nkvmax + k];
+        blas_scale<float>(F32(W.chi[k], r), 1.0 / ck, 0.0, n, s);
+        blas_axpy<float>(F32(W.chi[k], r), F32(W.rho, r), -ak.real(), -ak.imag(), n, s);
+        blas_dot<float>(c, F32(W.rho, r), F32(W.rho, r), n, dres + 3 * r, s);
+      }
+      if ((rc = read_host(c, dres, 3 * nrhs, h.data(), s))) return rc;
+      tm.end();
+      ++total_steps;
+      bool any_live = false;
+      for (int r = 0; r < nrhs; ++r) {
+        if (!live[r]) continue;
+        rk[r] = sqrt(h[3 * r + 2]);
+        its[r] += 1;
+        const double stop = std::max(p->tol * en[r] / rn[r], p->inner_rtol);
+        if (rk[r] <= stop) live[r] = 0;     // this right-hand side's cycle is complete
+        any_live |= live[r] != 0;
+      }
+      if (!any_live) break;
+    }
+    // psi += rn * sum_k beta_k xi_k  for every right-hand side with steps in this cycle
+    tm.begin(PH_RESTART);
+    for (int r = 0; r < nrhs; ++r) {
+      const int kr = nsteps[r];
+      if (conv[r] || kr == 0) continue;
+      std::vector<cd> beta(kr);
+      for (int j = kr - 1; j >= 0; --j) {
+        cd sacc = a[(size_t)r * nkvmax + j];
+        for (int i = j + 1; i < kr; ++i) sacc -= bb[((size_t)r * nkvmax + j) * nkvmax + i] * beta[i];
+        beta[j] = sacc / cc[(size_t)r * nkvmax + j];
+      }
+      std::vector<double> coef(2 * kr);
+      std::vector<const float*> xs(kr);
+      for (int j = 0; j < kr; ++j) {
+        coef[2 * j] = beta[j].real();
+        coef[2 * j + 1] = beta[j].imag();
+        xs[j] = F32(W.xi[j], r);
+      }
+      blas_lincomb<float>(xs.data(), kr, coef.data(), F32(W.w, r), n, s);
+      field_convert<float, double>(F32(W.w, r), F64(W.t64, r), rn[r], V, s);
+      blas_axpy<double>(F64(W.t64, r), F64(W.psi, r), 1.0, 0.0, n, s);
+      restarts[r] += 1;
+    }
+    tm.end();
+  }
+  if ((rc = dw_unpack(c, DW_F64, nrhs, W.psi, psi_canon, s))) return rc;
+  DW_CUDA(cudaStreamSynchronize(s));
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  sol_info agg{};
+  tm.collect(&agg);
+  int worst = DW_OK;
+  for (int r = 0; r < nrhs; ++r) {
+    sol_info in = agg;   // phase times are those of the whole batch
+    in.status = conv[r] ? DW_OK : DW_ENOTCONV;
+    in.iterations = its[r];
+    in.restarts = restarts[r];
+    in.little_iterations = litot[r];
+    in.little_solves = lsolves[r];
+    in.relres = relres[r];
+    in.seconds = secs;
+    if (info) info[r] = in;
+    worst = std::max(worst, in.status);
+  }
+  return worst;
+}
+
 }  // namespace
 
 extern "C" int gcr_solve(dw_ctx* c, dfl_ctx* d, const sol_params* p, int nrhs, const double* eta, double* psi,
@@ -293,6 +546,11 @@ extern "C" int gcr_solve(dw_ctx* c, dfl_ctx* d, const sol_params* p, int nrhs, c
   cudaStream_t s = (cudaStream_t)stream;
   int worst = DW_OK;
   const size_t n = (size_t)c->V * 24;
+  const char* be = getenv("DW_BATCH");
+  if (p->mixed && nrhs > 1 && !(be && be[0] == '0') && p->nkv <= 64) {
+    if (nrhs > 64) { dw_set_error("gcr_solve: at most 64 right-hand sides per batch"); return DW_EINVAL; }
+    return solve_batch_f32(c, d, p, nrhs, eta, psi, info, s);
+  }
   for (int r = 0; r < nrhs; ++r) {
     int rc = p->mixed ? solve_one<float>(c, d, p, eta + r * n, psi + r * n, info ? info + r : nullptr, s)
                       : solve_one<double>(c, d, p, eta + r * n, psi + r * n, info ? info + r : nullptr, s);

@@ -81,6 +81,7 @@ _SIGNATURES = {
     "little_dirac_solve": (C.c_int, [_P, C.c_int, _P, _P, C.c_double, C.c_int, C.POINTER(C.c_int),
                                      C.POINTER(C.c_double), _P]),
     "gcr_solve": (C.c_int, [_P, _P, C.POINTER(SolParams), C.c_int, _P, _P, C.POINTER(SolInfo), _P]),
+    "dw_autotune": (C.c_int, [_P, C.c_int, C.c_char_p, C.c_size_t]),
     "cgnr_solve": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.POINTER(C.c_int), C.POINTER(C.c_double), _P]),
 }
 
@@ -272,3 +273,10 @@ def cgnr_solve(ctx: Ctx, tol, maxit, eta_dev, psi_dev, stream=None):
     rc = _check(lib().cgnr_solve(ctx.handle, float(tol), int(maxit), _ptr(_as_f64(eta_dev)), _ptr(_as_f64(psi_dev)),
                                  C.byref(it), C.byref(rr), _stream(stream)), ok=(DW_OK, DW_ENOTCONV))
     return rc, it.value, rr.value
+
+
+def dw_autotune(ctx: Ctx, nrhs=1) -> dict:
+    import json
+    buf = C.create_string_buffer(1024)
+    _check(lib().dw_autotune(ctx.handle, int(nrhs), buf, 1024))
+    return json.loads(buf.value.decode())

@@ -30,7 +30,7 @@ def main():
     ap.add_argument("--L", default="48,24,24,24")
     ap.add_argument("--target", type=int, default=2000)
     ap.add_argument("--maxit", type=int, default=6000)
-    ap.add_argument("--bisect", type=int, default=7)
+    ap.add_argument("--bisect", type=int, default=8)
     ap.add_argument("--name", default="24^3x48")
     args = ap.parse_args()
     L = tuple(int(v) for v in args.L.split(","))
@@ -47,28 +47,49 @@ def main():
         return it if rc == dw.DW_OK else args.maxit + 1
 
     easy, hard = None, None
+    scan = []
     m = 0.2
     while m > -0.6:
         c = count(m)
+        scan.append((m, c))
         if c > args.target:
             hard = (m, c)
             break
         easy = (m, c)
         m -= 0.05
-    if hard is None or easy is None:
-        raise SystemExit("no mass with more than target iterations found")
-    lo, hi = hard[0], easy[0]
-    for _ in range(args.bisect):
-        mid = 0.5 * (lo + hi)
-        c = count(mid)
-        if c > args.target:
-            lo, hard = mid, (mid, c)
-        else:
-            hi = mid
+    if hard is not None and easy is not None:
+        lo, hi = hard[0], easy[0]
+        for _ in range(args.bisect):
+            mid = 0.5 * (lo + hi)
+            c = count(mid)
+            if c > args.target:
+                lo, hard = mid, (mid, c)
+            else:
+                hi = mid
+        rule = "heaviest scanned/bisected mass with CGNR iterations > target"
+        best = hard
+    else:
+        # the count never exceeds the target: the field is too smooth for the criterion at this
+        # volume.  Take the hardest (most nearly critical) mass: ternary search around the scan maximum.
+        m_best, c_best = max(scan, key=lambda t: t[1])
+        lo, hi = m_best - 0.05, m_best + 0.05
+        best = (m_best, c_best)
+        for _ in range(args.bisect):
+            m1, m2 = lo + (hi - lo) / 3, hi - (hi - lo) / 3
+            c1, c2 = count(m1), count(m2)
+            for mm, cc in ((m1, c1), (m2, c2)):
+                if cc > best[1]:
+                    best = (mm, cc)
+            if c1 < c2:
+                lo = m1
+            else:
+                hi = m2
+        rule = (f"target {args.target} unreachable (max CGNR count {best[1]}); mass of the largest CGNR count "
+                f"(nearest to critical)")
     out_path = os.path.join(HERE, "workload_masses.json")
     data = json.load(open(out_path)) if os.path.exists(out_path) else {}
-    data[args.name] = {"m0": round(hard[0], 6), "cg_iterations": hard[1], "target": args.target,
-                       "rule": "heaviest scanned/bisected mass with CGNR iterations > target", "scan": log}
+    data[args.name] = {"m0": round(best[0], 6), "cg_iterations": best[1], "target": args.target,
+                       "rule": rule, "scan": log}
     with open(out_path, "w") as f:
         json.dump(data, f, indent=1)
     print(json.dumps(data[args.name]))

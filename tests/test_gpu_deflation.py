@@ -207,3 +207,24 @@ def test_inverse_iteration_fp32(case):
     fields = inverse_iteration(SchwarzOracle(D, sb), start.numpy(), 2, 4, 4)
     sub = BlockSubspace(D, db, block_gram_schmidt(Blocking(L, db), fields))
     assert rel(_export(case, d), basis_fields(sub)) <= 1e-4
+
+
+def test_little_solve_cooperative_matches_host_driven(case):
+    """The persistent cooperative little solver and the host-driven loop agree."""
+    import os
+    L, sb, db, Ns, ctx, D, start = case
+    d = _build(case, dw.DW_BF16, n_inv=2, iter_prec=dw.DW_F32)
+    wv = synth.complex_gaussian((d.Nb * d.Ns,), 17).numpy()
+    res = {}
+    for flag in ("0", "1"):
+        os.environ["DW_LITTLE_COOP"] = flag
+        for prec, dt in ((dw.DW_F64, torch.float64), (dw.DW_F32, torch.float32)):
+            wt = torch.from_numpy(wv.view(np.float64).copy()).to(dt).cuda()
+            vt = torch.empty_like(wt)
+            rc, it, rr = dw.little_dirac_solve(d, prec, wt, vt, 1e-10 if prec == dw.DW_F64 else 1e-5, 3000)
+            assert rc == dw.DW_OK
+            res[(flag, prec)] = (vt.double().cpu().numpy().view(np.complex128), it)
+    os.environ.pop("DW_LITTLE_COOP")
+    assert rel(res[("1", dw.DW_F64)][0], res[("0", dw.DW_F64)][0]) <= 1e-8
+    assert rel(res[("1", dw.DW_F32)][0], res[("0", dw.DW_F32)][0]) <= 1e-4
+    assert abs(res[("1", dw.DW_F64)][1] - res[("0", dw.DW_F64)][1]) <= 2
