@@ -116,6 +116,14 @@ typedef struct {
                           DW_F64: FP64 basis (plain path) */
   int iter_prec;       /* precision of the inverse iteration: DW_F32 or DW_F64 */
   double cond_max;     /* largest accepted condition number of a diagonal little block (A.2) */
+  /* learned generation (optional; iter_prec must be DW_F32): after net_k0 plain steps the fields go
+   * through the parallel-transport network (weights: ptnet_weight_count(net_channels) complex FP32),
+   * unless the network output fails the judge -- mean ||D psi||/||psi|| must fall below
+   * net_judge times its value at the network input -- in which case the plain steps continue. */
+  const void* net_weights;   /* NULL: plain procedure only */
+  int net_channels;          /* 16 */
+  int net_k0;                /* plain steps before the network */
+  double net_judge;          /* e.g. 0.95 */
 } dfl_params;
 
 typedef struct {
@@ -124,6 +132,9 @@ typedef struct {
   double max_block_cond;   /* largest condition-number estimate of B_LL */
   int Nb;                  /* number of deflation blocks */
   int N;                   /* little dimension Nb * Ns */
+  int learned_used;        /* 1: the network output was accepted */
+  double rho_in;           /* mean ||D psi||/||psi|| at the network input (after net_k0 steps) */
+  double rho_out;          /* ... of the network output (or of the fields after the plain fallback) */
 } dfl_info;
 
 /* Build the deflation subspace (Sections 4.2, 5.3) and the little Dirac
@@ -195,6 +206,24 @@ int gcr_solve(dw_ctx* ctx, dfl_ctx* d, const sol_params* p, int nrhs, const doub
  * keeps the fastest in the context and writes a JSON summary to report
  * (may be NULL).  Synchronous; allocates two temporary batches of fields. */
 int dw_autotune(dw_ctx* ctx, int nrhs, char* report, size_t report_len);
+
+/* Parallel-transport network of the learned subspace generation (3 layers, 1 -> C -> C -> 1
+ * channels; each layer h'(x) = sum over the 9 transports {1, U_mu(x) . (x+mu), U_mu(x-mu)^+ . (x-mu)}
+ * of a (channel x spin) matrix; gauge covariant).  Weights: ptnet_weight_count(C) complex FP32
+ * (layers back to back, each [9][4 C_out][4 C_in] row-major).  Only C = 16 is built. */
+size_t ptnet_weight_count(int C);
+/* y_f = N(x_f) for nf packed FP32 fields.  Synchronous. */
+int ptnet_forward(dw_ctx* ctx, int C, const void* weights, int nf, const void* x, void* y, void* stream);
+/* Loss L = sum_f |N(x_f) - y_f|^2 / sum_f |y_f|^2 and gradient dL/dRe W + i dL/dIm W (same layout
+ * as the weights), computed by the network's backward kernels.  Synchronous. */
+int ptnet_loss_grad(dw_ctx* ctx, int C, const void* weights, int nf, const void* x, const void* y, void* grad,
+                    double* loss, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999) on ncomplex complex weights; m, v: optimiser state. */
+int ptnet_adam(size_t ncomplex, void* weights, const void* grad, void* m, void* v, int step, double lr,
+               void* stream);
+/* The plain subspace generation (5.1) on nf packed FP32 fields in place: nsteps times
+ * psi <- M_sap psi, normalised.  Synchronous. */
+int dfl_inverse_iteration(dw_ctx* ctx, int ncy, int nmr, int nsteps, int nf, void* fields, void* stream);
 
 /* Conjugate gradient on the normal equations D^+ D psi = D^+ eta, FP64,
  * unpreconditioned (the plain iterative method against which the paper's

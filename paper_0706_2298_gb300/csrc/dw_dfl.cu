@@ -22,6 +22,8 @@
 
 namespace cg = cooperative_groups;
 
+extern "C" int ptnet_forward(dw_ctx* c, int C, const void* W, int nf, const void* x, void* y, void* stream);
+
 using cd = std::complex<double>;
 
 struct dfl_ctx {
@@ -1460,7 +1462,31 @@ static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_c
   if ((rc = dw_pack(c, ip, Ns, start, work, s))) return rc;
   const size_t n = V * 12;
   std::vector<double> h(3);
-  for (int it = 0; it < p->n_inv; ++it)
+  const bool use_net = p->net_weights != nullptr;
+  if (use_net && (ip != DW_F32 || p->net_channels != 16 || p->net_k0 < 0 || p->net_k0 > p->n_inv)) {
+    dw_set_error("deflation_build: the network needs iter_prec DW_F32, 16 channels and 0 <= net_k0 <= n_inv");
+    return DW_EINVAL;
+  }
+  // mean ||D psi_l|| / ||psi_l|| of the FP32 work fields, the relaxation measure of (5.2)
+  auto rho_measure = [&](const float* fields, double* out) -> int {
+    double sum = 0;
+    for (int l = 0; l < Ns; ++l) {
+      const float* f = fields + (size_t)l * 24 * V;
+      dirac_full<float>(c, f, (float*)tmp, s);
+      blas_dot<float>(c, (float*)tmp, (float*)tmp, n, c->d_red + 65536, s);
+      blas_dot<float>(c, f, f, n, c->d_red + 65536 + 3, s);
+      double hh[6];
+      int e = sync_read(c, c->d_red + 65536, 6, hh, s);
+      if (e) return e;
+      sum += sqrt(hh[2] / hh[5]);
+    }
+    *out = sum / Ns;
+    return DW_OK;
+  };
+  int learned = 0;
+  double rho_in = 0, rho_out = 0;
+  const int n_first = use_net ? p->net_k0 : p->n_inv;
+  for (int it = 0; it < n_first; ++it)
     for (int l = 0; l < Ns; ++l) {
       if (ip == DW_F64) {
         double* w = (double*)work + (size_t)l * 24 * V;
@@ -1476,6 +1502,36 @@ static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_c
         blas_convert<float, float>((float*)tmp, w, 1.0 / sqrt(h[2]), n, s);
       }
     }
+  if (use_net) {
+    // learned generation: network on the fields after net_k0 plain steps, judged by (5.2)
+    if ((rc = rho_measure((const float*)work, &rho_in))) return rc;
+    float* out = nullptr;
+    DW_CUDA(cudaMalloc(&out, fb * Ns));
+    struct F1 { void* p; ~F1() { if (p) cudaFree(p); } } g2{out};
+    if ((rc = ptnet_forward(c, p->net_channels, p->net_weights, Ns, work, out, s))) return rc;
+    for (int l = 0; l < Ns; ++l) {
+      float* f = out + (size_t)l * 24 * V;
+      blas_dot<float>(c, f, f, n, c->d_red + 65536, s);
+      if ((rc = sync_read(c, c->d_red + 65536, 3, h.data(), s))) return rc;
+      blas_scale<float>(f, h[2] > 0 ? 1.0 / sqrt(h[2]) : 0.0, 0.0, n, s);
+    }
+    if ((rc = rho_measure(out, &rho_out))) return rc;
+    if (std::isfinite(rho_out) && rho_out <= p->net_judge * rho_in) {
+      learned = 1;
+      DW_CUDA(cudaMemcpyAsync(work, out, fb * Ns, cudaMemcpyDeviceToDevice, s));
+    } else {
+      // fallback: the plain procedure finishes the generation
+      for (int it = p->net_k0; it < p->n_inv; ++it)
+        for (int l = 0; l < Ns; ++l) {
+          float* w = (float*)work + (size_t)l * 24 * V;
+          if ((rc = sap_apply<float>(c, p->ncy, p->nmr, w, (float*)tmp, s))) return rc;
+          blas_dot<float>(c, (float*)tmp, (float*)tmp, n, c->d_red + 65536, s);
+          if ((rc = sync_read(c, c->d_red + 65536, 3, h.data(), s))) return rc;
+          blas_convert<float, float>((float*)tmp, w, 1.0 / sqrt(h[2]), n, s);
+        }
+      if ((rc = rho_measure((const float*)work, &rho_out))) return rc;
+    }
+  }
   // ---- block Gram-Schmidt in FP64
   DW_CUDA(cudaMalloc(&d->basis64, (size_t)Ns * 24 * V * sizeof(double)));
   if (ip == DW_F64) DW_CUDA(cudaMemcpyAsync(d->basis64, work, fb * Ns, cudaMemcpyDeviceToDevice, s));
@@ -1648,6 +1704,9 @@ static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_c
     info->max_block_cond = d->max_cond;
     info->Nb = d->Nb;
     info->N = d->N;
+    info->learned_used = learned;
+    info->rho_in = rho_in;
+    info->rho_out = rho_out;
   }
   return d->illcond ? DW_ILLCOND : DW_OK;
 }

@@ -33,12 +33,15 @@ class DwParams(C.Structure):
 
 class DflParams(C.Structure):
     _fields_ = [("bs", C.c_int * 4), ("Ns", C.c_int), ("n_inv", C.c_int), ("ncy", C.c_int), ("nmr", C.c_int),
-                ("basis_prec", C.c_int), ("iter_prec", C.c_int), ("cond_max", C.c_double)]
+                ("basis_prec", C.c_int), ("iter_prec", C.c_int), ("cond_max", C.c_double),
+                ("net_weights", C.c_void_p), ("net_channels", C.c_int), ("net_k0", C.c_int),
+                ("net_judge", C.c_double)]
 
 
 class DflInfo(C.Structure):
     _fields_ = [("seconds", C.c_double), ("seconds_little", C.c_double), ("max_block_cond", C.c_double),
-                ("Nb", C.c_int), ("N", C.c_int)]
+                ("Nb", C.c_int), ("N", C.c_int), ("learned_used", C.c_int), ("rho_in", C.c_double),
+                ("rho_out", C.c_double)]
 
 
 class SolParams(C.Structure):
@@ -83,6 +86,11 @@ _SIGNATURES = {
     "gcr_solve": (C.c_int, [_P, _P, C.POINTER(SolParams), C.c_int, _P, _P, C.POINTER(SolInfo), _P]),
     "dw_autotune": (C.c_int, [_P, C.c_int, C.c_char_p, C.c_size_t]),
     "cgnr_solve": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.POINTER(C.c_int), C.POINTER(C.c_double), _P]),
+    "ptnet_weight_count": (C.c_size_t, [C.c_int]),
+    "ptnet_forward": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, _P, _P]),
+    "ptnet_loss_grad": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, _P, _P, C.POINTER(C.c_double), _P]),
+    "ptnet_adam": (C.c_int, [C.c_size_t, _P, _P, _P, _P, C.c_int, C.c_double, _P]),
+    "dfl_inverse_iteration": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P]),
 }
 
 _lib = None
@@ -213,11 +221,13 @@ def sap_precondition(ctx: Ctx, prec, ncy, nmr, nrhs, rho_dev, xi_dev, stream=Non
 
 
 def deflation_build(ctx: Ctx, bs, Ns, n_inv, ncy, nmr, start_canon_dev, basis_prec=DW_BF16, iter_prec=DW_F32,
-                    cond_max=1e8):
+                    cond_max=1e8, net_weights=None, net_k0=2, net_judge=0.95, net_channels=16):
     p = DflParams()
     p.bs = (C.c_int * 4)(*bs)
     p.Ns, p.n_inv, p.ncy, p.nmr = Ns, n_inv, ncy, nmr
     p.basis_prec, p.iter_prec, p.cond_max = basis_prec, iter_prec, float(cond_max)
+    p.net_weights = _ptr(net_weights).value if net_weights is not None else None
+    p.net_channels, p.net_k0, p.net_judge = int(net_channels), int(net_k0), float(net_judge)
     info = DflInfo()
     h = C.c_void_p()
     rc = _check(lib().deflation_build(ctx.handle, C.byref(p), _ptr(_as_f64(start_canon_dev)), C.byref(h),
@@ -280,3 +290,29 @@ def dw_autotune(ctx: Ctx, nrhs=1) -> dict:
     buf = C.create_string_buffer(1024)
     _check(lib().dw_autotune(ctx.handle, int(nrhs), buf, 1024))
     return json.loads(buf.value.decode())
+
+
+def ptnet_weight_count(channels=16) -> int:
+    return int(lib().ptnet_weight_count(int(channels)))
+
+
+def ptnet_forward(ctx: Ctx, weights, nf, x, y, channels=16, stream=None):
+    _check(lib().ptnet_forward(ctx.handle, int(channels), _ptr(weights), int(nf), _ptr(x), _ptr(y),
+                               _stream(stream)))
+
+
+def ptnet_loss_grad(ctx: Ctx, weights, nf, x, y, grad, channels=16, stream=None) -> float:
+    loss = C.c_double()
+    _check(lib().ptnet_loss_grad(ctx.handle, int(channels), _ptr(weights), int(nf), _ptr(x), _ptr(y), _ptr(grad),
+                                 C.byref(loss), _stream(stream)))
+    return loss.value
+
+
+def ptnet_adam(weights, grad, m, v, step, lr, stream=None):
+    n = weights.numel() // 2 if weights.dtype == torch.float32 else weights.numel()
+    _check(lib().ptnet_adam(n, _ptr(weights), _ptr(grad), _ptr(m), _ptr(v), int(step), float(lr), _stream(stream)))
+
+
+def dfl_inverse_iteration(ctx: Ctx, ncy, nmr, nsteps, nf, fields, stream=None):
+    _check(lib().dfl_inverse_iteration(ctx.handle, int(ncy), int(nmr), int(nsteps), int(nf), _ptr(fields),
+                                       _stream(stream)))

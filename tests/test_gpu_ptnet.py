@@ -1,0 +1,113 @@
+"""GPU parity of the parallel-transport network kernels (forward, backward,
+Adam training) against the FP64 oracle, whose gradient is pinned by finite
+differences, and of the learned subspace generation with its judge."""
+import numpy as np
+import pytest
+import torch
+
+from oracle.dirac import WilsonClover
+from oracle.ptnet import PTNet, init_weights
+from paper_0706_2298_gb300 import dwsolve as dw
+from paper_0706_2298_gb300 import synth
+
+from .gpu_util import from_packed, rel, to_packed
+
+pytestmark = pytest.mark.gpu
+
+L = (8, 8, 8, 8)
+
+
+def weights_to_dev(W):
+    flat = np.concatenate([w.reshape(-1) for w in W]).astype(np.complex64)
+    return torch.from_numpy(flat.view(np.float32).copy()).cuda()
+
+
+def dev_to_weights(t, C=16):
+    flat = t.cpu().numpy().view(np.complex64).astype(np.complex128)
+    dims = [(1, C), (C, C), (C, 1)]
+    out, o = [], 0
+    for cin, cout in dims:
+        n = 9 * 4 * cout * 4 * cin
+        out.append(flat[o:o + n].reshape(9, 4 * cout, 4 * cin))
+        o += n
+    return out
+
+
+@pytest.fixture(scope="module")
+def setup():
+    U = synth.random_gauge(L, 51)
+    ctx = dw.dw_create(L, 0.0, 1.0, U, (4, 4, 4, 4))
+    P = PTNet(WilsonClover(L, U.numpy(), 0.0, 1.0))
+    return ctx, P
+
+
+def test_weight_count():
+    assert dw.ptnet_weight_count(16) == 9 * 16 * (16 + 256 + 16)
+
+
+def test_forward(setup):
+    ctx, P = setup
+    W = init_weights(16, seed=1, scale=0.5)
+    x = synth.gaussian_source(L, 3).numpy()
+    xd = to_packed(ctx, dw.DW_F32, x)
+    yd = ctx.empty_field(dw.DW_F32)
+    dw.ptnet_forward(ctx, weights_to_dev(W), 1, xd, yd)
+    assert rel(from_packed(ctx, dw.DW_F32, yd), P.forward(W, x)) <= 2e-5
+
+
+def test_loss_and_gradient(setup):
+    ctx, P = setup
+    W = init_weights(16, seed=2, scale=0.5)
+    xs = [synth.gaussian_source(L, 4 + k).numpy() for k in range(2)]
+    ys = [synth.gaussian_source(L, 6 + k).numpy() for k in range(2)]
+    loss_o, G = P.loss_and_grad(W, xs, ys)
+    xd = to_packed(ctx, dw.DW_F32, np.stack(xs))
+    yd = to_packed(ctx, dw.DW_F32, np.stack(ys))
+    g = torch.empty(2 * dw.ptnet_weight_count(16), dtype=torch.float32, device="cuda")
+    loss = dw.ptnet_loss_grad(ctx, weights_to_dev(W), 2, xd, yd, g)
+    assert abs(loss - loss_o) <= 1e-4 * loss_o
+    Gd = dev_to_weights(g)
+    for li in range(3):
+        assert rel(Gd[li], G[li]) <= 1e-3, li
+
+
+def test_training_reduces_loss(setup):
+    """Adam steps on the GPU lower the regression loss of the plain procedure's fields."""
+    ctx, P = setup
+    Ns = 4
+    start = synth.start_fields(L, Ns, 9).cuda()
+    x = ctx.empty_field(dw.DW_F32, Ns)
+    dw.dw_pack(ctx, dw.DW_F32, Ns, start, x)
+    dw.dfl_inverse_iteration(ctx, 4, 4, 1, Ns, x)
+    y = x.clone()
+    dw.dfl_inverse_iteration(ctx, 4, 4, 4, Ns, y)
+    W = weights_to_dev(init_weights(16, seed=3, scale=0.1))
+    m = torch.zeros_like(W)
+    v = torch.zeros_like(W)
+    g = torch.empty_like(W)
+    first = dw.ptnet_loss_grad(ctx, W, Ns, x, y, g)
+    loss = first
+    for step in range(1, 41):
+        loss = dw.ptnet_loss_grad(ctx, W, Ns, x, y, g)
+        dw.ptnet_adam(W, g, m, v, step, 3e-3)
+    assert loss < 0.7 * first, (first, loss)
+
+
+def test_learned_build_judge(setup):
+    """With random (untrained) weights the judge rejects the network output and the plain
+    procedure finishes; the subspace is then the plain one."""
+    ctx, P = setup
+    start = synth.start_fields(L, 6, 10).cuda()
+    W = weights_to_dev(init_weights(16, seed=4, scale=3.0))
+    d = dw.deflation_build(ctx, (4, 4, 4, 4), 6, 5, 4, 4, start, basis_prec=dw.DW_F64, iter_prec=dw.DW_F32,
+                           net_weights=W, net_k0=2, net_judge=0.95)
+    info = d.info
+    assert info.rho_in > 0 and info.rho_out > 0
+    if not info.learned_used:
+        d_plain = dw.deflation_build(ctx, (4, 4, 4, 4), 6, 5, 4, 4, start, basis_prec=dw.DW_F64,
+                                     iter_prec=dw.DW_F32)
+        a = torch.empty((6, ctx.V, 4, 3), dtype=torch.complex128, device="cuda")
+        b = torch.empty_like(a)
+        dw.dfl_basis_export(d, a)
+        dw.dfl_basis_export(d_plain, b)
+        assert rel(a.cpu().numpy(), b.cpu().numpy()) <= 1e-6
