@@ -494,28 +494,34 @@ DW_D cplx<T> warp_mv(const cplx<T>* __restrict__ m, const cplx<T>* __restrict__ 
   return acc;
 }
 
-// out[i] = base[i] - sum_d M[blk_i][d] src[lnb[i][d]]   (one warp per block row, lane = row;
-// base may be null).  M column-major: M[((L*8+d)*Ns + col)*Ns + row].
+// out[i] = base[i] - sum_d M[blk_i][d] src[lnb[i][d]]   (one CTA of 8 warps per block row,
+// warp d computes direction d, lane = row of the Ns x Ns blocks; base may be null).
+// M column-major: M[((L*8+d)*Ns + col)*Ns + row].
 template <typename T, int NS>
-__global__ void little_hop_kernel(int n, int Ns, const int* __restrict__ list, const int* __restrict__ lnb,
-                                  const T* __restrict__ M, const T* __restrict__ src, const T* base, T* out) {
-  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (wid >= n) return;
+__global__ void __launch_bounds__(256) little_hop_kernel(int n, int Ns, const int* __restrict__ list,
+                                                         const int* __restrict__ lnb, const T* __restrict__ M,
+                                                         const T* __restrict__ src, const T* base, T* out) {
+  __shared__ double hop64[8][2 * 32];
+  const int r = blockIdx.x;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (r >= n) return;
   const int ns = NS ? NS : Ns;
-  const int L = __ldg(list + wid);
+  const int L = __ldg(list + r);
+  const int j = __ldg(lnb + r * 8 + w);
   const cplx<T>* Mc = reinterpret_cast<const cplx<T>*>(M);
   const cplx<T>* S = reinterpret_cast<const cplx<T>*>(src);
-  cplx<T> acc = {T(0), T(0)};
-#pragma unroll 2
-  for (int d = 0; d < 8; ++d) {
-    const int j = __ldg(lnb + wid * 8 + d);
-    acc = warp_mv<T, NS>(Mc + ((size_t)L * 8 + d) * ns * ns, S + (size_t)j * ns, ns, lane, acc);
-  }
-  if (lane < ns) {
+  const cplx<T> acc = warp_mv<T, NS>(Mc + ((size_t)L * 8 + w) * ns * ns, S + (size_t)j * ns, ns, lane,
+                                     cplx<T>{T(0), T(0)});
+  hop64[w][2 * lane] = (double)acc.re;
+  hop64[w][2 * lane + 1] = (double)acc.im;
+  __syncthreads();
+  if (w == 0 && lane < ns) {
+    double re = 0, im = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) { re += hop64[q][2 * lane]; im += hop64[q][2 * lane + 1]; }
     cplx<T>* O = reinterpret_cast<cplx<T>*>(out);
-    cplx<T> b = base ? reinterpret_cast<const cplx<T>*>(base)[(size_t)wid * ns + lane] : cplx<T>{T(0), T(0)};
-    O[(size_t)wid * ns + lane] = b - acc;
+    cplx<T> b = base ? reinterpret_cast<const cplx<T>*>(base)[(size_t)r * ns + lane] : cplx<T>{T(0), T(0)};
+    O[(size_t)r * ns + lane] = b - cplx<T>{(T)re, (T)im};
   }
 }
 
@@ -620,29 +626,39 @@ struct CoopShared {
   double a[2 * COOP_NKV], c[COOP_NKV], beta[2 * COOP_NKV];
   double bb[COOP_NKV][2 * COOP_NKV];
   double z[2 * 32];
+  double hop[8][2 * 32];     // per-direction partial sums of one block row
   int phase;
 };
 
-// sum nv per-thread values over the grid; result in sh.res (all CTAs).  After the barrier each CTA
-// copies the partials into shared memory with all threads loading in parallel, then warp w adds the
-// partials of values j = w, w + 8, ... in a fixed tree: identical, deterministic sums in every CTA.
-DW_D void coop_reduce(cg::grid_group& grid, CoopShared& sh, double* acc, int nv, double* partial_base,
-                      double* stage) {
+// Sum nv <= NV per-thread values over the grid; result in sh.res (all CTAs).  The NV values are
+// reduced across the warp with interleaved shuffles; after the barrier each CTA copies the partials
+// into shared memory with all threads loading in parallel, then warp w adds the partials of values
+// j = w, w + 8, ... in a fixed tree: identical, deterministic sums in every CTA.
+template <int NV>
+DW_D void coop_reduce(cg::grid_group& grid, CoopShared& sh, const double (&acc)[NV], int nv,
+                      double* partial_base, double* stage) {
   // two partial buffers used alternately: a CTA that runs ahead into the next reduction
   // cannot overwrite partials another CTA is still adding up
   double* partial = partial_base + (size_t)(sh.phase & 1) * gridDim.x * COOP_NV;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int j = 0; j < nv; ++j) {
-    double x = acc[j];
+  double x[NV];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) sh.ws[w][j] = x;
+  for (int j = 0; j < NV; ++j) x[j] = acc[j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int j = 0; j < NV; ++j) x[j] += __shfl_xor_sync(0xffffffffu, x[j], o);
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j)
+      if (j < nv) sh.ws[w][j] = x[j];
   }
   __syncthreads();
   if (threadIdx.x < nv) {
-    double x = 0;
-    for (int q = 0; q < COOP_THREADS / 32; ++q) x += sh.ws[q][threadIdx.x];
-    partial[blockIdx.x * COOP_NV + threadIdx.x] = x;
+    double y = 0;
+#pragma unroll
+    for (int q = 0; q < COOP_THREADS / 32; ++q) y += sh.ws[q][threadIdx.x];
+    partial[blockIdx.x * COOP_NV + threadIdx.x] = y;
   }
   grid.sync();
   const int G = gridDim.x;
@@ -652,66 +668,78 @@ DW_D void coop_reduce(cg::grid_group& grid, CoopShared& sh, double* acc, int nv,
   }
   __syncthreads();
   for (int j = w; j < nv; j += COOP_THREADS / 32) {
-    double x = 0;
-    for (int q = lane; q < G; q += 32) x += stage[j * G + q];
+    double y = 0;
+    for (int q = lane; q < G; q += 32) y += stage[j * G + q];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) sh.res[j] = x;
+    for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+    if (lane == 0) sh.res[j] = y;
   }
   __syncthreads();
   if (threadIdx.x == 0) sh.phase += 1;
   __syncthreads();
 }
 
-// out[r] = base[r] - sum_d M[list[r]][d] src[lnb[r][d]]  (warp per block row; base may be null)
+// out[r] = base[r] + out_sign * sum_d M[list[r]][d] src[lnb[r][d]]: one CTA per block row,
+// warp d computes direction d, the 8 partial sums meet in shared memory
 template <typename T, int NS>
-DW_D void coop_hop(int nrow, int Ns, const int* list, const int* lnb, const T* M, const cplx<T>* src,
-                   const cplx<T>* base, cplx<T>* out, T out_sign) {
-  const int lane = threadIdx.x & 31;
-  const int nw = gridDim.x * (COOP_THREADS / 32);
+DW_D void coop_hop(CoopShared& sh, int nrow, int Ns, const int* list, const int* lnb, const T* M,
+                   const cplx<T>* src, const cplx<T>* base, cplx<T>* out, T out_sign) {
   const int ns = NS ? NS : Ns;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const cplx<T>* Mc = reinterpret_cast<const cplx<T>*>(M);
-  for (int r = blockIdx.x * (COOP_THREADS / 32) + (threadIdx.x >> 5); r < nrow; r += nw) {
+  for (int r = blockIdx.x; r < nrow; r += gridDim.x) {
     const int L = list[r];
-    cplx<T> acc = {T(0), T(0)};
-#pragma unroll 2
-    for (int d = 0; d < 8; ++d) {
-      const int j = lnb[r * 8 + d];
-      acc = warp_mv<T, NS>(Mc + ((size_t)L * 8 + d) * ns * ns, src + (size_t)j * ns, ns, lane, acc);
-    }
-    if (lane < ns) {
+    const int j = lnb[r * 8 + w];
+    cplx<T> acc = warp_mv<T, NS>(Mc + ((size_t)L * 8 + w) * ns * ns, src + (size_t)j * ns, ns, lane,
+                                 cplx<T>{T(0), T(0)});
+    sh.hop[w][2 * lane] = (double)acc.re;
+    sh.hop[w][2 * lane + 1] = (double)acc.im;
+    __syncthreads();
+    if (w == 0 && lane < ns) {
+      double re = 0, im = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) { re += sh.hop[q][2 * lane]; im += sh.hop[q][2 * lane + 1]; }
       cplx<T> bse = base ? base[(size_t)r * ns + lane] : cplx<T>{T(0), T(0)};
-      out[(size_t)r * ns + lane] = bse + out_sign * acc;
+      out[(size_t)r * ns + lane] = bse + out_sign * cplx<T>{(T)re, (T)im};
     }
+    __syncthreads();
   }
 }
 
 // y = B^ x = x - M_eo (M_oe x); ends with a grid barrier
 template <typename T, int NS>
-DW_D void coop_bhat(cg::grid_group& grid, const CoopArgs<T>& a, const cplx<T>* x, cplx<T>* tmpo, cplx<T>* y) {
-  coop_hop<T, NS>(a.No, a.Ns, a.list_o, a.lnb_o, a.M, x, nullptr, tmpo, T(1));    // tmpo = M_oe x
+DW_D void coop_bhat(cg::grid_group& grid, CoopShared& sh, const CoopArgs<T>& a, const cplx<T>* x, cplx<T>* tmpo,
+                    cplx<T>* y) {
+  coop_hop<T, NS>(sh, a.No, a.Ns, a.list_o, a.lnb_o, a.M, x, nullptr, tmpo, T(1));    // tmpo = M_oe x
   grid.sync();
-  coop_hop<T, NS>(a.Ne, a.Ns, a.list_e, a.lnb_e, a.M, tmpo, x, y, T(-1));        // y = x - M_eo tmpo
+  coop_hop<T, NS>(sh, a.Ne, a.Ns, a.list_e, a.lnb_e, a.M, tmpo, x, y, T(-1));        // y = x - M_eo tmpo
   grid.sync();
 }
 
-// u -= Bg A~^{-1} g^+ u  (P~_L, in place; elementwise part by the owning thread, no trailing barrier)
+// u -= Bg A~^{-1} g^+ u  (P~_L, in place); with add_to set, only z = A~^{-1} g^+ u is formed and
+// add_to += g z is applied instead.  Elementwise parts by the owning thread, no trailing barrier.
 template <typename T, int NS>
-DW_D void coop_PL(cg::grid_group& grid, CoopShared& sh, const CoopArgs<T>& a, cplx<T>* u, double* acc,
-                  const cplx<T>* gsrc, const cplx<T>* bgsrc, bool subtract_from_u, double* stage) {
+DW_D void coop_PL(cg::grid_group& grid, CoopShared& sh, const CoopArgs<T>& a, cplx<T>* u, const cplx<T>* gsrc,
+                  const cplx<T>* bgsrc, cplx<T>* add_to, double* stage) {
+  constexpr int NSM = NS ? NS : 32;
   const size_t n = (size_t)a.Ne * a.Ns;
   const size_t tid = blockIdx.x * (size_t)COOP_THREADS + threadIdx.x, nth = (size_t)gridDim.x * COOP_THREADS;
   const int Ns = NS ? NS : a.Ns;
-  for (int j = 0; j < 2 * Ns; ++j) acc[j] = 0;
+  double acc[2 * NSM];
+#pragma unroll
+  for (int j = 0; j < 2 * NSM; ++j) acc[j] = 0;
   for (size_t i = tid; i < n; i += nth) {
-    cplx<T> x = u[i];
-    for (int l = 0; l < Ns; ++l) {
-      cplx<T> gl = gsrc[(size_t)l * n + i];
-      acc[2 * l] += (double)gl.re * x.re + (double)gl.im * x.im;
-      acc[2 * l + 1] += (double)gl.re * x.im - (double)gl.im * x.re;
+    const cplx<T> x = u[i];
+#pragma unroll
+    for (int l = 0; l < NSM; ++l) {
+      if (l < Ns) {
+        const cplx<T> gl = gsrc[(size_t)l * n + i];
+        acc[2 * l] += (double)gl.re * x.re + (double)gl.im * x.im;
+        acc[2 * l + 1] += (double)gl.re * x.im - (double)gl.im * x.re;
+      }
     }
   }
-  coop_reduce(grid, sh, acc, 2 * Ns, a.partial, stage);
+  coop_reduce<2 * NSM>(grid, sh, acc, 2 * Ns, a.partial, stage);
   if (threadIdx.x < Ns) {          // z = A~^{-1} y
     const cplx<T>* Ai = reinterpret_cast<const cplx<T>*>(a.Ainv);
     double zr = 0, zi = 0;
@@ -725,25 +753,29 @@ DW_D void coop_PL(cg::grid_group& grid, CoopShared& sh, const CoopArgs<T>& a, cp
     sh.z[2 * threadIdx.x + 1] = zi;
   }
   __syncthreads();
+  cplx<T>* tgt = add_to ? add_to : u;
+  const cplx<T>* vecs = add_to ? gsrc : bgsrc;
+  const T sg = add_to ? T(1) : T(-1);
   for (size_t i = tid; i < n; i += nth) {
-    cplx<T> x = u[i];
-    for (int l = 0; l < Ns; ++l) {
-      cplx<T> zl = {(T)sh.z[2 * l], (T)sh.z[2 * l + 1]};
-      if (subtract_from_u) x -= zl * bgsrc[(size_t)l * n + i];
-      else x += zl * bgsrc[(size_t)l * n + i];
+    cplx<T> x = tgt[i];
+#pragma unroll
+    for (int l = 0; l < NSM; ++l) {
+      if (l < Ns) {
+        const cplx<T> zl = {(T)sh.z[2 * l], (T)sh.z[2 * l + 1]};
+        x += sg * (zl * vecs[(size_t)l * n + i]);
+      }
     }
-    u[i] = x;
+    tgt[i] = x;
   }
 }
 
 template <typename T, int NS>
-__global__ void __launch_bounds__(COOP_THREADS) little_gcr_coop_kernel(CoopArgs<T> a) {
+__global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_kernel(CoopArgs<T> a) {
   cg::grid_group grid = cg::this_grid();
   __shared__ CoopShared sh;
   extern __shared__ double stage[];     // [COOP_NV][gridDim]
   if (threadIdx.x == 0) sh.phase = 0;
   __syncthreads();
-  double acc[COOP_NV];
   const size_t n = (size_t)a.Ne * a.Ns;
   const size_t tid = blockIdx.x * (size_t)COOP_THREADS + threadIdx.x, nth = (size_t)gridDim.x * COOP_THREADS;
   const int nkv = a.nkv;
@@ -761,15 +793,15 @@ __global__ void __launch_bounds__(COOP_THREADS) little_gcr_coop_kernel(CoopArgs<
 
   // rhsd = P~_L b, rho = rhsd, v = 0
   for (size_t i = tid; i < n; i += nth) rhsd[i] = b[i];
-  if (a.a3) coop_PL<T, NS>(grid, sh, a, rhsd, acc, g, Bg, true, stage);
-  acc[0] = 0;
+  if (a.a3) coop_PL<T, NS>(grid, sh, a, rhsd, g, Bg, nullptr, stage);
+  double s1[1] = {0};
   for (size_t i = tid; i < n; i += nth) {
     cplx<T> x = rhsd[i];
     rho[i] = x;
     v[i] = {T(0), T(0)};
-    acc[0] += (double)x.re * x.re + (double)x.im * x.im;
+    s1[0] += (double)x.re * x.re + (double)x.im * x.im;
   }
-  coop_reduce(grid, sh, acc, 1, a.partial, stage);
+  coop_reduce<1>(grid, sh, s1, 1, a.partial, stage);
   const double bn = sqrt(sh.res[0]);
   double rn = bn;
   int total = 0;
@@ -780,53 +812,61 @@ __global__ void __launch_bounds__(COOP_THREADS) little_gcr_coop_kernel(CoopArgs<
       cplx<T>* xk = xi(k);
       for (size_t i = tid; i < n; i += nth) xk[i] = rho[i];
       grid.sync();
-      coop_bhat<T, NS>(grid, a, xk, tmpo, ck);
-      if (a.a3) coop_PL<T, NS>(grid, sh, a, ck, acc, g, Bg, true, stage);
+      coop_bhat<T, NS>(grid, sh, a, xk, tmpo, ck);
+      if (a.a3) coop_PL<T, NS>(grid, sh, a, ck, g, Bg, nullptr, stage);
       if (k > 0) {
-        for (int j = 0; j < 2 * k; ++j) acc[j] = 0;
+        double sb[2 * COOP_NKV];
+#pragma unroll
+        for (int j = 0; j < 2 * COOP_NKV; ++j) sb[j] = 0;
         for (size_t i = tid; i < n; i += nth) {
-          cplx<T> y = ck[i];
-          for (int j = 0; j < k; ++j) {
-            cplx<T> x = chi(j)[i];
-            acc[2 * j] += (double)x.re * y.re + (double)x.im * y.im;
-            acc[2 * j + 1] += (double)x.re * y.im - (double)x.im * y.re;
+          const cplx<T> y = ck[i];
+#pragma unroll
+          for (int j = 0; j < COOP_NKV; ++j) {
+            if (j < k) {
+              const cplx<T> x = chi(j)[i];
+              sb[2 * j] += (double)x.re * y.re + (double)x.im * y.im;
+              sb[2 * j + 1] += (double)x.re * y.im - (double)x.im * y.re;
+            }
           }
         }
-        coop_reduce(grid, sh, acc, 2 * k, a.partial, stage);
+        coop_reduce<2 * COOP_NKV>(grid, sh, sb, 2 * k, a.partial, stage);
         if (threadIdx.x < 2 * k) sh.bb[threadIdx.x >> 1][2 * k + (threadIdx.x & 1)] = sh.res[threadIdx.x];
         __syncthreads();
         for (size_t i = tid; i < n; i += nth) {
           cplx<T> y = ck[i];
-          for (int j = 0; j < k; ++j) {
-            cplx<T> bj = {(T)sh.bb[j][2 * k], (T)sh.bb[j][2 * k + 1]};
-            y -= bj * chi(j)[i];
+#pragma unroll
+          for (int j = 0; j < COOP_NKV; ++j) {
+            if (j < k) {
+              const cplx<T> bj = {(T)sh.bb[j][2 * k], (T)sh.bb[j][2 * k + 1]};
+              y -= bj * chi(j)[i];
+            }
           }
           ck[i] = y;
         }
       }
-      acc[0] = acc[1] = acc[2] = 0;
+      double s3[3] = {0, 0, 0};
       for (size_t i = tid; i < n; i += nth) {
-        cplx<T> x = ck[i], y = rho[i];
-        acc[0] += (double)x.re * y.re + (double)x.im * y.im;
-        acc[1] += (double)x.re * y.im - (double)x.im * y.re;
-        acc[2] += (double)x.re * x.re + (double)x.im * x.im;
+        const cplx<T> x = ck[i], y = rho[i];
+        s3[0] += (double)x.re * y.re + (double)x.im * y.im;
+        s3[1] += (double)x.re * y.im - (double)x.im * y.re;
+        s3[2] += (double)x.re * x.re + (double)x.im * x.im;
       }
-      coop_reduce(grid, sh, acc, 3, a.partial, stage);
+      coop_reduce<3>(grid, sh, s3, 3, a.partial, stage);
       const double cn = sqrt(sh.res[2]);
       if (!(cn > 0)) break;
       const double ar = sh.res[0] / cn, ai = sh.res[1] / cn;
       if (threadIdx.x == 0) { sh.c[k] = cn; sh.a[2 * k] = ar; sh.a[2 * k + 1] = ai; }
-      acc[0] = 0;
+      s1[0] = 0;
       const T inv = (T)(1.0 / cn);
       const cplx<T> ak = {(T)ar, (T)ai};
       for (size_t i = tid; i < n; i += nth) {
-        cplx<T> x = inv * ck[i];
+        const cplx<T> x = inv * ck[i];
         ck[i] = x;
-        cplx<T> y = rho[i] - ak * x;
+        const cplx<T> y = rho[i] - ak * x;
         rho[i] = y;
-        acc[0] += (double)y.re * y.re + (double)y.im * y.im;
+        s1[0] += (double)y.re * y.re + (double)y.im * y.im;
       }
-      coop_reduce(grid, sh, acc, 1, a.partial, stage);
+      coop_reduce<1>(grid, sh, s1, 1, a.partial, stage);
       rn = sqrt(sh.res[0]);
       ++total;
       if (rn <= a.tol * bn) { ++k; break; }
@@ -853,29 +893,23 @@ __global__ void __launch_bounds__(COOP_THREADS) little_gcr_coop_kernel(CoopArgs<
     grid.sync();
     if (k == 0) break;
     // true residual of the deflated system
-    coop_bhat<T, NS>(grid, a, v, tmpo, t);
-    if (a.a3) coop_PL<T, NS>(grid, sh, a, t, acc, g, Bg, true, stage);
-    acc[0] = 0;
+    coop_bhat<T, NS>(grid, sh, a, v, tmpo, t);
+    if (a.a3) coop_PL<T, NS>(grid, sh, a, t, g, Bg, nullptr, stage);
+    s1[0] = 0;
     for (size_t i = tid; i < n; i += nth) {
-      cplx<T> y = rhsd[i] - t[i];
+      const cplx<T> y = rhsd[i] - t[i];
       rho[i] = y;
-      acc[0] += (double)y.re * y.re + (double)y.im * y.im;
+      s1[0] += (double)y.re * y.re + (double)y.im * y.im;
     }
-    coop_reduce(grid, sh, acc, 1, a.partial, stage);
+    coop_reduce<1>(grid, sh, s1, 1, a.partial, stage);
     rn = sqrt(sh.res[0]);
   }
   if (a.a3) {
     // v = chi + g A~^{-1} g^+ (b - B^ chi)
     grid.sync();
-    coop_bhat<T, NS>(grid, a, v, tmpo, t);
+    coop_bhat<T, NS>(grid, sh, a, v, tmpo, t);
     for (size_t i = tid; i < n; i += nth) t[i] = b[i] - t[i];
-    coop_PL<T, NS>(grid, sh, a, t, acc, g, g, false, stage);   // t += g z  (z from g^+ t); only z is used below
-    // coop_PL updated t, not v: redo the elementwise part on v with the same z
-    for (size_t i = tid; i < n; i += nth) {
-      cplx<T> x = v[i];
-      for (int l = 0; l < a.Ns; ++l) x += cplx<T>{(T)sh.z[2 * l], (T)sh.z[2 * l + 1]} * g[(size_t)l * n + i];
-      v[i] = x;
-    }
+    coop_PL<T, NS>(grid, sh, a, t, g, g, v, stage);     // v += g z,  z = A~^{-1} g^+ t
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.out[0] = total;
@@ -904,11 +938,11 @@ template <> const double* Bgp<double>(dfl_ctx* d) { return d->Bg64; }
 // B^ v_e = v_e - M_eo (M_oe v_e);  tmp_o: No*Ns complex
 template <typename T>
 static void apply_bhat(dfl_ctx* d, const T* ve, T* tmp_o, T* out, cudaStream_t s) {
-  NS_DISPATCH(d->Ns, (little_hop_kernel<T, NSV><<<warps_grid(d->No), 128, 0, s>>>(
+  NS_DISPATCH(d->Ns, (little_hop_kernel<T, NSV><<<d->No, 256, 0, s>>>(
                                 d->No, d->Ns, d->d_list[1], d->d_lnb[1], Mp<T>(d), ve, nullptr, tmp_o)));
   dw_note_launch();
   // tmp_o = -M_oe v_e; out = v_e - M_eo(M_oe v_e) = v_e + M_eo tmp_o  ->  use base = v_e and src = -tmp
-  NS_DISPATCH(d->Ns, (little_hop_kernel<T, NSV><<<warps_grid(d->Ne), 128, 0, s>>>(
+  NS_DISPATCH(d->Ns, (little_hop_kernel<T, NSV><<<d->Ne, 256, 0, s>>>(
                                 d->Ne, d->Ns, d->d_list[0], d->d_lnb[0], Mp<T>(d), tmp_o, nullptr, out)));
   dw_note_launch();
   // out = -M_eo tmp_o = M_eo M_oe v_e ; final = v_e - out
@@ -1281,14 +1315,14 @@ static int little_solve_t(dfl_ctx* d, const T* w, T* v, double tol, int maxit, i
                                                                              Binvp<T>(d), wo, yo)));
   NS_DISPATCH(Ns, (little_bdiag_kernel<T, NSV><<<warps_grid(d->Ne), 128, 0, s>>>(d->Ne, Ns, d->d_list[0],
                                                                              Binvp<T>(d), we, wt)));
-  NS_DISPATCH(Ns, (little_hop_kernel<T, NSV><<<warps_grid(d->Ne), 128, 0, s>>>(d->Ne, Ns, d->d_list[0],
+  NS_DISPATCH(Ns, (little_hop_kernel<T, NSV><<<d->Ne, 256, 0, s>>>(d->Ne, Ns, d->d_list[0],
                                                                            d->d_lnb[0], Mp<T>(d), yo, wt, we)));
   dw_note_launch(); dw_note_launch(); dw_note_launch();
   // we now holds w~_e ; solve B^ v_e = w~_e into wt
   rc = little_gcr<T>(d, we, wt, tol, maxit, nkv, iters, relres, s);
   if (rc < 0) return rc;
   // v_o = yo - M_oe v_e  -> into wo
-  NS_DISPATCH(Ns, (little_hop_kernel<T, NSV><<<warps_grid(d->No), 128, 0, s>>>(d->No, Ns, d->d_list[1],
+  NS_DISPATCH(Ns, (little_hop_kernel<T, NSV><<<d->No, 256, 0, s>>>(d->No, Ns, d->d_list[1],
                                                                            d->d_lnb[1], Mp<T>(d), wt, yo, wo)));
   dw_note_launch();
   little_scatter_kernel<T, T><<<ge, 256, 0, s>>>(d->Ne, Ns, d->d_list[0], wt, v); dw_note_launch();

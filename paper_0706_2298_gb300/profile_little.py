@@ -27,9 +27,15 @@ def main():
     d = dw.deflation_build(ctx, (4, 4, 4, 4), 20, 4, 4, 4, synth.start_fields(L, 20, 3).cuda())
     w = torch.randn(d.Nb * d.Ns * 2, dtype=torch.float32, device="cuda")
     v = torch.empty_like(w)
+    import time
     for _ in range(args.solves):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         rc, it, rr = dw.little_dirac_solve(d, dw.DW_F32, w, v, 1e-6, 2000)
-        print("little solve", rc, it, rr, flush=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        print(f"little solve rc {rc} iterations {it} relres {rr:.3e} time {dt * 1e3:.3f} ms "
+              f"({dt * 1e6 / max(it, 1):.1f} us/iteration)", flush=True)
 
 
 if __name__ == "__main__":
