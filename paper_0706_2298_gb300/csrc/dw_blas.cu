@@ -44,10 +44,14 @@ __device__ void grid_reduce(double* v, double* partial, unsigned* count, double*
   __syncthreads();
   if (!last) return;
   __threadfence();
-  if (threadIdx.x < NV) {
+  // the last CTA adds the CTA partials: warp w owns values k = w, w + 8, ...; lane q adds
+  // partials q, q + 32, ... (independent loads, all in flight), then a fixed butterfly
+  for (int k = w; k < NV; k += RB / 32) {
     double s = 0;
-    for (unsigned b = 0; b < gridDim.x; ++b) s += ((volatile double*)partial)[b * NV + threadIdx.x];
-    out[threadIdx.x] = s;
+#pragma unroll 8
+    for (unsigned b = lane; b < gridDim.x; b += 32) s += __ldcg(partial + b * NV + k);
+    s = warp_sum(s);
+    if (lane == 0) out[k] = s;
   }
   if (threadIdx.x == 0) *count = 0;
 }

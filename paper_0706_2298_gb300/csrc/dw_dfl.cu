@@ -261,6 +261,95 @@ __global__ void __launch_bounds__(128) restrict_kernel(Geom g, const int* __rest
   }
 }
 
+// Warp sum of M values per lane by recursive halving: at each butterfly step a lane keeps
+// one half of its values, sends the other half to its partner and adds what it receives, so
+// M values cost about M shuffles instead of 5 M.  When M becomes odd the remaining steps
+// exchange all values.  On return x[0..M_final) holds the warp sums of the values
+// base, ..., base + M_final - 1 (base depends on the lane; lanes that differ only in the
+// bits of the full-exchange steps hold the same values).  Fixed order: deterministic.
+template <typename T, int M, int O>
+struct WarpHalve {
+  __host__ __device__ static constexpr int final_m() {
+    if constexpr (O == 0) return M;
+    else if constexpr (M % 2 == 0) return WarpHalve<T, M / 2, O / 2>::final_m();
+    else return WarpHalve<T, M, O / 2>::final_m();
+  }
+  static DW_D void run(T* x, int lane, int& base) {
+    if constexpr (O == 0) {
+      return;
+    } else if constexpr (M % 2 == 0) {
+      constexpr int H = M / 2;
+      const bool up = (lane & O) != 0;
+#pragma unroll
+      for (int i = 0; i < H; ++i) {
+        const T send = up ? x[i] : x[i + H];
+        const T keep = up ? x[i + H] : x[i];
+        x[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+      }
+      if (up) base += H;
+      WarpHalve<T, H, O / 2>::run(x, lane, base);
+    } else {
+#pragma unroll
+      for (int i = 0; i < M; ++i) x[i] += __shfl_xor_sync(0xffffffffu, x[i], O);
+      WarpHalve<T, M, O / 2>::run(x, lane, base);
+    }
+  }
+};
+
+// c[L][k] = (phi^L_k, psi), Ns known at compile time: CTA per deflation block, per-thread
+// partial sums in the working precision, CTA sum by warp halving + shared memory.
+template <typename T, int NS>
+__global__ void __launch_bounds__(128, 4) restrict_ns_kernel(Geom g, const int* __restrict__ sub, int nsub,
+                                                             const double* b64, const uint4* b16,
+                                                             const T* __restrict__ psi0, T* __restrict__ c0,
+                                                             int nrhs, size_t fstride, size_t cstride) {
+  using WH = WarpHalve<T, 2 * NS, 16>;
+  constexpr int MF = WH::final_m();
+  __shared__ T sh[4][2 * NS];
+  const int L = blockIdx.x;
+  const size_t V = g.V;
+  const int nsite = nsub * g.svol;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int rhs = 0; rhs < nrhs; ++rhs) {
+    const T* psi = psi0 + (size_t)rhs * fstride;
+    T* c = c0 + (size_t)rhs * cstride;
+    T acc[2 * NS];
+#pragma unroll
+    for (int k = 0; k < 2 * NS; ++k) acc[k] = T(0);
+    for (int t = threadIdx.x; t < nsite; t += blockDim.x) {
+      const long long i = dfl_site(g, sub, nsub, L, t);
+      cplx<T> p[12];
+      load_site<T, 12>(psi, V, i, p);
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        cplx<T> f[12];
+        load_basis<T>(b64, b16, V, k, i, f);
+        T re = 0, im = 0;
+#pragma unroll
+        for (int j = 0; j < 12; ++j) {
+          re += f[j].re * p[j].re + f[j].im * p[j].im;
+          im += f[j].re * p[j].im - f[j].im * p[j].re;
+        }
+        acc[2 * k] += re;
+        acc[2 * k + 1] += im;
+      }
+    }
+    int base = 0;
+    WH::run(acc, lane, base);
+    // lanes holding the same index block hold equal sums; all of them store
+#pragma unroll
+    for (int m = 0; m < MF; ++m) sh[w][base + m] = acc[m];
+    __syncthreads();
+    if (threadIdx.x < 2 * NS) {
+      T y = sh[0][threadIdx.x];
+#pragma unroll
+      for (int q = 1; q < 4; ++q) y += sh[q][threadIdx.x];
+      c[(size_t)L * 2 * NS + threadIdx.x] = y;
+    }
+    __syncthreads();
+  }
+}
+
 // psi = mode 0: Phi c ; 1: psi + Phi c ; 2: psi - Phi c
 template <typename T>
 __global__ void __launch_bounds__(128) prolong_kernel(Geom g, const int* __restrict__ sap2dfl, int Ns,
@@ -601,12 +690,18 @@ inline unsigned warps_grid(int n, int threads = 128) { return (unsigned)((n * 32
 // ------------------------------------------------------------------ cooperative little GCR (A.2-A.4)
 // The whole even-odd, globally deflated little GCR in one persistent kernel:
 // grid-wide barriers replace the host round trips of the host-driven loop.
-// Reductions: per-thread partials -> per-CTA sums in shared memory -> one
-// partial per CTA in global memory -> after the barrier every CTA adds the
-// partials in CTA order (identical, deterministic values in every CTA).
+// Ownership: CTA c owns the contiguous slice [c S, (c+1) S) of the n = Ne Ns
+// vector entries (elementwise work) and the contiguous range of block rows
+// [c R, (c+1) R) of each parity (hops).  Reductions: per-CTA sums in shared
+// memory -> one partial per CTA in global memory -> after the barrier every
+// CTA adds the partials in CTA order (identical, deterministic values in every
+// CTA).  Inner products with many vectors are CTA-slice GEMVs: warp w owns the
+// vectors j = w, w + 8, ...
 constexpr int COOP_THREADS = 256;
-constexpr int COOP_NV = 64;
-constexpr int COOP_NKV = 24;
+constexpr int COOP_WARPS = COOP_THREADS / 32;
+constexpr int COOP_NV = 64;          // values per grid reduction
+constexpr int COOP_NKV = 24;         // Krylov vectors per cycle
+constexpr int COOP_CH = 16;          // block rows per hop chunk
 
 template <typename T>
 struct CoopArgs {
@@ -615,63 +710,80 @@ struct CoopArgs {
   const T *M, *g, *Bg, *Ainv, *b;
   T* v;
   T* work;            // (2 nkv + 4) vectors of Ne*Ns complex
-  double* partial;    // [2][gridDim][COOP_NV]
+  T* partial;         // [2][COOP_NV][gridDim]
   double* out;        // [0] iterations, [1] relative residual
   double tol;
 };
 
+// Shared state of one CTA.  All arithmetic of the solver runs in the working precision T:
+// FP32 throughput is many times that of FP64 on this part, and the FP32 solve is a
+// preconditioner-level solve whose residual is recomputed in FP64 by the caller.
+template <typename T>
 struct CoopShared {
-  double ws[COOP_THREADS / 32][COOP_NV];
-  double res[COOP_NV];
-  double a[2 * COOP_NKV], c[COOP_NKV], beta[2 * COOP_NKV];
-  double bb[COOP_NKV][2 * COOP_NKV];
-  double z[2 * 32];
-  double hop[8][2 * 32];     // per-direction partial sums of one block row
+  T ws[COOP_WARPS][4];
+  T cta[COOP_NV];            // this CTA's share of the values being reduced
+  T res[COOP_NV];            // grid-wide sums
+  T a[2 * COOP_NKV], c[COOP_NKV], beta[2 * COOP_NKV];
+  T bb[COOP_NKV][2 * COOP_NKV];
+  T z[2 * 32];
+  T ainv[2 * 32 * 32];       // A~^{-1}, row-major
   int phase;
 };
 
-// Sum nv <= NV per-thread values over the grid; result in sh.res (all CTAs).  The NV values are
-// reduced across the warp with interleaved shuffles; after the barrier each CTA copies the partials
-// into shared memory with all threads loading in parallel, then warp w adds the partials of values
-// j = w, w + 8, ... in a fixed tree: identical, deterministic sums in every CTA.
-template <int NV>
-DW_D void coop_reduce(cg::grid_group& grid, CoopShared& sh, const double (&acc)[NV], int nv,
-                      double* partial_base, double* stage) {
-  // two partial buffers used alternately: a CTA that runs ahead into the next reduction
-  // cannot overwrite partials another CTA is still adding up
-  double* partial = partial_base + (size_t)(sh.phase & 1) * gridDim.x * COOP_NV;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  double x[NV];
+// dynamic shared memory of the cooperative kernel: reduction staging + hop partial sums
+template <typename T>
+inline size_t coop_dyn_smem(int grid) {
+  return ((size_t)COOP_NV * grid + (size_t)COOP_CH * 8 * 64) * sizeof(T);
+}
+
+struct CoopSlice {
+  size_t s0, s1;
+};
+
+DW_D CoopSlice coop_slice(size_t n) {
+  const size_t S = (n + gridDim.x - 1) / gridDim.x;
+  const size_t s0 = min(n, (size_t)blockIdx.x * S);
+  return {s0, min(n, s0 + S)};
+}
+
+template <typename T>
+DW_D T warp_allsum(T y) {
 #pragma unroll
-  for (int j = 0; j < NV; ++j) x[j] = acc[j];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-    for (int j = 0; j < NV; ++j) x[j] += __shfl_xor_sync(0xffffffffu, x[j], o);
-  if (lane == 0) {
-#pragma unroll
-    for (int j = 0; j < NV; ++j)
-      if (j < nv) sh.ws[w][j] = x[j];
-  }
-  __syncthreads();
-  if (threadIdx.x < nv) {
-    double y = 0;
-#pragma unroll
-    for (int q = 0; q < COOP_THREADS / 32; ++q) y += sh.ws[q][threadIdx.x];
-    partial[blockIdx.x * COOP_NV + threadIdx.x] = y;
-  }
-  grid.sync();
+  for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+  return y;
+}
+
+// Sum the nv values sh.cta[0..nv) over all CTAs; result in sh.res (all CTAs).
+// Two partial buffers used alternately: a CTA that runs ahead into the next
+// reduction cannot overwrite partials another CTA is still adding up.
+template <typename T>
+DW_D void coop_reduce(cg::grid_group& grid, CoopShared<T>& sh, int nv, T* partial_base, T* stage) {
   const int G = gridDim.x;
-  for (int idx = threadIdx.x; idx < G * nv; idx += COOP_THREADS) {
-    const int q = idx / nv, j = idx - q * nv;
-    stage[j * G + q] = __ldcg(partial + q * COOP_NV + j);
+  T* partial = partial_base + (size_t)(sh.phase & 1) * G * COOP_NV;
+  __syncthreads();
+  if (threadIdx.x < nv) partial[threadIdx.x * G + blockIdx.x] = sh.cta[threadIdx.x];
+  grid.sync();
+  // copy the nv x G partials into shared memory, 8 loads in flight per thread
+  const int tot = G * nv;
+  for (int base = 0; base < tot; base += 8 * COOP_THREADS) {
+    T v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * COOP_THREADS + threadIdx.x;
+      v[u] = idx < tot ? __ldcg(partial + idx) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * COOP_THREADS + threadIdx.x;
+      if (idx < tot) stage[idx] = v[u];
+    }
   }
   __syncthreads();
-  for (int j = w; j < nv; j += COOP_THREADS / 32) {
-    double y = 0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int j = w; j < nv; j += COOP_WARPS) {
+    T y = 0;
     for (int q = lane; q < G; q += 32) y += stage[j * G + q];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+    y = warp_allsum(y);
     if (lane == 0) sh.res[j] = y;
   }
   __syncthreads();
@@ -679,28 +791,117 @@ DW_D void coop_reduce(cg::grid_group& grid, CoopShared& sh, const double (&acc)[
   __syncthreads();
 }
 
-// out[r] = base[r] + out_sign * sum_d M[list[r]][d] src[lnb[r][d]]: one CTA per block row,
-// warp d computes direction d, the 8 partial sums meet in shared memory
+// per-thread values x[0..NV) -> their CTA sums in sh.cta[0..NV)
+template <typename T, int NV>
+DW_D void cta_sum(CoopShared<T>& sh, T (&x)[NV]) {
+  static_assert(NV <= 4, "few values only");
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    const T y = warp_allsum(x[j]);
+    if (lane == 0) sh.ws[w][j] = y;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    T y = 0;
+#pragma unroll
+    for (int q = 0; q < COOP_WARPS; ++q) y += sh.ws[q][threadIdx.x];
+    sh.cta[threadIdx.x] = y;
+  }
+}
+
+// sh.cta[2j], sh.cta[2j+1] = this CTA's share of (X_j, y) for j < nvec; X_j = X + j xstride.
+// Starts with a CTA barrier (y may have been written by other threads of the CTA).
+template <typename T>
+DW_D void cta_dots(CoopShared<T>& sh, const cplx<T>* X, size_t xstride, int nvec, const cplx<T>* y,
+                   const CoopSlice& sl) {
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int j = w; j < nvec; j += COOP_WARPS) {
+    const cplx<T>* x = X + (size_t)j * xstride;
+    T re = 0, im = 0;
+#pragma unroll 4
+    for (size_t i = sl.s0 + lane; i < sl.s1; i += 32) {
+      const cplx<T> p = x[i], q = y[i];
+      re += p.re * q.re + p.im * q.im;
+      im += p.re * q.im - p.im * q.re;
+    }
+    re = warp_allsum(re);
+    im = warp_allsum(im);
+    if (lane == 0) { sh.cta[2 * j] = re; sh.cta[2 * j + 1] = im; }
+  }
+}
+
+// Ns x Ns block times vector, loads issued up front: lane = output row, x broadcast by shuffles
 template <typename T, int NS>
-DW_D void coop_hop(CoopShared& sh, int nrow, int Ns, const int* list, const int* lnb, const T* M,
-                   const cplx<T>* src, const cplx<T>* base, cplx<T>* out, T out_sign) {
+struct RowLoad {
+  cplx<T> m[NS];
+  cplx<T> x;
+  DW_D void load(const cplx<T>* __restrict__ Mb, const cplx<T>* __restrict__ sv, int lane) {
+#pragma unroll
+    for (int c = 0; c < NS; ++c) m[c] = lane < NS ? Mb[c * NS + lane] : cplx<T>{T(0), T(0)};
+    x = lane < NS ? sv[lane] : cplx<T>{T(0), T(0)};
+  }
+  DW_D cplx<T> mv() const {
+    cplx<T> acc = {T(0), T(0)};
+#pragma unroll
+    for (int c = 0; c < NS; ++c) {
+      const cplx<T> xc = {__shfl_sync(0xffffffffu, x.re, c), __shfl_sync(0xffffffffu, x.im, c)};
+      acc += m[c] * xc;
+    }
+    return acc;
+  }
+};
+
+// out[r] = base[r] + out_sign * sum_d M[list[r]][d] src[lnb[r][d]] for this CTA's block rows.
+// Rows in chunks of COOP_CH; warp d computes direction d of every row of the chunk (FP32:
+// the next row's block is loaded while the current one is multiplied), the 8 partial sums
+// meet in shared memory (hp, COOP_CH x 8 x 32 complex).
+template <typename T, int NS>
+DW_D void coop_hop(int nrow, int Ns, const int* list, const int* lnb, const T* M, const cplx<T>* src,
+                   const cplx<T>* base, cplx<T>* out, T out_sign, cplx<T>* hp) {
   const int ns = NS ? NS : Ns;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const cplx<T>* Mc = reinterpret_cast<const cplx<T>*>(M);
-  for (int r = blockIdx.x; r < nrow; r += gridDim.x) {
-    const int L = list[r];
-    const int j = lnb[r * 8 + w];
-    cplx<T> acc = warp_mv<T, NS>(Mc + ((size_t)L * 8 + w) * ns * ns, src + (size_t)j * ns, ns, lane,
-                                 cplx<T>{T(0), T(0)});
-    sh.hop[w][2 * lane] = (double)acc.re;
-    sh.hop[w][2 * lane + 1] = (double)acc.im;
+  const int R = (nrow + gridDim.x - 1) / gridDim.x;
+  const int rb = min(nrow, (int)blockIdx.x * R), re = min(nrow, rb + R);
+  constexpr bool PIPE = sizeof(T) == 4 && NS > 0 && NS <= 24;
+  for (int r0 = rb; r0 < re; r0 += COOP_CH) {
+    const int nr = min(COOP_CH, re - r0);
+    int myL = 0, myj = 0;
+    if (lane < nr) { myL = list[r0 + lane]; myj = lnb[(r0 + lane) * 8 + w]; }
+    if constexpr (PIPE) {
+      RowLoad<T, (PIPE ? NS : 1)> buf[2];
+      buf[0].load(Mc + ((size_t)__shfl_sync(0xffffffffu, myL, 0) * 8 + w) * NS * NS,
+                  src + (size_t)__shfl_sync(0xffffffffu, myj, 0) * NS, lane);
+      for (int q = 0; q < nr; q += 2) {
+        if (q + 1 < nr)
+          buf[1].load(Mc + ((size_t)__shfl_sync(0xffffffffu, myL, q + 1) * 8 + w) * NS * NS,
+                      src + (size_t)__shfl_sync(0xffffffffu, myj, q + 1) * NS, lane);
+        hp[(q * 8 + w) * 32 + lane] = buf[0].mv();
+        if (q + 1 < nr) {
+          if (q + 2 < nr)
+            buf[0].load(Mc + ((size_t)__shfl_sync(0xffffffffu, myL, q + 2) * 8 + w) * NS * NS,
+                        src + (size_t)__shfl_sync(0xffffffffu, myj, q + 2) * NS, lane);
+          hp[((q + 1) * 8 + w) * 32 + lane] = buf[1].mv();
+        }
+      }
+    } else {
+      for (int q = 0; q < nr; ++q) {
+        const int L = __shfl_sync(0xffffffffu, myL, q), j = __shfl_sync(0xffffffffu, myj, q);
+        hp[(q * 8 + w) * 32 + lane] = warp_mv<T, NS>(Mc + ((size_t)L * 8 + w) * ns * ns, src + (size_t)j * ns, ns,
+                                                     lane, cplx<T>{T(0), T(0)});
+      }
+    }
     __syncthreads();
-    if (w == 0 && lane < ns) {
-      double re = 0, im = 0;
+    for (int t = threadIdx.x; t < nr * ns; t += COOP_THREADS) {
+      const int q = t / ns, k = t - q * ns;
+      cplx<T> sum = hp[(q * 8) * 32 + k];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) { re += sh.hop[q][2 * lane]; im += sh.hop[q][2 * lane + 1]; }
-      cplx<T> bse = base ? base[(size_t)r * ns + lane] : cplx<T>{T(0), T(0)};
-      out[(size_t)r * ns + lane] = bse + out_sign * cplx<T>{(T)re, (T)im};
+      for (int d = 1; d < 8; ++d) sum += hp[(q * 8 + d) * 32 + k];
+      const size_t o = (size_t)(r0 + q) * ns + k;
+      const cplx<T> bse = base ? base[o] : cplx<T>{T(0), T(0)};
+      out[o] = bse + out_sign * sum;
     }
     __syncthreads();
   }
@@ -708,46 +909,31 @@ DW_D void coop_hop(CoopShared& sh, int nrow, int Ns, const int* list, const int*
 
 // y = B^ x = x - M_eo (M_oe x); ends with a grid barrier
 template <typename T, int NS>
-DW_D void coop_bhat(cg::grid_group& grid, CoopShared& sh, const CoopArgs<T>& a, const cplx<T>* x, cplx<T>* tmpo,
-                    cplx<T>* y) {
-  coop_hop<T, NS>(sh, a.No, a.Ns, a.list_o, a.lnb_o, a.M, x, nullptr, tmpo, T(1));    // tmpo = M_oe x
+DW_D void coop_bhat(cg::grid_group& grid, const CoopArgs<T>& a, const cplx<T>* x, cplx<T>* tmpo, cplx<T>* y,
+                    cplx<T>* hp) {
+  coop_hop<T, NS>(a.No, a.Ns, a.list_o, a.lnb_o, a.M, x, nullptr, tmpo, T(1), hp);    // tmpo = M_oe x
   grid.sync();
-  coop_hop<T, NS>(sh, a.Ne, a.Ns, a.list_e, a.lnb_e, a.M, tmpo, x, y, T(-1));        // y = x - M_eo tmpo
+  coop_hop<T, NS>(a.Ne, a.Ns, a.list_e, a.lnb_e, a.M, tmpo, x, y, T(-1), hp);         // y = x - M_eo tmpo
   grid.sync();
 }
 
 // u -= Bg A~^{-1} g^+ u  (P~_L, in place); with add_to set, only z = A~^{-1} g^+ u is formed and
-// add_to += g z is applied instead.  Elementwise parts by the owning thread, no trailing barrier.
+// add_to += g z is applied instead.  Elementwise parts on the CTA slice, no trailing barrier.
 template <typename T, int NS>
-DW_D void coop_PL(cg::grid_group& grid, CoopShared& sh, const CoopArgs<T>& a, cplx<T>* u, const cplx<T>* gsrc,
-                  const cplx<T>* bgsrc, cplx<T>* add_to, double* stage) {
+DW_D void coop_PL(cg::grid_group& grid, CoopShared<T>& sh, const CoopArgs<T>& a, cplx<T>* u, const cplx<T>* gsrc,
+                  const cplx<T>* bgsrc, cplx<T>* add_to, T* stage, const CoopSlice& sl) {
   constexpr int NSM = NS ? NS : 32;
   const size_t n = (size_t)a.Ne * a.Ns;
-  const size_t tid = blockIdx.x * (size_t)COOP_THREADS + threadIdx.x, nth = (size_t)gridDim.x * COOP_THREADS;
   const int Ns = NS ? NS : a.Ns;
-  double acc[2 * NSM];
-#pragma unroll
-  for (int j = 0; j < 2 * NSM; ++j) acc[j] = 0;
-  for (size_t i = tid; i < n; i += nth) {
-    const cplx<T> x = u[i];
-#pragma unroll
-    for (int l = 0; l < NSM; ++l) {
-      if (l < Ns) {
-        const cplx<T> gl = gsrc[(size_t)l * n + i];
-        acc[2 * l] += (double)gl.re * x.re + (double)gl.im * x.im;
-        acc[2 * l + 1] += (double)gl.re * x.im - (double)gl.im * x.re;
-      }
-    }
-  }
-  coop_reduce<2 * NSM>(grid, sh, acc, 2 * Ns, a.partial, stage);
+  cta_dots<T>(sh, gsrc, n, Ns, u, sl);
+  coop_reduce(grid, sh, 2 * Ns, a.partial, stage);
   if (threadIdx.x < Ns) {          // z = A~^{-1} y
-    const cplx<T>* Ai = reinterpret_cast<const cplx<T>*>(a.Ainv);
-    double zr = 0, zi = 0;
+    T zr = 0, zi = 0;
     for (int q = 0; q < Ns; ++q) {
-      cplx<T> m = Ai[threadIdx.x * Ns + q];
-      double yr = sh.res[2 * q], yi = sh.res[2 * q + 1];
-      zr += (double)m.re * yr - (double)m.im * yi;
-      zi += (double)m.re * yi + (double)m.im * yr;
+      const T mr = sh.ainv[2 * (threadIdx.x * Ns + q)], mi = sh.ainv[2 * (threadIdx.x * Ns + q) + 1];
+      const T yr = sh.res[2 * q], yi = sh.res[2 * q + 1];
+      zr += mr * yr - mi * yi;
+      zi += mr * yi + mi * yr;
     }
     sh.z[2 * threadIdx.x] = zr;
     sh.z[2 * threadIdx.x + 1] = zi;
@@ -756,12 +942,12 @@ DW_D void coop_PL(cg::grid_group& grid, CoopShared& sh, const CoopArgs<T>& a, cp
   cplx<T>* tgt = add_to ? add_to : u;
   const cplx<T>* vecs = add_to ? gsrc : bgsrc;
   const T sg = add_to ? T(1) : T(-1);
-  for (size_t i = tid; i < n; i += nth) {
+  for (size_t i = sl.s0 + threadIdx.x; i < sl.s1; i += COOP_THREADS) {
     cplx<T> x = tgt[i];
 #pragma unroll
     for (int l = 0; l < NSM; ++l) {
       if (l < Ns) {
-        const cplx<T> zl = {(T)sh.z[2 * l], (T)sh.z[2 * l + 1]};
+        const cplx<T> zl = {sh.z[2 * l], sh.z[2 * l + 1]};
         x += sg * (zl * vecs[(size_t)l * n + i]);
       }
     }
@@ -772,13 +958,22 @@ DW_D void coop_PL(cg::grid_group& grid, CoopShared& sh, const CoopArgs<T>& a, cp
 template <typename T, int NS>
 __global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_kernel(CoopArgs<T> a) {
   cg::grid_group grid = cg::this_grid();
-  __shared__ CoopShared sh;
-  extern __shared__ double stage[];     // [COOP_NV][gridDim]
-  if (threadIdx.x == 0) sh.phase = 0;
-  __syncthreads();
+  __shared__ CoopShared<T> sh;
+  extern __shared__ __align__(16) unsigned char coop_dyn[];
+  T* stage = reinterpret_cast<T*>(coop_dyn);                                   // [COOP_NV][gridDim]
+  cplx<T>* hp = reinterpret_cast<cplx<T>*>(stage + (size_t)COOP_NV * gridDim.x);  // [COOP_CH][8][32]
   const size_t n = (size_t)a.Ne * a.Ns;
-  const size_t tid = blockIdx.x * (size_t)COOP_THREADS + threadIdx.x, nth = (size_t)gridDim.x * COOP_THREADS;
+  const CoopSlice sl = coop_slice(n);
   const int nkv = a.nkv;
+  if (threadIdx.x == 0) sh.phase = 0;
+  if (a.a3) {
+    const cplx<T>* Ai = reinterpret_cast<const cplx<T>*>(a.Ainv);
+    for (int t = threadIdx.x; t < a.Ns * a.Ns; t += COOP_THREADS) {
+      sh.ainv[2 * t] = Ai[t].re;
+      sh.ainv[2 * t + 1] = Ai[t].im;
+    }
+  }
+  __syncthreads();
   cplx<T>* W = reinterpret_cast<cplx<T>*>(a.work);
   cplx<T>* rho = W + (size_t)2 * nkv * n;
   cplx<T>* tmpo = rho + n;
@@ -790,130 +985,128 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_kernel(CoopAr
   cplx<T>* v = reinterpret_cast<cplx<T>*>(a.v);
   auto chi = [&](int k) { return W + (size_t)k * n; };
   auto xi = [&](int k) { return W + (size_t)(nkv + k) * n; };
+  auto slice = [&](auto&& f) {
+    for (size_t i = sl.s0 + threadIdx.x; i < sl.s1; i += COOP_THREADS) f(i);
+  };
+  const int lane = threadIdx.x & 31;
 
   // rhsd = P~_L b, rho = rhsd, v = 0
-  for (size_t i = tid; i < n; i += nth) rhsd[i] = b[i];
-  if (a.a3) coop_PL<T, NS>(grid, sh, a, rhsd, g, Bg, nullptr, stage);
-  double s1[1] = {0};
-  for (size_t i = tid; i < n; i += nth) {
-    cplx<T> x = rhsd[i];
+  slice([&](size_t i) { rhsd[i] = b[i]; });
+  if (a.a3) coop_PL<T, NS>(grid, sh, a, rhsd, g, Bg, nullptr, stage, sl);
+  T s1[1] = {0};
+  slice([&](size_t i) {
+    const cplx<T> x = rhsd[i];
     rho[i] = x;
     v[i] = {T(0), T(0)};
-    s1[0] += (double)x.re * x.re + (double)x.im * x.im;
-  }
-  coop_reduce<1>(grid, sh, s1, 1, a.partial, stage);
-  const double bn = sqrt(sh.res[0]);
-  double rn = bn;
+    s1[0] += x.re * x.re + x.im * x.im;
+  });
+  cta_sum<T, 1>(sh, s1);
+  coop_reduce(grid, sh, 1, a.partial, stage);
+  const T bn = sqrt(sh.res[0]);
+  T rn = bn;
   int total = 0;
-  while (bn > 0 && rn > a.tol * bn && total < a.maxit) {
+  while (bn > 0 && (double)rn > a.tol * (double)bn && total < a.maxit) {
     int k = 0;
     for (; k < nkv && total < a.maxit; ++k) {
       cplx<T>* ck = chi(k);
       cplx<T>* xk = xi(k);
-      for (size_t i = tid; i < n; i += nth) xk[i] = rho[i];
-      grid.sync();
-      coop_bhat<T, NS>(grid, sh, a, xk, tmpo, ck);
-      if (a.a3) coop_PL<T, NS>(grid, sh, a, ck, g, Bg, nullptr, stage);
+      // xi_k = rho;  chi_k = P~_L B^ rho  (rho is stable until the update below)
+      slice([&](size_t i) { xk[i] = rho[i]; });
+      coop_bhat<T, NS>(grid, a, rho, tmpo, ck, hp);
+      if (a.a3) coop_PL<T, NS>(grid, sh, a, ck, g, Bg, nullptr, stage, sl);
       if (k > 0) {
-        double sb[2 * COOP_NKV];
-#pragma unroll
-        for (int j = 0; j < 2 * COOP_NKV; ++j) sb[j] = 0;
-        for (size_t i = tid; i < n; i += nth) {
-          const cplx<T> y = ck[i];
-#pragma unroll
-          for (int j = 0; j < COOP_NKV; ++j) {
-            if (j < k) {
-              const cplx<T> x = chi(j)[i];
-              sb[2 * j] += (double)x.re * y.re + (double)x.im * y.im;
-              sb[2 * j + 1] += (double)x.re * y.im - (double)x.im * y.re;
-            }
-          }
-        }
-        coop_reduce<2 * COOP_NKV>(grid, sh, sb, 2 * k, a.partial, stage);
+        cta_dots<T>(sh, W, n, k, ck, sl);
+        coop_reduce(grid, sh, 2 * k, a.partial, stage);
         if (threadIdx.x < 2 * k) sh.bb[threadIdx.x >> 1][2 * k + (threadIdx.x & 1)] = sh.res[threadIdx.x];
         __syncthreads();
-        for (size_t i = tid; i < n; i += nth) {
+        slice([&](size_t i) {
           cplx<T> y = ck[i];
 #pragma unroll
           for (int j = 0; j < COOP_NKV; ++j) {
             if (j < k) {
-              const cplx<T> bj = {(T)sh.bb[j][2 * k], (T)sh.bb[j][2 * k + 1]};
+              const cplx<T> bj = {sh.bb[j][2 * k], sh.bb[j][2 * k + 1]};
               y -= bj * chi(j)[i];
             }
           }
           ck[i] = y;
-        }
+        });
       }
-      double s3[3] = {0, 0, 0};
-      for (size_t i = tid; i < n; i += nth) {
+      T s3[3] = {0, 0, 0};
+      slice([&](size_t i) {
         const cplx<T> x = ck[i], y = rho[i];
-        s3[0] += (double)x.re * y.re + (double)x.im * y.im;
-        s3[1] += (double)x.re * y.im - (double)x.im * y.re;
-        s3[2] += (double)x.re * x.re + (double)x.im * x.im;
-      }
-      coop_reduce<3>(grid, sh, s3, 3, a.partial, stage);
-      const double cn = sqrt(sh.res[2]);
+        s3[0] += x.re * y.re + x.im * y.im;
+        s3[1] += x.re * y.im - x.im * y.re;
+        s3[2] += x.re * x.re + x.im * x.im;
+      });
+      cta_sum<T, 3>(sh, s3);
+      coop_reduce(grid, sh, 3, a.partial, stage);
+      const T cn = sqrt(sh.res[2]);
       if (!(cn > 0)) break;
-      const double ar = sh.res[0] / cn, ai = sh.res[1] / cn;
+      const T inv = T(1) / cn;
+      const T ar = sh.res[0] * inv, ai = sh.res[1] * inv;
       if (threadIdx.x == 0) { sh.c[k] = cn; sh.a[2 * k] = ar; sh.a[2 * k + 1] = ai; }
       s1[0] = 0;
-      const T inv = (T)(1.0 / cn);
-      const cplx<T> ak = {(T)ar, (T)ai};
-      for (size_t i = tid; i < n; i += nth) {
+      const cplx<T> ak = {ar, ai};
+      slice([&](size_t i) {
         const cplx<T> x = inv * ck[i];
         ck[i] = x;
         const cplx<T> y = rho[i] - ak * x;
         rho[i] = y;
-        s1[0] += (double)y.re * y.re + (double)y.im * y.im;
-      }
-      coop_reduce<1>(grid, sh, s1, 1, a.partial, stage);
+        s1[0] += y.re * y.re + y.im * y.im;
+      });
+      cta_sum<T, 1>(sh, s1);
+      coop_reduce(grid, sh, 1, a.partial, stage);
       rn = sqrt(sh.res[0]);
       ++total;
-      if (rn <= a.tol * bn) { ++k; break; }
+      if ((double)rn <= a.tol * (double)bn) { ++k; break; }
     }
-    // back substitution (thread 0 of every CTA), v += sum beta_k xi_k
-    if (threadIdx.x == 0) {
+    // back substitution by warp 0 (lane i holds row i), then v += sum beta_k xi_k
+    if (threadIdx.x < 32) {
+      T br = lane < k ? sh.a[2 * lane] : T(0), bi = lane < k ? sh.a[2 * lane + 1] : T(0);
       for (int j = k - 1; j >= 0; --j) {
-        double sr = sh.a[2 * j], si = sh.a[2 * j + 1];
-        for (int i = j + 1; i < k; ++i) {
-          double br = sh.bb[j][2 * i], bi = sh.bb[j][2 * i + 1];
-          sr -= br * sh.beta[2 * i] - bi * sh.beta[2 * i + 1];
-          si -= br * sh.beta[2 * i + 1] + bi * sh.beta[2 * i];
+        const T cj = sh.c[j];
+        const T yr = __shfl_sync(0xffffffffu, br, j) / cj, yi = __shfl_sync(0xffffffffu, bi, j) / cj;
+        if (lane == j) { sh.beta[2 * j] = yr; sh.beta[2 * j + 1] = yi; }
+        if (lane < j) {     // row lane -= bb[lane][j] beta_j
+          const T mr = sh.bb[lane][2 * j], mi = sh.bb[lane][2 * j + 1];
+          br -= mr * yr - mi * yi;
+          bi -= mr * yi + mi * yr;
         }
-        sh.beta[2 * j] = sr / sh.c[j];
-        sh.beta[2 * j + 1] = si / sh.c[j];
       }
     }
     __syncthreads();
-    for (size_t i = tid; i < n; i += nth) {
+    slice([&](size_t i) {
       cplx<T> x = v[i];
-      for (int j = 0; j < k; ++j) x += cplx<T>{(T)sh.beta[2 * j], (T)sh.beta[2 * j + 1]} * xi(j)[i];
+#pragma unroll
+      for (int j = 0; j < COOP_NKV; ++j)
+        if (j < k) x += cplx<T>{sh.beta[2 * j], sh.beta[2 * j + 1]} * xi(j)[i];
       v[i] = x;
-    }
+    });
     grid.sync();
     if (k == 0) break;
     // true residual of the deflated system
-    coop_bhat<T, NS>(grid, sh, a, v, tmpo, t);
-    if (a.a3) coop_PL<T, NS>(grid, sh, a, t, g, Bg, nullptr, stage);
+    coop_bhat<T, NS>(grid, a, v, tmpo, t, hp);
+    if (a.a3) coop_PL<T, NS>(grid, sh, a, t, g, Bg, nullptr, stage, sl);
     s1[0] = 0;
-    for (size_t i = tid; i < n; i += nth) {
+    slice([&](size_t i) {
       const cplx<T> y = rhsd[i] - t[i];
       rho[i] = y;
-      s1[0] += (double)y.re * y.re + (double)y.im * y.im;
-    }
-    coop_reduce<1>(grid, sh, s1, 1, a.partial, stage);
+      s1[0] += y.re * y.re + y.im * y.im;
+    });
+    cta_sum<T, 1>(sh, s1);
+    coop_reduce(grid, sh, 1, a.partial, stage);
     rn = sqrt(sh.res[0]);
   }
   if (a.a3) {
     // v = chi + g A~^{-1} g^+ (b - B^ chi)
     grid.sync();
-    coop_bhat<T, NS>(grid, sh, a, v, tmpo, t);
-    for (size_t i = tid; i < n; i += nth) t[i] = b[i] - t[i];
-    coop_PL<T, NS>(grid, sh, a, t, g, g, v, stage);     // v += g z,  z = A~^{-1} g^+ t
+    coop_bhat<T, NS>(grid, a, v, tmpo, t, hp);
+    slice([&](size_t i) { t[i] = b[i] - t[i]; });
+    coop_PL<T, NS>(grid, sh, a, t, g, g, v, stage, sl);     // v += g z,  z = A~^{-1} g^+ t
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.out[0] = total;
-    a.out[1] = bn > 0 ? rn / bn : 0.0;
+    a.out[1] = bn > 0 ? (double)rn / (double)bn : 0.0;
   }
 }
 
@@ -967,8 +1160,24 @@ extern "C" void dfl_destroy(dfl_ctx* d) {
   delete d;
 }
 
+template <typename T, int NS>
+static bool launch_restrict_ns(dfl_ctx* d, const T* psi, T* c, int nrhs, cudaStream_t s) {
+  if constexpr (NS == 0 || sizeof(T) != 4) {
+    return false;
+  } else {
+    restrict_ns_kernel<T, NS><<<d->Nb, 128, 0, s>>>(d->c->g, d->d_sub, d->nsub, d->basis16 ? nullptr : d->basis64,
+                                                    d->basis16, psi, c, nrhs, (size_t)d->c->V * 24,
+                                                    (size_t)d->N * 2);
+    return true;
+  }
+}
 template <typename T>
 static int restrict_t(dfl_ctx* d, const T* psi, T* c, cudaStream_t s, int nrhs = 1) {
+  if (sizeof(T) == 4) {
+    bool done = false;
+    NS_DISPATCH(d->Ns, (done = launch_restrict_ns<T, NSV>(d, psi, c, nrhs, s)));
+    if (done) { dw_note_launch(); return DW_OK; }
+  }
   restrict_kernel<T><<<d->Nb, 128, 0, s>>>(d->c->g, d->d_sub, d->nsub, d->Ns, d->basis16 ? nullptr : d->basis64,
                                             d->basis16, psi, c, nrhs, (size_t)d->c->V * 24,
                                             (size_t)d->N * 2); dw_note_launch();
@@ -1189,12 +1398,12 @@ static int little_gcr_coop(dfl_ctx* d, const T* b, T* v, double tol, int maxit, 
   a.M = Mp<T>(d); a.g = d->a3 ? gp<T>(d) : nullptr; a.Bg = d->a3 ? Bgp<T>(d) : nullptr;
   a.Ainv = d->a3 ? Ainvp<T>(d) : nullptr; a.b = b; a.v = v;
   a.work = lwork<T>(d, 0);
-  a.partial = d->coop_partial;
+  a.partial = reinterpret_cast<T*>(d->coop_partial);
   a.out = d->coop_out + (d->defer_slot >= 0 ? 2 * d->defer_slot : 0);
   a.tol = tol;
   void* args[] = {&a};
   cudaError_t le = cudaSuccess;
-  const size_t dsm = (size_t)COOP_NV * d->coop_grid * sizeof(double);
+  const size_t dsm = coop_dyn_smem<T>(d->coop_grid);
   NS_DISPATCH(d->Ns, (le = cudaLaunchCooperativeKernel((void*)little_gcr_coop_kernel<T, NSV>, d->coop_grid,
                                                        COOP_THREADS, args, dsm, s)));
   DW_CUDA(le);
@@ -1715,7 +1924,7 @@ static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_c
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-    const size_t dsm = (size_t)COOP_NV * sms * sizeof(double);
+    const size_t dsm = coop_dyn_smem<double>(sms);
     NS_DISPATCH(Ns, (cudaFuncSetAttribute(little_gcr_coop_kernel<float, NSV>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm)));
     NS_DISPATCH(Ns, (cudaFuncSetAttribute(little_gcr_coop_kernel<double, NSV>,

@@ -176,41 +176,34 @@ int solve_one(dw_ctx* c, dfl_ctx* d, const sol_params* p, const double* eta_cano
   double relres = 1.0;
   const int max_restarts = 10000;
   for (int restart = 0; restart < max_restarts; ++restart) {
-    if ((rc = residual64())) return rc;
-    double rn = sqrt(h[2]);
+    double rn;
+    if (restart == 0) {     // psi = 0: the residual is eta
+      DW_CUDA(cudaMemcpyAsync(W.r64, W.eta, fb64, cudaMemcpyDeviceToDevice, s));
+      rn = en;
+    } else {
+      if ((rc = residual64())) return rc;
+      rn = sqrt(h[2]);
+    }
     if (d) {
+      // deflation correction psi += Phi A^{-1} Phi^+ r in FP64 precision (A.5: high precision
+      // outside the cycles; the error of the correction is amplified by the small eigenvalues
+      // of A).  Mixed: FP32 little GCR with FP64 little residuals; else FP64 little GCR.
       int it = 0;
       double rr = 0;
-      if (p->mixed) {
-        // deflation correction accurate to the outer tolerance, all little iterations in FP32
-        // (A.5 asks for high precision outside the cycles): FP32 GCR + FP64 little residuals
-        tm.begin(PH_PROJECT);
-        restrict_(d, W.r64, W.c64, s);
-        tm.end();
-        tm.begin(PH_LITTLE);
-        rc = little_solve_refined(d, W.c64, W.v64, p->little_tol_out, p->little_maxit, p->little_nkv, &it, &rr, s);
-        tm.end();
-        if (rc < 0) return rc;
-        tm.begin(PH_PROJECT);
-        prolong_(d, W.v64, W.psi, 1, s);
-        tm.end();
-        if ((rc = residual64())) return rc;
-        rn = sqrt(h[2]);
-      } else {
-        // deflation correction with the FP64 little solve (A.5: high precision outside the cycles)
-        tm.begin(PH_PROJECT);
-        restrict_(d, W.r64, W.c64, s);
-        tm.end();
-        tm.begin(PH_LITTLE);
-        rc = lsolve_(d, W.c64, W.v64, p->little_tol_out, p->little_maxit, p->little_nkv, &it, &rr, s);
-        tm.end();
-        if (rc < 0) return rc;
-        tm.begin(PH_PROJECT);
-        prolong_(d, W.v64, W.psi, 1, s);
-        tm.end();
-        if ((rc = residual64())) return rc;
-        rn = sqrt(h[2]);
-      }
+      tm.begin(PH_PROJECT);
+      restrict_(d, W.r64, W.c64, s);
+      tm.end();
+      tm.begin(PH_LITTLE);
+      rc = p->mixed ? little_solve_refined(d, W.c64, W.v64, p->little_tol_out, p->little_maxit, p->little_nkv, &it,
+                                           &rr, s)
+                    : lsolve_(d, W.c64, W.v64, p->little_tol_out, p->little_maxit, p->little_nkv, &it, &rr, s);
+      tm.end();
+      if (rc < 0) return rc;
+      tm.begin(PH_PROJECT);
+      prolong_(d, W.v64, W.psi, 1, s);
+      tm.end();
+      if ((rc = residual64())) return rc;
+      rn = sqrt(h[2]);
       inf.little_iterations += it;
       inf.little_solves += 1;
     }
@@ -370,7 +363,12 @@ int solve_batch_f32(dw_ctx* c, dfl_ctx* d, const sol_params* p, int nrhs, const 
   const int max_restarts = 10000;
   int total_steps = 0;
   for (int restart = 0; restart < max_restarts; ++restart) {
-    if ((rc = residual64())) return rc;
+    if (restart == 0) {     // psi = 0: the residuals are the sources
+      DW_CUDA(cudaMemcpyAsync(W.r64, W.eta, fb64, cudaMemcpyDeviceToDevice, s));
+      rn = en;
+    } else if ((rc = residual64())) {
+      return rc;
+    }
     if (d) {
       // deflation correction accurate to the outer tolerance (FP32 little iterations, FP64 residuals)
       tm.begin(PH_PROJECT);
@@ -405,7 +403,8 @@ int solve_batch_f32(dw_ctx* c, dfl_ctx* d, const sol_params* p, int nrhs, const 
       }
       all &= conv[r] != 0;
     }
-    if (all || total_steps >= p->nmx) break;
+    if (all) break;
+    if (total_steps >= p->nmx) break;
     // ---- one GCR cycle for the batch
     for (int r = 0; r < nrhs; ++r) {
       live[r] = !conv[r];
