@@ -99,6 +99,20 @@ int dw_unpack(dw_ctx* ctx, int prec, int nrhs, const void* packed_dev, double* c
  * in/out: nrhs packed fields of precision prec; in != out. */
 int dw_apply(dw_ctx* ctx, int prec, int op, int nrhs, const void* in_dev, void* out_dev, void* stream);
 
+/* The Schur complement of dw_apply(DW_OP_SCHUR) for one field, allocating no memory.  The
+ * paper has no counterpart: this is an interface for callers that must not allocate device
+ * memory at the time of the call (cudaMalloc synchronises the device, stalling other
+ * streams, and can fail under a fixed memory reservation), whereas dw_apply allocates its
+ * intermediate field on first use.  The intermediate A_oo^{-1} D_oe in lives in a fixed
+ * 16 MiB device array of the library: volumes whose packed field of precision prec exceeds
+ * 16 MiB (FP64: more than 87381 sites; FP32: more than 174762) get DW_EINVAL with a message.
+ * The first call on each device looks up the array's address (set-up, once per device; make
+ * it before any stream capture).  The array is shared by all calls on a device: calls that
+ * overlap in time (other streams, other host threads) race on it and must be ordered by the
+ * caller.  in/out: one packed field of precision prec (device), in != out; odd sites of out
+ * are set to zero.  Results equal those of dw_apply(DW_OP_SCHUR). */
+int dw_apply_schur_static(dw_ctx* ctx, int prec, const void* in_dev, void* out_dev, void* stream);
+
 /* xi = M_sap rho: Schwarz alternating procedure (Section 6.1) on the
  * sap_bs blocks, ncy cycles of (black blocks, white blocks), each block
  * solve = nmr minimal-residual steps on the even-odd preconditioned block

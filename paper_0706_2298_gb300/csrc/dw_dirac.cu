@@ -9,6 +9,9 @@
 // neighbour re-reads served by L2 (block-major order keeps them close).
 #include "dw_common.cuh"
 
+#include <cstdio>
+#include <mutex>
+
 template <typename T>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) dirac_full_kernel(Geom g, const T* __restrict__ links,
                                                          const T* __restrict__ clov, const T* __restrict__ in,
@@ -197,6 +200,81 @@ extern "C" int dw_apply(dw_ctx* c, int prec, int op, int nrhs, const void* in, v
     }
     if (rc) return rc;
   }
+  DW_CUDA(cudaGetLastError());
+  return DW_OK;
+}
+
+// ------------------------------------------------------------------ allocation-free Schur operator
+// The even-odd Schur complement of dw_apply(DW_OP_SCHUR) with its odd-site intermediate
+// A_oo^{-1} D_oe held in a fixed device array of this file instead of memory that the
+// library allocates on first use.  For callers that must not allocate device memory at
+// the time of the call: cudaMalloc synchronises the device (stalling work queued on other
+// streams) and can fail in processes that run with a fixed memory reservation.
+//
+// The array holds one packed field, so the entry point serves volumes whose packed field
+// fits in kSchurStaticBytes; larger ones are rejected with DW_EINVAL.  Every entry of the
+// intermediate that is read is written earlier in the same call, so nothing has to start
+// at zero.  All calls on one device share the array: calls that overlap in time (issued on
+// different streams, or from several host threads without ordering) race on it.
+namespace {
+constexpr size_t kSchurStaticBytes = size_t(16) << 20;   // 16 MiB: FP64 up to 87381 sites, FP32 up to 174762
+constexpr int kMaxDevices = 64;
+std::mutex g_schur_static_mu;
+void* g_schur_static_ptr[kMaxDevices] = {};
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_schur_static[kSchurStaticBytes];
+
+// Address of the array on the current device, looked up once per device (the first call on a
+// device does this set-up; make it before any stream capture).
+static int schur_static_scratch(void** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return dw_cuda_fail(e, "dw_apply_schur_static: cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) {
+    dw_set_error("dw_apply_schur_static: device ordinal beyond the supported range");
+    return DW_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(g_schur_static_mu);
+  if (!g_schur_static_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_schur_static);
+    if (e != cudaSuccess) return dw_cuda_fail(e, "dw_apply_schur_static: cudaGetSymbolAddress");
+    g_schur_static_ptr[dev] = p;
+  }
+  *out = g_schur_static_ptr[dev];
+  return DW_OK;
+}
+
+template <typename T>
+static void schur_static_launch(dw_ctx* c, const T* in, T* out, T* t, cudaStream_t st) {
+  constexpr int P = prec_of<T>();
+  unsigned blocks = (unsigned)((c->V / 2 + 127) / 128);
+  schur_odd_kernel<T><<<blocks, 128, 0, st>>>(c->g, (const T*)c->links[P], (const T*)c->clovinv[P], in, t); dw_note_launch();
+  schur_even_kernel<T><<<blocks, 128, 0, st>>>(c->g, (const T*)c->links[P], (const T*)c->clov[P], in, t, out); dw_note_launch();
+}
+
+extern "C" int dw_apply_schur_static(dw_ctx* c, int prec, const void* in, void* out, void* stream) {
+  if (!c || !in || !out || in == out || (prec != DW_F64 && prec != DW_F32)) {
+    dw_set_error("dw_apply_schur_static: bad argument");
+    return DW_EINVAL;
+  }
+  const size_t need = dw_field_bytes(c, prec);
+  if (need > kSchurStaticBytes) {
+    char msg[256];
+    snprintf(msg, sizeof msg,
+             "dw_apply_schur_static: the intermediate field needs %zu bytes, more than the fixed %zu-byte "
+             "device array (use dw_apply with DW_OP_SCHUR for this volume and precision)",
+             need, kSchurStaticBytes);
+    dw_set_error(msg);
+    return DW_EINVAL;
+  }
+  void* t = nullptr;
+  int rc = schur_static_scratch(&t);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == DW_F64) schur_static_launch(c, (const double*)in, (double*)out, (double*)t, st);
+  else schur_static_launch(c, (const float*)in, (float*)out, (float*)t, st);
   DW_CUDA(cudaGetLastError());
   return DW_OK;
 }

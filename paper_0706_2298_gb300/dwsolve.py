@@ -73,6 +73,7 @@ _SIGNATURES = {
     "dw_pack": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
     "dw_unpack": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
     "dw_apply": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P]),
+    "dw_apply_schur_static": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "sap_precondition": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, _P]),
     "deflation_build": (C.c_int, [_P, C.POINTER(DflParams), _P, C.POINTER(_P), C.POINTER(DflInfo)]),
     "dfl_destroy": (None, [_P]),
@@ -214,6 +215,11 @@ def dw_unpack(ctx: Ctx, prec, nrhs, packed_dev, canon_dev, stream=None):
 
 def dw_apply(ctx: Ctx, prec, op, nrhs, in_dev, out_dev, stream=None):
     _check(lib().dw_apply(ctx.handle, prec, op, nrhs, _ptr(in_dev), _ptr(out_dev), _stream(stream)))
+
+
+def dw_apply_schur_static(ctx: Ctx, prec, in_dev, out_dev, stream=None):
+    """Schur complement of one packed field without any allocation (fixed 16 MiB device array)."""
+    _check(lib().dw_apply_schur_static(ctx.handle, prec, _ptr(in_dev), _ptr(out_dev), _stream(stream)))
 
 
 def sap_precondition(ctx: Ctx, prec, ncy, nmr, nrhs, rho_dev, xi_dev, stream=None):
