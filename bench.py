@@ -40,6 +40,11 @@ WORKLOADS = {
 MASS_FILE = os.path.join(ROOT, "paper_0706_2298_gb300", "workload_masses.json")
 
 
+# DRAM bytes per little-GCR iteration of the cooperative kernel, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch / its iterations); None until taken
+LITTLE_TRAFFIC = {}
+
+
 def load_masses():
     if os.path.exists(MASS_FILE):
         with open(MASS_FILE) as f:
@@ -249,16 +254,31 @@ def main():
     value = (t_ms / 1e3) / (args.steps * world)
     iters = statistics.median([i.iterations for i in infos])
 
-    # ---- roofline of the dominant kernel (Schwarz block kernel): algorithmic bytes per launch / event time
+    # ---- rooflines from the library's CUDA-event phase timers over the timed solves
     hbm, peak_kind = peaks()
+    # dominant kernel: the cooperative little GCR (A.2-A.4).  Algorithmic bytes per little-GCR
+    # iteration (FP32): the eight off-diagonal Ns x Ns blocks of every block row of the little
+    # operator (both parities, read once by the two hops) and the 2 Ns global-mode vectors g, B^g
+    # of the A.3 projection (Ne Ns complex each).  The operator (66 MB) is L2-resident.
+    Nb, Ns = dfl.Nb, dfl.Ns
+    lit_bytes = Nb * 8 * Ns * Ns * 8 + 2 * Ns * (Nb // 2) * Ns * 8
+    t_little = sum(i.t_little for i in infos)
+    n_lit = sum(i.little_iterations for i in infos)
+    lit_s = t_little / max(n_lit, 1)
+    roof = {"kernel": f"little_gcr_coop_kernel<float,{Ns}>", "bound": "hbm", "achieved": lit_bytes / lit_s / 1e9,
+            "peak": hbm, "unit": "GB/s", "frac": lit_bytes / lit_s / 1e9 / hbm, "traffic": LITTLE_TRAFFIC.get(
+                (args.workload, Ns)), "peak_kind": peak_kind, "per": "little GCR iteration",
+            "us_per_iteration": lit_s * 1e6, "algorithmic_bytes": lit_bytes, "l2_resident": True,
+            "iterations_per_solve": n_lit / max(len(infos), 1)}
+    # the Schwarz block kernel (second largest): 960 algorithmic bytes per site processed
     t_sap = sum(i.t_sap for i in infos)
     n_sap_launch = sum(i.iterations for i in infos) * 2 * wl["ncy"]
     sap_launch_s = t_sap / max(n_sap_launch, 1)
     # per site processed (FP32): links 4 x 12 reals, clover (A or A^-1) 72 reals, r in/out, delta out, xi in/out
     sap_bytes = (V // 2) * 4 * (48 + 72 + 24 * 5)
-    roof = {"kernel": "sap_block_kernel<float,128>", "bound": "hbm", "achieved": sap_bytes / sap_launch_s / 1e9,
-            "peak": hbm, "unit": "GB/s", "frac": sap_bytes / sap_launch_s / 1e9 / hbm, "traffic": None,
-            "peak_kind": peak_kind, "launch_us": sap_launch_s * 1e6, "algorithmic_bytes_per_launch": sap_bytes}
+    roof_sap = {"kernel": "sap_staged_kernel<128>", "bound": "hbm", "achieved": sap_bytes / sap_launch_s / 1e9,
+                "peak": hbm, "unit": "GB/s", "frac": sap_bytes / sap_launch_s / 1e9 / hbm,
+                "launch_us": sap_launch_s * 1e6, "algorithmic_bytes_per_launch": sap_bytes}
 
     # ---- D_w bandwidth: FP32 and FP64 applications, L2 flushed before each timed launch
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -373,7 +393,7 @@ def main():
                             for k in ("t_sap", "t_dirac", "t_project", "t_little", "t_orth", "t_restart")},
                 "dfl_build_s": t_build, "plain_fp64": plain,
                 "speedup_vs_plain_fp64": (plain["s_per_solve"] / value) if plain else None,
-                "dirac": dirac, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "dirac": dirac, "roofline": roof, "roofline_sap": roof_sap, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "batch12": batch}
         print(json.dumps(line), flush=True)
     if world > 1:

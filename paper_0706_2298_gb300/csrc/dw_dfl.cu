@@ -690,18 +690,25 @@ inline unsigned warps_grid(int n, int threads = 128) { return (unsigned)((n * 32
 // ------------------------------------------------------------------ cooperative little GCR (A.2-A.4)
 // The whole even-odd, globally deflated little GCR in one persistent kernel:
 // grid-wide barriers replace the host round trips of the host-driven loop.
-// Ownership: CTA c owns the contiguous slice [c S, (c+1) S) of the n = Ne Ns
-// vector entries (elementwise work) and the contiguous range of block rows
-// [c R, (c+1) R) of each parity (hops).  Reductions: per-CTA sums in shared
+// Ownership: CTA c owns the contiguous range of block rows [c R, (c+1) R) of
+// each parity, and with its even rows the entries of every even-site little
+// vector on them, so the even hop and all elementwise work and inner products
+// that follow it stay inside the CTA.  Reductions: per-CTA sums in shared
 // memory -> one partial per CTA in global memory -> after the barrier every
 // CTA adds the partials in CTA order (identical, deterministic values in every
 // CTA).  Inner products with many vectors are CTA-slice GEMVs: warp w owns the
-// vectors j = w, w + 8, ...
+// vectors j = w, w + 8, ...  One GCR step takes four grid barriers: after the
+// odd hop, and three reductions (the A.3 projection and the Gram-Schmidt
+// coefficients share one, with the coefficients of the projected vector
+// obtained from those of the raw vector and a table of (chi_j, B^ g_l)).
 constexpr int COOP_THREADS = 256;
 constexpr int COOP_WARPS = COOP_THREADS / 32;
-constexpr int COOP_NV = 64;          // values per grid reduction
+constexpr int COOP_NV = 128;         // values per grid reduction
 constexpr int COOP_NKV = 24;         // Krylov vectors per cycle
 constexpr int COOP_CH = 16;          // block rows per hop chunk
+#ifndef COOP_HOP_DEPTH
+#define COOP_HOP_DEPTH 2             // rows in flight per warp in the FP32 hops
+#endif
 
 template <typename T>
 struct CoopArgs {
@@ -710,7 +717,7 @@ struct CoopArgs {
   const T *M, *g, *Bg, *Ainv, *b;
   T* v;
   T* work;            // (2 nkv + 4) vectors of Ne*Ns complex
-  T* partial;         // [2][COOP_NV][gridDim]
+  T* partial;         // [2][COOP_NV][coop_gpad(gridDim)]
   double* out;        // [0] iterations, [1] relative residual
   double tol;
 };
@@ -725,25 +732,34 @@ struct CoopShared {
   T res[COOP_NV];            // grid-wide sums
   T a[2 * COOP_NKV], c[COOP_NKV], beta[2 * COOP_NKV];
   T bb[COOP_NKV][2 * COOP_NKV];
+  T tg[COOP_NKV][2 * 32];    // (chi_j, B^ g_l) of the current cycle's chi_j
   T z[2 * 32];
   T ainv[2 * 32 * 32];       // A~^{-1}, row-major
   int phase;
 };
 
+// row stride of the partial-sum table: a multiple of 4 so that it is read with 16-byte loads
+DW_HD int coop_gpad(int grid) { return (grid + 3) & ~3; }
+
+// values staged in shared memory at a time by a grid reduction
+template <typename T>
+__host__ __device__ constexpr int coop_stage_v() { return sizeof(T) == 4 ? 128 : 64; }
+
 // dynamic shared memory of the cooperative kernel: reduction staging + hop partial sums
 template <typename T>
 inline size_t coop_dyn_smem(int grid) {
-  return ((size_t)COOP_NV * grid + (size_t)COOP_CH * 8 * 64) * sizeof(T);
+  return ((size_t)coop_stage_v<T>() * coop_gpad(grid) + (size_t)COOP_CH * 8 * 64) * sizeof(T);
 }
 
 struct CoopSlice {
   size_t s0, s1;
 };
 
-DW_D CoopSlice coop_slice(size_t n) {
-  const size_t S = (n + gridDim.x - 1) / gridDim.x;
-  const size_t s0 = min(n, (size_t)blockIdx.x * S);
-  return {s0, min(n, s0 + S)};
+// entries of the even-site little vectors on this CTA's even block rows
+DW_D CoopSlice coop_rows_slice(int nrow, int ns) {
+  const int R = (nrow + gridDim.x - 1) / gridDim.x;
+  const int rb = min(nrow, (int)blockIdx.x * R), re = min(nrow, rb + R);
+  return {(size_t)rb * ns, (size_t)re * ns};
 }
 
 template <typename T>
@@ -753,40 +769,52 @@ DW_D T warp_allsum(T y) {
   return y;
 }
 
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using t = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using t = double2; static constexpr int n = 2; };
+
 // Sum the nv values sh.cta[0..nv) over all CTAs; result in sh.res (all CTAs).
 // Two partial buffers used alternately: a CTA that runs ahead into the next
 // reduction cannot overwrite partials another CTA is still adding up.
 template <typename T>
 DW_D void coop_reduce(cg::grid_group& grid, CoopShared<T>& sh, int nv, T* partial_base, T* stage) {
-  const int G = gridDim.x;
-  T* partial = partial_base + (size_t)(sh.phase & 1) * G * COOP_NV;
+  const int G = gridDim.x, Gp = coop_gpad(G);
+  T* partial = partial_base + (size_t)(sh.phase & 1) * Gp * COOP_NV;
   __syncthreads();
-  if (threadIdx.x < nv) partial[threadIdx.x * G + blockIdx.x] = sh.cta[threadIdx.x];
+  if (threadIdx.x < nv) partial[threadIdx.x * Gp + blockIdx.x] = sh.cta[threadIdx.x];
   grid.sync();
-  // copy the nv x G partials into shared memory, 8 loads in flight per thread
-  const int tot = G * nv;
-  for (int base = 0; base < tot; base += 8 * COOP_THREADS) {
-    T v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * COOP_THREADS + threadIdx.x;
-      v[u] = idx < tot ? __ldcg(partial + idx) : T(0);
+  using V = typename Vec16<T>::t;
+  constexpr int VN = Vec16<T>::n;
+  constexpr int SV = coop_stage_v<T>();
+  for (int v0 = 0; v0 < nv; v0 += SV) {
+    const int cv = min(SV, nv - v0);
+    // copy the cv x Gp partials into shared memory: 16-byte asynchronous copies, all in flight
+    const int tot = cv * Gp / VN;
+    const V* src = reinterpret_cast<const V*>(partial + (size_t)v0 * Gp);
+    V* dst = reinterpret_cast<V*>(stage);
+    for (int idx = threadIdx.x; idx < tot; idx += COOP_THREADS) {
+      const unsigned saddr = (unsigned)__cvta_generic_to_shared(dst + idx);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(src + idx) : "memory");
     }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * COOP_THREADS + threadIdx.x;
-      if (idx < tot) stage[idx] = v[u];
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    // tpv threads per value (neighbouring lanes), each adding every tpv-th partial with two
+    // accumulators, then a butterfly over the tpv lanes: a fixed order in every CTA
+    int tpv = 32;
+    while (tpv > 1 && tpv * cv > COOP_THREADS) tpv >>= 1;
+    const int j = threadIdx.x / tpv, sub = threadIdx.x - j * tpv;
+    T y0 = 0, y1 = 0;
+    if (j < cv) {
+      const T* row = stage + j * Gp;
+      int q = sub;
+      for (; q + tpv < G; q += 2 * tpv) { y0 += row[q]; y1 += row[q + tpv]; }
+      if (q < G) y0 += row[q];
     }
+    T y = y0 + y1;
+    for (int o = tpv >> 1; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+    if (j < cv && sub == 0) sh.res[v0 + j] = y;
+    __syncthreads();
   }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int j = w; j < nv; j += COOP_WARPS) {
-    T y = 0;
-    for (int q = lane; q < G; q += 32) y += stage[j * G + q];
-    y = warp_allsum(y);
-    if (lane == 0) sh.res[j] = y;
-  }
-  __syncthreads();
   if (threadIdx.x == 0) sh.phase += 1;
   __syncthreads();
 }
@@ -810,25 +838,40 @@ DW_D void cta_sum(CoopShared<T>& sh, T (&x)[NV]) {
   }
 }
 
-// sh.cta[2j], sh.cta[2j+1] = this CTA's share of (X_j, y) for j < nvec; X_j = X + j xstride.
-// Starts with a CTA barrier (y may have been written by other threads of the CTA).
+// sh.cta[off + 2j], sh.cta[off + 2j + 1] = this CTA's share of (X_j, y) for j < nvec;
+// X_j = X + j xstride.  Starts with a CTA barrier (y may have been written by other
+// threads of the CTA).
 template <typename T>
 DW_D void cta_dots(CoopShared<T>& sh, const cplx<T>* X, size_t xstride, int nvec, const cplx<T>* y,
-                   const CoopSlice& sl) {
+                   const CoopSlice& sl, int off) {
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int j = w; j < nvec; j += COOP_WARPS) {
-    const cplx<T>* x = X + (size_t)j * xstride;
-    T re = 0, im = 0;
+  // four vectors per warp and pass (j0 + 8u), so that their loads are in flight together;
+  // the eight sums of a warp are reduced by recursive halving
+  for (int j0 = w; j0 < nvec; j0 += 4 * COOP_WARPS) {
+    const cplx<T>* xs[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int jj = j0 + u * COOP_WARPS;
+      xs[u] = X + (size_t)(jj < nvec ? jj : j0) * xstride;
+    }
+    T acc[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) acc[m] = 0;
 #pragma unroll 4
     for (size_t i = sl.s0 + lane; i < sl.s1; i += 32) {
-      const cplx<T> p = x[i], q = y[i];
-      re += p.re * q.re + p.im * q.im;
-      im += p.re * q.im - p.im * q.re;
+      const cplx<T> q = y[i];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const cplx<T> p = xs[u][i];
+        acc[2 * u] += p.re * q.re + p.im * q.im;
+        acc[2 * u + 1] += p.re * q.im - p.im * q.re;
+      }
     }
-    re = warp_allsum(re);
-    im = warp_allsum(im);
-    if (lane == 0) { sh.cta[2 * j] = re; sh.cta[2 * j + 1] = im; }
+    int base = 0;
+    WarpHalve<T, 8, 16>::run(acc, lane, base);     // lane holds the sum of value 'base'
+    const int u = base >> 1, jj = j0 + u * COOP_WARPS;
+    if ((lane & 3) == 0 && jj < nvec) sh.cta[off + 2 * jj + (base & 1)] = acc[0];
   }
 }
 
@@ -871,19 +914,25 @@ DW_D void coop_hop(int nrow, int Ns, const int* list, const int* lnb, const T* M
     int myL = 0, myj = 0;
     if (lane < nr) { myL = list[r0 + lane]; myj = lnb[(r0 + lane) * 8 + w]; }
     if constexpr (PIPE) {
-      RowLoad<T, (PIPE ? NS : 1)> buf[2];
-      buf[0].load(Mc + ((size_t)__shfl_sync(0xffffffffu, myL, 0) * 8 + w) * NS * NS,
-                  src + (size_t)__shfl_sync(0xffffffffu, myj, 0) * NS, lane);
-      for (int q = 0; q < nr; q += 2) {
-        if (q + 1 < nr)
-          buf[1].load(Mc + ((size_t)__shfl_sync(0xffffffffu, myL, q + 1) * 8 + w) * NS * NS,
-                      src + (size_t)__shfl_sync(0xffffffffu, myj, q + 1) * NS, lane);
-        hp[(q * 8 + w) * 32 + lane] = buf[0].mv();
-        if (q + 1 < nr) {
-          if (q + 2 < nr)
-            buf[0].load(Mc + ((size_t)__shfl_sync(0xffffffffu, myL, q + 2) * 8 + w) * NS * NS,
-                        src + (size_t)__shfl_sync(0xffffffffu, myj, q + 2) * NS, lane);
-          hp[((q + 1) * 8 + w) * 32 + lane] = buf[1].mv();
+      // rolling register pipeline: the blocks of the next COOP_HOP_DEPTH - 1 rows are in flight
+      // while the current row is multiplied
+      constexpr int NB = COOP_HOP_DEPTH;
+      RowLoad<T, (PIPE ? NS : 1)> buf[NB];
+      auto load_row = [&](RowLoad<T, (PIPE ? NS : 1)>& b, int q) {
+        b.load(Mc + ((size_t)__shfl_sync(0xffffffffu, myL, q) * 8 + w) * NS * NS,
+               src + (size_t)__shfl_sync(0xffffffffu, myj, q) * NS, lane);
+      };
+#pragma unroll
+      for (int u = 0; u < NB - 1; ++u)
+        if (u < nr) load_row(buf[u], u);
+      for (int q0 = 0; q0 < nr; q0 += NB) {
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+          const int q = q0 + u;
+          if (q < nr) {
+            if (q + NB - 1 < nr) load_row(buf[(u + NB - 1) % NB], q + NB - 1);
+            hp[(q * 8 + w) * 32 + lane] = buf[u].mv();
+          }
         }
       }
     } else {
@@ -917,23 +966,16 @@ DW_D void coop_bhat(cg::grid_group& grid, const CoopArgs<T>& a, const cplx<T>* x
   __syncthreads();
   grid.sync();
   __syncthreads();
-  coop_hop<T, NS>(a.Ne, a.Ns, a.list_e, a.lnb_e, a.M, tmpo, x, y, T(-1), hp);         // y = x - M_eo tmpo
+  coop_hop<T, NS>(a.Ne, a.Ns, a.list_e, a.lnb_e, a.M, tmpo, x, y, T(-1), hp);       // y = x - M_eo tmpo
   __syncthreads();
   grid.sync();
   __syncthreads();
 }
 
-// u -= Bg A~^{-1} g^+ u  (P~_L, in place); with add_to set, only z = A~^{-1} g^+ u is formed and
-// add_to += g z is applied instead.  Elementwise parts on the CTA slice, no trailing barrier.
-template <typename T, int NS>
-DW_D void coop_PL(cg::grid_group& grid, CoopShared<T>& sh, const CoopArgs<T>& a, cplx<T>* u, const cplx<T>* gsrc,
-                  const cplx<T>* bgsrc, cplx<T>* add_to, T* stage, const CoopSlice& sl) {
-  constexpr int NSM = NS ? NS : 32;
-  const size_t n = (size_t)a.Ne * a.Ns;
-  const int Ns = NS ? NS : a.Ns;
-  cta_dots<T>(sh, gsrc, n, Ns, u, sl);
-  coop_reduce(grid, sh, 2 * Ns, a.partial, stage);
-  if (threadIdx.x < Ns) {          // z = A~^{-1} y
+// z = A~^{-1} u with u = sh.res[0..2 Ns), into sh.z (threads < Ns; no barrier)
+template <typename T>
+DW_D void coop_z(CoopShared<T>& sh, int Ns) {
+  if (threadIdx.x < Ns) {
     T zr = 0, zi = 0;
     for (int q = 0; q < Ns; ++q) {
       const T mr = sh.ainv[2 * (threadIdx.x * Ns + q)], mi = sh.ainv[2 * (threadIdx.x * Ns + q) + 1];
@@ -944,6 +986,19 @@ DW_D void coop_PL(cg::grid_group& grid, CoopShared<T>& sh, const CoopArgs<T>& a,
     sh.z[2 * threadIdx.x] = zr;
     sh.z[2 * threadIdx.x + 1] = zi;
   }
+}
+
+// u -= Bg A~^{-1} g^+ u  (P~_L, in place); with add_to set, only z = A~^{-1} g^+ u is formed and
+// add_to += g z is applied instead.  Elementwise parts on the CTA's rows, no trailing barrier.
+template <typename T, int NS>
+DW_D void coop_PL(cg::grid_group& grid, CoopShared<T>& sh, const CoopArgs<T>& a, cplx<T>* u, const cplx<T>* gsrc,
+                  const cplx<T>* bgsrc, cplx<T>* add_to, T* stage, const CoopSlice& sl) {
+  constexpr int NSM = NS ? NS : 32;
+  const size_t n = (size_t)a.Ne * a.Ns;
+  const int Ns = NS ? NS : a.Ns;
+  cta_dots<T>(sh, gsrc, n, Ns, u, sl, 0);
+  coop_reduce(grid, sh, 2 * Ns, a.partial, stage);
+  coop_z(sh, Ns);
   __syncthreads();
   cplx<T>* tgt = add_to ? add_to : u;
   const cplx<T>* vecs = add_to ? gsrc : bgsrc;
@@ -963,18 +1018,21 @@ DW_D void coop_PL(cg::grid_group& grid, CoopShared<T>& sh, const CoopArgs<T>& a,
 
 template <typename T, int NS>
 __global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_kernel(CoopArgs<T> a) {
+  constexpr int NSM = NS ? NS : 32;
   cg::grid_group grid = cg::this_grid();
   __shared__ CoopShared<T> sh;
   extern __shared__ __align__(16) unsigned char coop_dyn[];
-  T* stage = reinterpret_cast<T*>(coop_dyn);                                   // [COOP_NV][gridDim]
-  cplx<T>* hp = reinterpret_cast<cplx<T>*>(stage + (size_t)COOP_NV * gridDim.x);  // [COOP_CH][8][32]
-  const size_t n = (size_t)a.Ne * a.Ns;
-  const CoopSlice sl = coop_slice(n);
+  T* stage = reinterpret_cast<T*>(coop_dyn);                                          // [stage_v][Gp]
+  cplx<T>* hp = reinterpret_cast<cplx<T>*>(stage + (size_t)coop_stage_v<T>() * coop_gpad(gridDim.x));  // [COOP_CH][8][32]
+  const int ns = NS ? NS : a.Ns;
+  const size_t n = (size_t)a.Ne * ns;
+  const CoopSlice sl = coop_rows_slice(a.Ne, ns);
   const int nkv = a.nkv;
+  const int na = a.a3 ? 2 * ns : 0;          // reduced values of the A.3 projection
   if (threadIdx.x == 0) sh.phase = 0;
   if (a.a3) {
     const cplx<T>* Ai = reinterpret_cast<const cplx<T>*>(a.Ainv);
-    for (int t = threadIdx.x; t < a.Ns * a.Ns; t += COOP_THREADS) {
+    for (int t = threadIdx.x; t < ns * ns; t += COOP_THREADS) {
       sh.ainv[2 * t] = Ai[t].re;
       sh.ainv[2 * t + 1] = Ai[t].im;
     }
@@ -994,7 +1052,6 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_kernel(CoopAr
   auto slice = [&](auto&& f) {
     for (size_t i = sl.s0 + threadIdx.x; i < sl.s1; i += COOP_THREADS) f(i);
   };
-  const int lane = threadIdx.x & 31;
 
   // rhsd = P~_L b, rho = rhsd, v = 0
   slice([&](size_t i) { rhsd[i] = b[i]; });
@@ -1016,41 +1073,65 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_kernel(CoopAr
     for (; k < nkv && total < a.maxit; ++k) {
       cplx<T>* ck = chi(k);
       cplx<T>* xk = xi(k);
-      // xi_k = rho;  chi_k = P~_L B^ rho  (rho is stable until the update below)
+      // xi_k = rho;  chi_k = B^ rho  (rho is stable until the update below); the even hop
+      // writes this CTA's own rows, so no grid barrier follows it
       slice([&](size_t i) { xk[i] = rho[i]; });
-      coop_bhat<T, NS>(grid, a, rho, tmpo, ck, hp);
-      if (a.a3) coop_PL<T, NS>(grid, sh, a, ck, g, Bg, nullptr, stage, sl);
-      if (k > 0) {
-        cta_dots<T>(sh, W, n, k, ck, sl);
-        coop_reduce(grid, sh, 2 * k, a.partial, stage);
-        if (threadIdx.x < 2 * k) sh.bb[threadIdx.x >> 1][2 * k + (threadIdx.x & 1)] = sh.res[threadIdx.x];
-        __syncthreads();
-        slice([&](size_t i) {
-          cplx<T> y = ck[i];
-#pragma unroll
-          for (int j = 0; j < COOP_NKV; ++j) {
-            if (j < k) {
-              const cplx<T> bj = {sh.bb[j][2 * k], sh.bb[j][2 * k + 1]};
-              y -= bj * chi(j)[i];
-            }
+      coop_hop<T, NS>(a.No, ns, a.list_o, a.lnb_o, a.M, rho, nullptr, tmpo, T(1), hp);
+      __syncthreads();
+      grid.sync();
+      __syncthreads();
+      coop_hop<T, NS>(a.Ne, ns, a.list_e, a.lnb_e, a.M, tmpo, rho, ck, T(-1), hp);
+      // one reduction: u = g^+ chi_k (A.3) and the raw coefficients (chi_j, chi_k), j < k
+      if (a.a3) cta_dots<T>(sh, g, n, ns, ck, sl, 0);
+      if (k > 0) cta_dots<T>(sh, W, n, k, ck, sl, na);
+      if (na + 2 * k > 0) coop_reduce(grid, sh, na + 2 * k, a.partial, stage);
+      if (a.a3) coop_z(sh, ns);
+      __syncthreads();
+      // coefficients of the projected vector P~_L chi_k: (chi_j, chi_k) - sum_l z_l (chi_j, B^ g_l)
+      if (threadIdx.x < k) {
+        const int j = threadIdx.x;
+        T br = sh.res[na + 2 * j], bi = sh.res[na + 2 * j + 1];
+        if (a.a3) {
+          for (int l = 0; l < ns; ++l) {
+            const T zr = sh.z[2 * l], zi = sh.z[2 * l + 1], tr = sh.tg[j][2 * l], ti = sh.tg[j][2 * l + 1];
+            br -= zr * tr - zi * ti;
+            bi -= zr * ti + zi * tr;
           }
-          ck[i] = y;
-        });
+        }
+        sh.bb[j][2 * k] = br;
+        sh.bb[j][2 * k + 1] = bi;
       }
+      __syncthreads();
+      // chi_k <- P~_L chi_k - sum_j b_jk chi_j ; then (chi_k, rho), |chi_k|^2 and (B^ g_l, chi_k)
       T s3[3] = {0, 0, 0};
       slice([&](size_t i) {
-        const cplx<T> x = ck[i], y = rho[i];
-        s3[0] += x.re * y.re + x.im * y.im;
-        s3[1] += x.re * y.im - x.im * y.re;
-        s3[2] += x.re * x.re + x.im * x.im;
+        cplx<T> y = ck[i];
+        if (a.a3) {
+#pragma unroll
+          for (int l = 0; l < NSM; ++l)
+            if (l < ns) y -= cplx<T>{sh.z[2 * l], sh.z[2 * l + 1]} * Bg[(size_t)l * n + i];
+        }
+#pragma unroll
+        for (int j = 0; j < COOP_NKV; ++j)
+          if (j < k) y -= cplx<T>{sh.bb[j][2 * k], sh.bb[j][2 * k + 1]} * chi(j)[i];
+        ck[i] = y;
+        const cplx<T> r = rho[i];
+        s3[0] += y.re * r.re + y.im * r.im;
+        s3[1] += y.re * r.im - y.im * r.re;
+        s3[2] += y.re * y.re + y.im * y.im;
       });
       cta_sum<T, 3>(sh, s3);
-      coop_reduce(grid, sh, 3, a.partial, stage);
+      if (a.a3) cta_dots<T>(sh, Bg, n, ns, ck, sl, 3);
+      coop_reduce(grid, sh, 3 + na, a.partial, stage);
       const T cn = sqrt(sh.res[2]);
       if (!(cn > 0)) break;
       const T inv = T(1) / cn;
       const T ar = sh.res[0] * inv, ai = sh.res[1] * inv;
       if (threadIdx.x == 0) { sh.c[k] = cn; sh.a[2 * k] = ar; sh.a[2 * k + 1] = ai; }
+      if (a.a3 && threadIdx.x < ns) {     // (chi_k, B^ g_l) = conj((B^ g_l, chi_k)) / c_k
+        sh.tg[k][2 * threadIdx.x] = sh.res[3 + 2 * threadIdx.x] * inv;
+        sh.tg[k][2 * threadIdx.x + 1] = -sh.res[3 + 2 * threadIdx.x + 1] * inv;
+      }
       s1[0] = 0;
       const cplx<T> ak = {ar, ai};
       slice([&](size_t i) {
@@ -1068,6 +1149,7 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_kernel(CoopAr
     }
     // back substitution by warp 0 (lane i holds row i), then v += sum beta_k xi_k
     if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
       T br = lane < k ? sh.a[2 * lane] : T(0), bi = lane < k ? sh.a[2 * lane + 1] : T(0);
       for (int j = k - 1; j >= 0; --j) {
         const T cj = sh.c[j];
@@ -1930,18 +2012,18 @@ static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_c
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-    const size_t dsm = coop_dyn_smem<double>(sms);
+    const size_t dsm32 = coop_dyn_smem<float>(sms), dsm64 = coop_dyn_smem<double>(sms);
     NS_DISPATCH(Ns, (cudaFuncSetAttribute(little_gcr_coop_kernel<float, NSV>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm)));
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm32)));
     NS_DISPATCH(Ns, (cudaFuncSetAttribute(little_gcr_coop_kernel<double, NSV>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm)));
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm64)));
     NS_DISPATCH(Ns, (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, little_gcr_coop_kernel<float, NSV>,
-                                                                   COOP_THREADS, dsm)));
+                                                                   COOP_THREADS, dsm32)));
     NS_DISPATCH(Ns, (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, little_gcr_coop_kernel<double, NSV>,
-                                                                   COOP_THREADS, dsm)));
+                                                                   COOP_THREADS, dsm64)));
     d->coop_grid = (coop && b32 > 0 && b64 > 0 && Ns <= 32) ? sms : 0;
     if (d->coop_grid) {
-      DW_CUDA(cudaMalloc(&d->coop_partial, (size_t)2 * d->coop_grid * COOP_NV * sizeof(double)));
+      DW_CUDA(cudaMalloc(&d->coop_partial, (size_t)2 * coop_gpad(d->coop_grid) * COOP_NV * sizeof(double)));
       DW_CUDA(cudaMalloc(&d->coop_out, 2 * 64 * sizeof(double)));
     }
     if ((rc = ensure_little_work(d, DW_F64, COOP_NKV))) return rc;
