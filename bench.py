@@ -40,9 +40,11 @@ WORKLOADS = {
 MASS_FILE = os.path.join(ROOT, "paper_0706_2298_gb300", "workload_masses.json")
 
 
-# DRAM bytes per little-GCR iteration of the cooperative kernel, from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum of one launch / its iterations); None until taken
-LITTLE_TRAFFIC = {}
+# DRAM bytes per little-GCR iteration of the cooperative kernel, from one ncu capture of the
+# current kernel (dram__bytes_read.sum + dram__bytes_write.sum of one launch / its iterations):
+# 48x24^3, Ns = 20: (84.87 + 4.76) MB over 42 iterations (cold cache: the first iteration reads
+# the little operator from HBM, the rest hit L2).  Remove an entry when the kernel changes.
+LITTLE_TRAFFIC = {("24^3x48", 20): 89.63e6 / 42}
 
 
 def load_masses():
