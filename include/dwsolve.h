@@ -55,7 +55,12 @@ typedef enum {
   DW_ILLCOND = 2       /* a diagonal little block was ill-conditioned (Appendix A.2) */
 } dw_status;
 
-typedef enum { DW_F64 = 0, DW_F32 = 1, DW_BF16 = 2 } dw_prec;
+/* DW_F64X: FP64 fields and results, computed in double-float arithmetic (each real as the
+ * unevaluated sum of two FP32 values, about 48 significant bits) on the FP32 pipes, whose rate on
+ * this GPU is many times its FP64 rate; accepted by dw_apply (DW_OP_FULL), dfl_restrict and
+ * dfl_prolong, and used for the restart steps of the mixed-precision solver.  Relative error of
+ * D in a few 1e-14. */
+typedef enum { DW_F64 = 0, DW_F32 = 1, DW_BF16 = 2, DW_F64X = 3 } dw_prec;
 
 typedef enum { DW_OP_FULL = 0, DW_OP_SCHUR = 1 } dw_op;
 
@@ -96,7 +101,8 @@ int dw_unpack(dw_ctx* ctx, int prec, int nrhs, const void* packed_dev, double* c
 
 /* out = D in (op = DW_OP_FULL) or, on even sites, out = (A_ee - D_eo A_oo^{-1} D_oe) in
  * with odd sites of out set to zero (op = DW_OP_SCHUR; even-odd Schur complement).
- * in/out: nrhs packed fields of precision prec; in != out. */
+ * in/out: nrhs packed fields of precision prec; in != out.  prec DW_F64X: FP64 packed fields
+ * (pack with DW_F64), DW_OP_FULL only, computed in double-float arithmetic. */
 int dw_apply(dw_ctx* ctx, int prec, int op, int nrhs, const void* in_dev, void* out_dev, void* stream);
 
 /* The Schur complement of dw_apply(DW_OP_SCHUR) for one field, allocating no memory.  The
@@ -167,7 +173,8 @@ int dfl_dims(const dfl_ctx* d, int* Nb, int* Ns);
 
 /* Little vectors: complex[Nb][Ns] (re, im interleaved) of precision prec,
  * block index = lexicographic deflation-block coordinate (x0 slowest).
- * c = Phi^+ psi  (block restriction of (4.1));  psi = Phi c  (prolongation). */
+ * c = Phi^+ psi  (block restriction of (4.1));  psi = Phi c  (prolongation).
+ * prec DW_F64X: FP64 fields and little vectors, computed in double-float arithmetic. */
 int dfl_restrict(dfl_ctx* d, int prec, const void* psi_packed_dev, void* c_dev, void* stream);
 int dfl_prolong(dfl_ctx* d, int prec, const void* c_dev, void* psi_packed_dev, void* stream);
 /* The stored basis as canonical FP64 fields complex128[Ns][V][4][3]: field l

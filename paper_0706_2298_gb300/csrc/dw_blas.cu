@@ -292,3 +292,77 @@ template void field_convert<double, float>(const double*, float*, double, size_t
 template void field_convert<float, double>(const float*, double*, double, size_t, cudaStream_t);
 template void field_convert<double, double>(const double*, double*, double, size_t, cudaStream_t);
 template void field_convert<float, float>(const float*, float*, double, size_t, cudaStream_t);
+
+// ---------------------------------------------------------------- double-float conversions
+namespace {
+
+// double -> (hi, lo): hi = x with its fraction cut to 23 bits, lo = the remaining 29 bits rounded
+// to FP32 (relative error <= 2^-48).  Integer operations only; zero, tiny (|x| < 2^-74), huge,
+// infinite and NaN values take a plain conversion.
+DW_D dd split_double(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e < 949 || e > 1150) {
+    const float h = __double2float_rz(x);
+    return {h, __double2float_rn(x - (double)h)};
+  }
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const float hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
+  const float lo = __uint2float_rn((unsigned)(b & 0x1FFFFFFFull)) * __uint_as_float((unsigned)(e - 948) << 23);
+  return {hi, sign ? -lo : lo};
+}
+// FP32 -> FP64 by moving exponent and fraction (exact); zero and subnormal/special values aside
+DW_D double widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if ((u & 0x7FFFFFFFu) == 0) return __longlong_as_double((long long)((unsigned long long)u << 32));
+  if (e == 0 || e == 255) return (double)f;
+  return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) |
+                                          ((unsigned long long)(e + 896) << 52) |
+                                          ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+
+__global__ void f64_to_dd_kernel(const double2* __restrict__ x, float4* __restrict__ y, size_t n2) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 v = x[i];
+    const dd a = split_double(v.x), b = split_double(v.y);
+    y[i] = make_float4(a.hi, a.lo, b.hi, b.lo);
+  }
+}
+__global__ void dd_to_f64_kernel(const float4* __restrict__ x, double2* y, size_t n2, int add) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 v = x[i];
+    double2 o = make_double2(widen(v.x) + widen(v.y), widen(v.z) + widen(v.w));
+    if (add) {
+      const double2 t = y[i];
+      o.x += t.x;
+      o.y += t.y;
+    }
+    y[i] = o;
+  }
+}
+
+}  // namespace
+
+void f64_to_dd(const double* x, dd* y, size_t n_real, cudaStream_t s) {
+  const size_t n2 = n_real / 2;
+  f64_to_dd_kernel<<<RGRID * 2, 256, 0, s>>>(reinterpret_cast<const double2*>(x), reinterpret_cast<float4*>(y), n2);
+  dw_note_launch();
+}
+void dd_to_f64(const dd* x, double* y, size_t n_real, int add, cudaStream_t s) {
+  const size_t n2 = n_real / 2;
+  dd_to_f64_kernel<<<RGRID * 2, 256, 0, s>>>(reinterpret_cast<const float4*>(x), reinterpret_cast<double2*>(y), n2,
+                                            add);
+  dw_note_launch();
+}
+
+int dw_make_dd(dw_ctx* c, cudaStream_t s) {
+  if (c->links_dd) return DW_OK;
+  const size_t nl = (size_t)c->V * 4 * 12, nc = (size_t)c->V * 72;   // reals (FP64 layouts)
+  DW_CUDA(cudaMalloc(&c->links_dd, nl * sizeof(dd)));
+  DW_CUDA(cudaMalloc(&c->clov_dd, nc * sizeof(dd)));
+  f64_to_dd((const double*)c->links[DW_F64], (dd*)c->links_dd, nl, s);
+  f64_to_dd((const double*)c->clov[DW_F64], (dd*)c->clov_dd, nc, s);
+  DW_CUDA(cudaGetLastError());
+  return DW_OK;
+}

@@ -66,6 +66,52 @@ DW_D void unpack_unit(const double2& v, cplx<double>* c) { c[0] = {v.x, v.y}; }
 DW_D float4 pack_unit(const cplx<float>* c) { return make_float4(c[0].re, c[0].im, c[1].re, c[1].im); }
 DW_D double2 pack_unit(const cplx<double>* c) { return make_double2(c[0].re, c[0].im); }
 
+// ---------------------------------------------------------------- double-float ("dd") arithmetic
+// A real number held as an unevaluated sum hi + lo of two FP32 values (|lo| <= ulp(hi)/2),
+// about 48 significant bits.  Sums use Knuth's TwoSum, products Dekker's exact product formed
+// with one FMA; both run on the FP32 pipes, whose rate on this part is many times the FP64 rate.
+// Used where FP64-class accuracy is needed on large fields (restart residuals, restriction,
+// prolongation).  Memory form: the FP64 layout with every double replaced by (hi, lo) floats.
+struct dd {
+  float hi, lo;
+  dd() = default;
+  DW_HD constexpr dd(float h, float l) : hi(h), lo(l) {}
+  DW_HD constexpr dd(float f) : hi(f), lo(0.f) {}
+  DW_HD constexpr dd(int i) : hi((float)i), lo(0.f) {}
+  DW_HD dd(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+};
+DW_D dd dd_two_sum(float a, float b) {        // exact: a + b = s + e
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+DW_D dd dd_quick_two_sum(float a, float b) {  // exact when |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+DW_D dd operator+(dd a, dd b) {
+  dd s = dd_two_sum(a.hi, b.hi);
+  return dd_quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+DW_D dd operator-(dd a) { return {-a.hi, -a.lo}; }
+DW_D dd operator-(dd a, dd b) { return a + (-b); }
+DW_D dd operator*(dd a, dd b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);                 // exact error of the leading product
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  return dd_quick_two_sum(p, e);
+}
+DW_D dd& operator+=(dd& a, dd b) { a = a + b; return a; }
+DW_D dd& operator-=(dd& a, dd b) { a = a - b; return a; }
+DW_D double dd_to_double(dd a) { return (double)a.hi + (double)a.lo; }
+DW_D dd __shfl_xor_sync(unsigned mask, dd v, int lane) {
+  return {__shfl_xor_sync(mask, v.hi, lane), __shfl_xor_sync(mask, v.lo, lane)};
+}
+template <> struct Unit<dd> { using t = float4; static constexpr int C = 1; };
+DW_D void unpack_unit(const float4& v, cplx<dd>* c) { c[0] = {dd(v.x, v.y), dd(v.z, v.w)}; }
+DW_D float4 pack_unit(const cplx<dd>* c) { return make_float4(c[0].re.hi, c[0].re.lo, c[0].im.hi, c[0].im.lo); }
+
 // load NC complex numbers of site i from unit planes (read-only path)
 template <typename T, int NC>
 DW_D void load_site(const T* __restrict__ base, size_t V, size_t i, cplx<T>* out) {
@@ -265,6 +311,8 @@ struct dw_ctx {
   void* links[2] = {nullptr, nullptr};    // [DW_F64], [DW_F32]
   void* clov[2] = {nullptr, nullptr};
   void* clovinv[2] = {nullptr, nullptr};
+  void* links_dd = nullptr;               // double-float copies (made on first use)
+  void* clov_dd = nullptr;
   void* sap_r[2] = {nullptr, nullptr};    // SAP residual workspace
   void* sap_d[2] = {nullptr, nullptr};    // SAP last-correction workspace
   int sap_cap = 1;                        // right-hand sides the FP32 SAP workspace holds
@@ -314,6 +362,15 @@ template <typename T> void blas_multi_axpy(const T* const* vs, int k, const doub
 // out = sum_j coef[j] * vs[j]
 template <typename T> void blas_lincomb(const T* const* vs, int k, const double* coef, T* out, size_t n_cplx,
                                         cudaStream_t s);
+
+// double-float fields (dd form: the FP64 layout with each double as (hi, lo) floats), n reals
+void f64_to_dd(const double* x, dd* y, size_t n_real, cudaStream_t s);
+// y = dd(x) (add = 0) or y += dd(x) (add = 1), in FP64
+void dd_to_f64(const dd* x, double* y, size_t n_real, int add, cudaStream_t s);
+// make the context's double-float copies of the links and the clover term (once)
+int dw_make_dd(dw_ctx* c, cudaStream_t s);
+// out = D in on dd-form fields (FP64-class accuracy on the FP32 pipes)
+void dirac_full_dd(dw_ctx* c, const dd* in, dd* out, cudaStream_t s);
 
 // dirac / sap entry points used by the solver ---------------------------------------
 template <typename T> void dirac_full(dw_ctx* c, const T* in, T* out, cudaStream_t s);

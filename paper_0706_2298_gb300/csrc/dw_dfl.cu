@@ -17,6 +17,7 @@
 #include <cmath>
 #include <complex>
 #include <cooperative_groups.h>
+#include <type_traits>
 
 #include "dw_common.cuh"
 
@@ -61,6 +62,8 @@ struct dfl_ctx {
   float* ref32 = nullptr;                              //                  2 FP32 little vectors
   double* coop_partial = nullptr;                      // [coop_grid][64]
   double* coop_out = nullptr;                          // iterations, relative residual
+  dd* ddf = nullptr;                                   // double-float field (restriction/prolongation)
+  dd* ddl = nullptr;                                   // double-float little vector
   // work vectors (little GCR)
   void* lw[2] = {nullptr, nullptr};                    // per precision
   size_t lw_count = 0;
@@ -212,7 +215,7 @@ __global__ void __launch_bounds__(128) restrict_kernel(Geom g, const int* __rest
                                                        const double* b64, const uint4* b16,
                                                        const T* __restrict__ psi0, T* __restrict__ c0, int nrhs,
                                                        size_t fstride, size_t cstride) {
-  __shared__ double sh[2][NSMAX][4];
+  __shared__ T sh[2][NSMAX][4];
   const int L = blockIdx.x;
   const size_t V = g.V;
   const int nsite = nsub * g.svol;
@@ -240,7 +243,7 @@ __global__ void __launch_bounds__(128) restrict_kernel(Geom g, const int* __rest
 #pragma unroll
   for (int k = 0; k < NSMAX; ++k) {
     if (k < Ns) {
-      double re = acc[k].re, im = acc[k].im;
+      T re = acc[k].re, im = acc[k].im;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         re += __shfl_xor_sync(0xffffffffu, re, o);
@@ -252,10 +255,10 @@ __global__ void __launch_bounds__(128) restrict_kernel(Geom g, const int* __rest
   __syncthreads();
   if (threadIdx.x < Ns) {
     int k = threadIdx.x;
-    double re = 0, im = 0;
-    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) { re += sh[0][k][j]; im += sh[1][k][j]; }
-    c[2 * ((size_t)L * Ns + k)] = (T)re;
-    c[2 * ((size_t)L * Ns + k) + 1] = (T)im;
+    T re = sh[0][k][0], im = sh[1][k][0];
+    for (int j = 1; j < (int)(blockDim.x >> 5); ++j) { re += sh[0][k][j]; im += sh[1][k][j]; }
+    c[2 * ((size_t)L * Ns + k)] = re;
+    c[2 * ((size_t)L * Ns + k) + 1] = im;
   }
   __syncthreads();
   }
@@ -299,7 +302,7 @@ struct WarpHalve {
 // c[L][k] = (phi^L_k, psi), Ns known at compile time: CTA per deflation block, per-thread
 // partial sums in the working precision, CTA sum by warp halving + shared memory.
 template <typename T, int NS>
-__global__ void __launch_bounds__(128, 4) restrict_ns_kernel(Geom g, const int* __restrict__ sub, int nsub,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) restrict_ns_kernel(Geom g, const int* __restrict__ sub, int nsub,
                                                              const double* b64, const uint4* b16,
                                                              const T* __restrict__ psi0, T* __restrict__ c0,
                                                              int nrhs, size_t fstride, size_t cstride) {
@@ -1242,7 +1245,7 @@ extern "C" void dfl_destroy(dfl_ctx* d) {
   void* ptrs[] = {d->d_sub, d->d_sap2dfl, d->d_bnb, d->d_list[0], d->d_list[1], d->d_lnb[0], d->d_lnb[1],
                   d->basis64, d->basis16, d->B64, d->Binv64, d->Binv32, d->M64, d->M32, d->g64, d->g32,
                   d->Bg64, d->Bg32, d->lw[0], d->lw[1], d->B32, d->fw[0], d->fw[1], d->Ainv64, d->Ainv32,
-                  d->coop_partial, d->coop_out, d->ref64, d->ref32};
+                  d->coop_partial, d->coop_out, d->ref64, d->ref32, d->ddf, d->ddl};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete d;
@@ -1250,7 +1253,7 @@ extern "C" void dfl_destroy(dfl_ctx* d) {
 
 template <typename T, int NS>
 static bool launch_restrict_ns(dfl_ctx* d, const T* psi, T* c, int nrhs, cudaStream_t s) {
-  if constexpr (NS == 0 || sizeof(T) != 4) {
+  if constexpr (NS == 0 || !std::is_same<T, float>::value) {
     return false;
   } else {
     restrict_ns_kernel<T, NS><<<d->Nb, 128, 0, s>>>(d->c->g, d->d_sub, d->nsub, d->basis16 ? nullptr : d->basis64,
@@ -1279,6 +1282,48 @@ static int prolong_t(dfl_ctx* d, const T* c, T* psi, int mode, cudaStream_t s, i
                                             (size_t)d->N * 2); dw_note_launch();
   return DW_OK;
 }
+template <int NS>
+static bool launch_restrict_dd(dfl_ctx* d, const dd* psi, dd* c, cudaStream_t s) {
+  if constexpr (NS == 0) {
+    return false;
+  } else {
+    restrict_ns_kernel<dd, NS><<<d->Nb, 128, 0, s>>>(d->c->g, d->d_sub, d->nsub, d->basis16 ? nullptr : d->basis64,
+                                                     d->basis16, psi, c, 1, (size_t)d->c->V * 24, (size_t)d->N * 2);
+    return true;
+  }
+}
+static int ensure_dd(dfl_ctx* d) {
+  if (!d->ddf) DW_CUDA(cudaMalloc(&d->ddf, (size_t)d->c->V * 24 * sizeof(dd)));
+  if (!d->ddl) DW_CUDA(cudaMalloc(&d->ddl, (size_t)d->N * 2 * sizeof(dd)));
+  return DW_OK;
+}
+// c = Phi^+ psi for FP64 psi and c, computed in double-float arithmetic on the FP32 pipes
+int dfl_restrict_f64x(dfl_ctx* d, const double* psi, double* c, cudaStream_t s) {
+  int rc = ensure_dd(d);
+  if (rc) return rc;
+  f64_to_dd(psi, d->ddf, (size_t)d->c->V * 24, s);
+  bool done = false;
+  NS_DISPATCH(d->Ns, (done = launch_restrict_dd<NSV>(d, d->ddf, d->ddl, s)));
+  if (!done)
+    restrict_kernel<dd><<<d->Nb, 128, 0, s>>>(d->c->g, d->d_sub, d->nsub, d->Ns, d->basis16 ? nullptr : d->basis64,
+                                              d->basis16, d->ddf, d->ddl, 1, (size_t)d->c->V * 24, (size_t)d->N * 2);
+  dw_note_launch();
+  dd_to_f64(d->ddl, c, (size_t)d->N * 2, 0, s);
+  return DW_OK;
+}
+// psi = Phi c (add = 0) or psi += Phi c (add = 1), FP64 fields, double-float arithmetic
+int dfl_prolong_f64x(dfl_ctx* d, const double* c, double* psi, int add, cudaStream_t s) {
+  int rc = ensure_dd(d);
+  if (rc) return rc;
+  f64_to_dd(c, d->ddl, (size_t)d->N * 2, s);
+  unsigned blocks = (unsigned)((d->c->V + 127) / 128);
+  prolong_kernel<dd><<<blocks, 128, 0, s>>>(d->c->g, d->d_sap2dfl, d->Ns, d->basis16 ? nullptr : d->basis64,
+                                            d->basis16, d->ddl, d->ddf, 0, 1, (size_t)d->c->V * 24,
+                                            (size_t)d->N * 2);
+  dw_note_launch();
+  dd_to_f64(d->ddf, psi, (size_t)d->c->V * 24, add, s);
+  return DW_OK;
+}
 int dfl_restrict_mrhs_f32(dfl_ctx* d, const float* psi, float* c, int nrhs, cudaStream_t s) {
   return restrict_t(d, psi, c, s, nrhs);
 }
@@ -1301,16 +1346,34 @@ int dfl_prolong_f64(dfl_ctx* d, const double* c, double* psi, int mode, cudaStre
 }
 
 extern "C" int dfl_restrict(dfl_ctx* d, int prec, const void* psi, void* c, void* stream) {
-  if (!d || !psi || !c || (prec != DW_F32 && prec != DW_F64)) { dw_set_error("dfl_restrict: bad argument"); return DW_EINVAL; }
+  if (!d || !psi || !c || (prec != DW_F32 && prec != DW_F64 && prec != DW_F64X)) {
+    dw_set_error("dfl_restrict: bad argument");
+    return DW_EINVAL;
+  }
   cudaStream_t s = (cudaStream_t)stream;
+  if (prec == DW_F64X) {
+    int rc = dfl_restrict_f64x(d, (const double*)psi, (double*)c, s);
+    if (rc) return rc;
+    DW_CUDA(cudaGetLastError());
+    return DW_OK;
+  }
   if (prec == DW_F64) restrict_t(d, (const double*)psi, (double*)c, s);
   else restrict_t(d, (const float*)psi, (float*)c, s);
   DW_CUDA(cudaGetLastError());
   return DW_OK;
 }
 extern "C" int dfl_prolong(dfl_ctx* d, int prec, const void* c, void* psi, void* stream) {
-  if (!d || !psi || !c || (prec != DW_F32 && prec != DW_F64)) { dw_set_error("dfl_prolong: bad argument"); return DW_EINVAL; }
+  if (!d || !psi || !c || (prec != DW_F32 && prec != DW_F64 && prec != DW_F64X)) {
+    dw_set_error("dfl_prolong: bad argument");
+    return DW_EINVAL;
+  }
   cudaStream_t s = (cudaStream_t)stream;
+  if (prec == DW_F64X) {
+    int rc = dfl_prolong_f64x(d, (const double*)c, (double*)psi, 0, s);
+    if (rc) return rc;
+    DW_CUDA(cudaGetLastError());
+    return DW_OK;
+  }
   if (prec == DW_F64) prolong_t(d, (const double*)c, (double*)psi, 0, s);
   else prolong_t(d, (const float*)c, (float*)psi, 0, s);
   DW_CUDA(cudaGetLastError());

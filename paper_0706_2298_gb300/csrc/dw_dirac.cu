@@ -162,6 +162,30 @@ void dirac_full(dw_ctx* c, const T* in, T* out, cudaStream_t st) {
 template void dirac_full<float>(dw_ctx*, const float*, float*, cudaStream_t);
 template void dirac_full<double>(dw_ctx*, const double*, double*, cudaStream_t);
 
+void dirac_full_dd(dw_ctx* c, const dd* in, dd* out, cudaStream_t st) {
+  unsigned blocks = (unsigned)((c->V + 127) / 128);
+  dirac_full_kernel<dd><<<blocks, 128, 0, st>>>(c->g, (const dd*)c->links_dd, (const dd*)c->clov_dd, in, out);
+  dw_note_launch();
+}
+
+// FP64 fields through double-float arithmetic: convert, apply, convert back (nrhs fields)
+static int dirac_full_f64x(dw_ctx* c, const double* in, double* out, int nrhs, cudaStream_t st) {
+  int rc = dw_make_dd(c, st);
+  if (rc) return rc;
+  const size_t n = (size_t)c->V * 24;
+  dd *a = nullptr, *b = nullptr;
+  DW_CUDA(cudaMallocAsync(&a, n * sizeof(dd), st));
+  DW_CUDA(cudaMallocAsync(&b, n * sizeof(dd), st));
+  for (int r = 0; r < nrhs; ++r) {
+    f64_to_dd(in + r * n, a, n, st);
+    dirac_full_dd(c, a, b, st);
+    dd_to_f64(b, out + r * n, n, 0, st);
+  }
+  DW_CUDA(cudaFreeAsync(a, st));
+  DW_CUDA(cudaFreeAsync(b, st));
+  return DW_OK;
+}
+
 template <typename T>
 static int dirac_schur(dw_ctx* c, const T* in, T* out, cudaStream_t st) {
   constexpr int P = prec_of<T>();
@@ -174,12 +198,18 @@ static int dirac_schur(dw_ctx* c, const T* in, T* out, cudaStream_t st) {
 }
 
 extern "C" int dw_apply(dw_ctx* c, int prec, int op, int nrhs, const void* in, void* out, void* stream) {
-  if (!c || !in || !out || in == out || nrhs < 1 || (prec != DW_F64 && prec != DW_F32) ||
-      (op != DW_OP_FULL && op != DW_OP_SCHUR)) {
+  if (!c || !in || !out || in == out || nrhs < 1 || (prec != DW_F64 && prec != DW_F32 && prec != DW_F64X) ||
+      (op != DW_OP_FULL && op != DW_OP_SCHUR) || (prec == DW_F64X && op != DW_OP_FULL)) {
     dw_set_error("dw_apply: bad argument");
     return DW_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  if (prec == DW_F64X) {
+    int rc = dirac_full_f64x(c, (const double*)in, (double*)out, nrhs, st);
+    if (rc) return rc;
+    DW_CUDA(cudaGetLastError());
+    return DW_OK;
+  }
   size_t n = (size_t)c->V * 24;
   if (nrhs > 1 && op == DW_OP_FULL) {   // multi-RHS kernel: links and clover read once per site
     if (prec == DW_F64) dirac_mrhs(c, (const double*)in, (double*)out, nrhs, c->tune_rgroup, st);

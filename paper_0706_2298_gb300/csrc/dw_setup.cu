@@ -258,7 +258,8 @@ static void free_ctx(dw_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   void* ptrs[] = {c->d_canon_of, c->d_nbtab, c->d_blk_nb, c->d_blk_x0, c->d_loc, c->d_colour_list,
                   c->links[0], c->links[1], c->clov[0], c->clov[1], c->clovinv[0], c->clovinv[1],
-                  c->sap_r[0], c->sap_r[1], c->sap_d[0], c->sap_d[1], c->d_red, c->d_count};
+                  c->sap_r[0], c->sap_r[1], c->sap_d[0], c->sap_d[1], c->d_red, c->d_count,
+                  c->links_dd, c->clov_dd};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_red) cudaFreeHost(c->h_red);

@@ -39,6 +39,8 @@ int dfl_prolong_mrhs_f32(dfl_ctx*, const float*, float*, int, int, cudaStream_t)
 int little_solve_batch_f32(dfl_ctx*, const float*, float*, const double*, const int*, int, int, int, int*, double*,
                            cudaStream_t);
 int little_solve_refined(dfl_ctx*, const double*, double*, double, int, int, int*, double*, cudaStream_t);
+int dfl_restrict_f64x(dfl_ctx*, const double*, double*, cudaStream_t);
+int dfl_prolong_f64x(dfl_ctx*, const double*, double*, int, cudaStream_t);
 int dfl_restrict_mrhs_f64(dfl_ctx*, const double*, double*, int, cudaStream_t);
 int dfl_prolong_mrhs_f64(dfl_ctx*, const double*, double*, int, int, cudaStream_t);
 
@@ -105,6 +107,7 @@ struct Work {
   std::vector<T*> xi, chi;
   T *rho = nullptr, *w = nullptr, *t1 = nullptr, *lc = nullptr, *lv = nullptr;
   double *eta = nullptr, *psi = nullptr, *r64 = nullptr, *t64 = nullptr, *c64 = nullptr, *v64 = nullptr;
+  dd *dda = nullptr, *ddb = nullptr;     // double-float fields of the mixed restarts
   std::vector<void*> owned;
   int alloc(size_t bytes, void** p) {
     cudaError_t e = cudaMalloc(p, bytes);
@@ -163,9 +166,20 @@ int solve_one(dw_ctx* c, dfl_ctx* d, const sol_params* p, const double* eta_cano
     if (info) *info = inf;
     return DW_OK;
   }
+  if (p->mixed) {      // restart steps in double-float arithmetic on the FP32 pipes
+    if ((rc = dw_make_dd(c, s)) || (rc = W.alloc(V * 24 * sizeof(dd), (void**)&W.dda)) ||
+        (rc = W.alloc(V * 24 * sizeof(dd), (void**)&W.ddb)))
+      return rc;
+  }
   auto residual64 = [&]() -> int {   // r64 = eta - D psi, returns via h[2] = |r|^2
     tm.begin(PH_RESTART);
-    dirac_full<double>(c, W.psi, W.t64, s);
+    if (p->mixed) {
+      f64_to_dd(W.psi, W.dda, V * 24, s);
+      dirac_full_dd(c, W.dda, W.ddb, s);
+      dd_to_f64(W.ddb, W.t64, V * 24, 0, s);
+    } else {
+      dirac_full<double>(c, W.psi, W.t64, s);
+    }
     DW_CUDA(cudaMemcpyAsync(W.r64, W.eta, fb64, cudaMemcpyDeviceToDevice, s));
     blas_axpy<double>(W.t64, W.r64, -1.0, 0.0, n, s);
     blas_dot<double>(c, W.r64, W.r64, n, dres, s);
@@ -191,8 +205,10 @@ int solve_one(dw_ctx* c, dfl_ctx* d, const sol_params* p, const double* eta_cano
       int it = 0;
       double rr = 0;
       tm.begin(PH_PROJECT);
-      restrict_(d, W.r64, W.c64, s);
+      if (p->mixed) rc = dfl_restrict_f64x(d, W.r64, W.c64, s);
+      else restrict_(d, W.r64, W.c64, s);
       tm.end();
+      if (rc < 0) return rc;
       tm.begin(PH_LITTLE);
       rc = p->mixed ? little_solve_refined(d, W.c64, W.v64, p->little_tol_out, p->little_maxit, p->little_nkv, &it,
                                            &rr, s)
@@ -200,8 +216,10 @@ int solve_one(dw_ctx* c, dfl_ctx* d, const sol_params* p, const double* eta_cano
       tm.end();
       if (rc < 0) return rc;
       tm.begin(PH_PROJECT);
-      prolong_(d, W.v64, W.psi, 1, s);
+      if (p->mixed) rc = dfl_prolong_f64x(d, W.v64, W.psi, 1, s);
+      else prolong_(d, W.v64, W.psi, 1, s);
       tm.end();
+      if (rc < 0) return rc;
       if ((rc = residual64())) return rc;
       rn = sqrt(h[2]);
       inf.little_iterations += it;
@@ -348,9 +366,17 @@ int solve_batch_f32(dw_ctx* c, dfl_ctx* d, const sol_params* p, int nrhs, const 
   std::vector<double> lrr(nrhs);
   if ((rc = norms64(W.eta, en))) return rc;
   for (int r = 0; r < nrhs; ++r) conv[r] = en[r] == 0.0;
-  auto residual64 = [&]() -> int {
+  dd *dda = nullptr, *ddb = nullptr;
+  if ((rc = dw_make_dd(c, s)) || (rc = W.alloc(fs * sizeof(dd), (void**)&dda)) ||
+      (rc = W.alloc(fs * sizeof(dd), (void**)&ddb)))
+    return rc;
+  auto residual64 = [&]() -> int {   // restart residuals in double-float arithmetic
     tm.begin(PH_RESTART);
-    dirac_mrhs<double>(c, W.psi, W.t64, nrhs, c->tune_rgroup, s);
+    for (int r = 0; r < nrhs; ++r) {
+      f64_to_dd(F64(W.psi, r), dda, fs, s);
+      dirac_full_dd(c, dda, ddb, s);
+      dd_to_f64(ddb, F64(W.t64, r), fs, 0, s);
+    }
     for (int r = 0; r < nrhs; ++r) {
       DW_CUDA(cudaMemcpyAsync(F64(W.r64, r), F64(W.eta, r), fs * sizeof(double), cudaMemcpyDeviceToDevice, s));
       blas_axpy<double>(F64(W.t64, r), F64(W.r64, r), -1.0, 0.0, n, s);
@@ -372,7 +398,8 @@ int solve_batch_f32(dw_ctx* c, dfl_ctx* d, const sol_params* p, int nrhs, const 
     if (d) {
       // deflation correction accurate to the outer tolerance (FP32 little iterations, FP64 residuals)
       tm.begin(PH_PROJECT);
-      dfl_restrict_mrhs_f64(d, W.r64, W.c64, nrhs, s);
+      for (int r = 0; r < nrhs; ++r)
+        if (!conv[r] && (rc = dfl_restrict_f64x(d, F64(W.r64, r), W.c64 + (size_t)r * Nl * 2, s))) return rc;
       tm.end();
       tm.begin(PH_LITTLE);
       for (int r = 0; r < nrhs; ++r) {
@@ -391,7 +418,8 @@ int solve_batch_f32(dw_ctx* c, dfl_ctx* d, const sol_params* p, int nrhs, const 
       }
       tm.end();
       tm.begin(PH_PROJECT);
-      dfl_prolong_mrhs_f64(d, W.v64, W.psi, 1, nrhs, s);
+      for (int r = 0; r < nrhs; ++r)
+        if (!conv[r] && (rc = dfl_prolong_f64x(d, W.v64 + (size_t)r * Nl * 2, F64(W.psi, r), 1, s))) return rc;
       tm.end();
       if ((rc = residual64())) return rc;
     }

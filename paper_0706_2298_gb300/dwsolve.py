@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdwsolve.so")
 
 DW_OK, DW_EINVAL, DW_ENOMEM, DW_ECUDA, DW_ENOTCONV, DW_ILLCOND = 0, -1, -2, -3, 1, 2
-DW_F64, DW_F32, DW_BF16 = 0, 1, 2
+DW_F64, DW_F32, DW_BF16, DW_F64X = 0, 1, 2, 3
 DW_OP_FULL, DW_OP_SCHUR = 0, 1
 
 

@@ -76,8 +76,9 @@ def test_basis_bf16_rounding(case):
 
 
 @pytest.mark.parametrize("basis_prec,prec,tol", [(dw.DW_F64, dw.DW_F64, 1e-13), (dw.DW_BF16, dw.DW_F32, 1e-5),
-                                                 (dw.DW_BF16, dw.DW_F64, 1e-12)])
+                                                 (dw.DW_BF16, dw.DW_F64, 1e-12), (dw.DW_BF16, dw.DW_F64X, 1e-12)])
 def test_restrict_prolong(case, basis_prec, prec, tol):
+    """(4.1) against the oracle; DW_F64X: FP64 fields through double-float arithmetic."""
     L, sb, db, Ns, ctx, D, start = case
     d = _build(case, basis_prec)
     phi = block_gram_schmidt(Blocking(L, db), start.numpy())
@@ -85,8 +86,9 @@ def test_restrict_prolong(case, basis_prec, prec, tol):
         phi = round_bf16(phi)
     sub = BlockSubspace(D, db, phi)
     psi = synth.gaussian_source(L, 11).numpy()
-    x = to_packed(ctx, prec, psi)
-    dt = torch.float64 if prec == dw.DW_F64 else torch.float32
+    fprec = dw.DW_F64 if prec == dw.DW_F64X else prec      # DW_F64X uses FP64 fields
+    x = to_packed(ctx, fprec, psi)
+    dt = torch.float32 if prec == dw.DW_F32 else torch.float64
     c = torch.empty(d.Nb * d.Ns * 2, dtype=dt, device="cuda")
     dw.dfl_restrict(d, prec, x, c)
     torch.cuda.synchronize()
@@ -95,10 +97,10 @@ def test_restrict_prolong(case, basis_prec, prec, tol):
     assert rel(cg, c_or) <= tol
     cin = synth.complex_gaussian((d.Nb, d.Ns), 12).numpy()
     ct = torch.from_numpy(cin.view(np.float64).reshape(-1).copy()).to(dt).cuda()
-    y = ctx.empty_field(prec)
+    y = ctx.empty_field(fprec)
     dw.dfl_prolong(d, prec, ct, y)
-    assert rel(from_packed(ctx, prec, y), sub.prolong(cin.astype(np.complex64 if prec == dw.DW_F32 else np.complex128)
-                                                      .astype(np.complex128))) <= tol
+    assert rel(from_packed(ctx, fprec, y), sub.prolong(cin.astype(np.complex64 if prec == dw.DW_F32 else np.complex128)
+                                                       .astype(np.complex128))) <= tol
 
 
 def test_little_operator_assembly(case):

@@ -52,6 +52,16 @@ def test_dirac_full(case, prec, tol):
     assert rel(from_packed(ctx, prec, y), D.apply(psi)) <= tol
 
 
+def test_dirac_full_double_float(case):
+    """DW_F64X: FP64 fields, D computed in double-float arithmetic on the FP32 pipes."""
+    L, sb, ctx, D = case
+    psi = synth.gaussian_source(L, 6).numpy()
+    x = to_packed(ctx, dw.DW_F64, psi)
+    y = ctx.empty_field(dw.DW_F64)
+    dw.dw_apply(ctx, dw.DW_F64X, dw.DW_OP_FULL, 1, x, y)
+    assert rel(from_packed(ctx, dw.DW_F64, y), D.apply(psi)) <= 5e-14
+
+
 @pytest.mark.parametrize("prec,tol", [(dw.DW_F64, 1e-14), (dw.DW_F32, 5e-6)])
 def test_dirac_schur(case, prec, tol):
     L, sb, ctx, D = case
