@@ -3,11 +3,12 @@
 
 Workload (default "24^3x48"): 48 x 24^3 lattice, smeared random SU(3)
 field (U = exp(0.3 i X), 5 APE steps, alpha = 0.5), c_sw = 1, bare mass at
-the near-critical value fixed by the unpreconditioned CG count (> 2000
-iterations), one Gaussian source.  Solver: flexible GCR (restart 16) with
-FP64 restart residuals, right-preconditioned by M_sap (4^4 blocks, ncy = 4,
-nmr = 4, FP32), deflated by Ns = 20 block fields on 4^4 blocks stored in
-BF16 (11 inverse-iteration steps), little operator FP32 with FP64 assembly.
+the most nearly critical value found by the unpreconditioned CG count scan
+(workload_masses.json), one Gaussian source.  Solver: flexible GCR (restart
+16) with FP64-class restart steps (double-float arithmetic), right-
+preconditioned by M_sap (4^4 blocks, ncy = 4, nmr = 4, FP32), deflated by
+Ns = 20 block fields on 4^4 blocks stored in BF16 (11 inverse-iteration
+steps), little operator FP32 with FP64 assembly.
 One step = one solve from psi = 0 with eta and all operator data resident
 in HBM.  The same algorithm in plain FP64 is timed beside it.
 
@@ -45,6 +46,18 @@ MASS_FILE = os.path.join(ROOT, "paper_0706_2298_gb300", "workload_masses.json")
 # 48x24^3, Ns = 20: (84.87 + 4.76) MB over 42 iterations (cold cache: the first iteration reads
 # the little operator from HBM, the rest hit L2).  Remove an entry when the kernel changes.
 LITTLE_TRAFFIC = {("24^3x48", 20): 89.63e6 / 42}
+
+
+def aggregate_ranks(t_ms, steps, world, device="cpu"):
+    """Timed region of the slowest rank and the whole-job seconds per solve (every rank solved
+    `steps` systems of its own: all ranks' solves over the slowest rank's time)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(t_ms)], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    return t_ms, (t_ms / 1e3) / (steps * world)
 
 
 def load_masses():
@@ -245,15 +258,11 @@ def main():
     ev1.record()
     torch.cuda.synchronize()
     launches = dw.dw_launch_count() - n0
-    t_ms = ev0.elapsed_time(ev1)
+    t_ms, value = aggregate_ranks(ev0.elapsed_time(ev1), args.steps, world, device="cuda")
     if world > 1:
-        t = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
         dist.barrier()
     clk = clocks.stop()
     ms_per_step = t_ms / args.steps
-    value = (t_ms / 1e3) / (args.steps * world)
     iters = statistics.median([i.iterations for i in infos])
 
     # ---- rooflines from the library's CUDA-event phase timers over the timed solves
