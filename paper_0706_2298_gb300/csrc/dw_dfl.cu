@@ -57,6 +57,14 @@ struct dfl_ctx {
   std::vector<cd> Atil_inv;                            // Ns x Ns row-major
   double* Ainv64 = nullptr; float* Ainv32 = nullptr;   // device copies of A~^{-1}
   int coop_grid = 0;                                   // CTAs of the cooperative little solver (0: not possible)
+  bool coop_m = false;                                 // multi-RHS cooperative little solver available
+  float* mw = nullptr;                                 // its work: (2 COOP_NKV + 4) x COOP_MAXR vectors
+  float* mio = nullptr;                                // right-hand sides and solutions [2][COOP_MAXR][Ne Ns]
+  float* meo = nullptr;                                // odd-part work [2][COOP_MAXR][No Ns]
+  float* mpart = nullptr;                              // reduction partials [COOP_MNV][Gp]
+  float* mred = nullptr;                               // reduction results [COOP_MNV]
+  float* mtol = nullptr;                               // tolerances [COOP_MAXR]
+  double* mout = nullptr;                              // iterations, relative residuals [COOP_MAXR][2]
   int defer_slot = -1;                                 // >= 0: write results to coop_out[2*slot], no host sync
   double* ref64 = nullptr;                             // refinement work: 3 FP64 little vectors
   float* ref32 = nullptr;                              //                  2 FP32 little vectors
@@ -1201,6 +1209,493 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_kernel(CoopAr
   }
 }
 
+// ------------------------------------------------------------------ multi-RHS cooperative little GCR
+// Up to COOP_MAXR little systems (the same operator, several right-hand sides) solved in lockstep
+// by one persistent kernel (FP32): every GCR step of every right-hand side shares the grid
+// barriers and reductions, and each block row of the operator is read once per step for all of
+// them.  Each right-hand side keeps its own GCR scalars, tolerance and convergence flag; a
+// converged (or stalled) right-hand side is frozen while the others continue.  Vectors are stored
+// [kind][rhs][n].  Reductions with many values use two phases: CTA c adds the partials of the
+// values v = c, c + G, ... (fixed order), a second barrier publishes the sums.
+constexpr int COOP_MAXR = 12;
+constexpr int COOP_MNV = COOP_MAXR * (2 * 32 + 2 * COOP_NKV);   // values of the largest reduction
+
+struct CoopMArgs {
+  int Ne, No, nkv, maxit, a3, R;
+  const int *list_e, *list_o, *lnb_e, *lnb_o;
+  const float *M, *g, *Bg, *Ainv, *b;
+  const float* tol;   // [R] relative tolerances
+  float* v;           // [R][Ne Ns] complex
+  float* work;        // (2 nkv + 4) x R vectors of Ne Ns complex
+  float* partial;     // [COOP_MNV][Gp]
+  float* red;         // [COOP_MNV]
+  double* out;        // [R][2]: iterations, relative residual
+};
+
+struct CoopMShared {
+  float cta[COOP_MNV];
+  float res[COOP_MNV];
+  float ws[COOP_WARPS][3 * COOP_MAXR];
+  float z[COOP_MAXR][2 * 32];
+  float ainv[2 * 32 * 32];
+  float a[COOP_MAXR][2 * COOP_NKV], c[COOP_MAXR][COOP_NKV], beta[COOP_MAXR][2 * COOP_NKV];
+  float bn[COOP_MAXR], rn[COOP_MAXR];
+  int live[COOP_MAXR], kr[COOP_MAXR], its[COOP_MAXR];
+  int any;
+};
+
+// dynamic shared memory: bb [R][nkv][2 nkv], tg [R][nkv][2 NS], staged neighbour vectors
+// xs [2][8][R][NS] complex, direction partial sums hp [2][R][8][NS] complex
+constexpr int COOP_YS_CAP = 2048;     // complex numbers of the shared-memory mirror of chi_k (all RHS)
+__host__ __device__ inline size_t coop_m_dyn_bytes(int ns) {
+  return ((size_t)COOP_MAXR * COOP_NKV * 2 * COOP_NKV + (size_t)COOP_MAXR * COOP_NKV * 2 * ns +
+          (size_t)2 * 8 * COOP_MAXR * ns * 2 + (size_t)2 * COOP_MAXR * 8 * ns * 2 + (size_t)COOP_YS_CAP * 2) *
+         sizeof(float);
+}
+
+// sums of sh.cta[0..nv) over all CTAs into sh.res (all CTAs); two grid barriers
+DW_D void coop_mreduce(cg::grid_group& grid, CoopMShared& sh, int nv, float* partial, float* red) {
+  const int G = gridDim.x, Gp = coop_gpad(G);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  for (int v = threadIdx.x; v < nv; v += COOP_THREADS) partial[(size_t)v * Gp + blockIdx.x] = sh.cta[v];
+  grid.sync();
+  for (int v = blockIdx.x + w * G; v < nv; v += COOP_WARPS * G) {
+    float y0 = 0.f, y1 = 0.f;
+    int q = lane;
+    for (; q + 32 < G; q += 64) { y0 += __ldcg(partial + (size_t)v * Gp + q); y1 += __ldcg(partial + (size_t)v * Gp + q + 32); }
+    if (q < G) y0 += __ldcg(partial + (size_t)v * Gp + q);
+    const float y = warp_allsum(y0 + y1);
+    if (lane == 0) red[v] = y;
+  }
+  grid.sync();
+  for (int v = threadIdx.x; v < nv; v += COOP_THREADS) sh.res[v] = __ldcg(red + v);
+  __syncthreads();
+}
+
+// per-thread values x[j][r] (j < NVAL, r < R) -> CTA sums in sh.cta[r * stride + j]
+template <int NVAL>
+DW_D void cta_msum(CoopMShared& sh, const float (&x)[NVAL][COOP_MAXR], int R, int stride) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int r = 0; r < COOP_MAXR; ++r) {
+    if (r < R) {
+#pragma unroll
+      for (int j = 0; j < NVAL; ++j) {
+        const float y = warp_allsum(x[j][r]);
+        if (lane == 0) sh.ws[w][j * COOP_MAXR + r] = y;
+      }
+    }
+  }
+  __syncthreads();
+  for (int tt = threadIdx.x; tt < NVAL * R; tt += COOP_THREADS) {
+    const int j = tt / R, r = tt - j * R;
+    float y = 0.f;
+#pragma unroll
+    for (int q = 0; q < COOP_WARPS; ++q) y += sh.ws[q][j * COOP_MAXR + r];
+    sh.cta[r * stride + j] = y;
+  }
+}
+
+// (X_j, y) for j < nvec over the CTA's slice into sh.cta[off + 2j], four vectors per warp pass
+DW_D void cta_mdots(CoopMShared& sh, const cplx<float>* X, size_t xstride, int nvec, const cplx<float>* y,
+                    const CoopSlice& sl, int off) {
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int j0 = w; j0 < nvec; j0 += 4 * COOP_WARPS) {
+    const cplx<float>* xs[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int jj = j0 + u * COOP_WARPS;
+      xs[u] = X + (size_t)(jj < nvec ? jj : j0) * xstride;
+    }
+    float acc[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) acc[m] = 0.f;
+#pragma unroll 4
+    for (size_t i = sl.s0 + lane; i < sl.s1; i += 32) {
+      const cplx<float> q = y[i];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const cplx<float> p = xs[u][i];
+        acc[2 * u] += p.re * q.re + p.im * q.im;
+        acc[2 * u + 1] += p.re * q.im - p.im * q.re;
+      }
+    }
+    int base = 0;
+    WarpHalve<float, 8, 16>::run(acc, lane, base);
+    const int u = base >> 1, jj = j0 + u * COOP_WARPS;
+    if ((lane & 3) == 0 && jj < nvec) sh.cta[off + 2 * jj + (base & 1)] = acc[0];
+  }
+}
+
+// out[r] = base[r] + sign * sum_d M[list[row]][d] src[r][lnb[row][d]] for all R right-hand sides on
+// this CTA's block rows: the 8 x R neighbour vectors of a row are staged in shared memory (the next
+// row's by cp.async while the current one is multiplied), warp d multiplies block d (its columns
+// held in registers) into all R vectors, the direction sums meet in shared memory.
+template <int NS>
+DW_D void coop_mhop(int nrow, int R, size_t n, const int* list, const int* lnb, const float* M, const cplx<float>* src,
+                    const cplx<float>* base, cplx<float>* out, float sign, cplx<float>* xs, cplx<float>* hp,
+                    cplx<float>* ymir = nullptr) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const cplx<float>* Mc = reinterpret_cast<const cplx<float>*>(M);
+  const int Rw = (nrow + gridDim.x - 1) / gridDim.x;
+  const int rb = min(nrow, (int)blockIdx.x * Rw), re = min(nrow, rb + Rw);
+  const int nx = 8 * R * NS;                       // complex numbers staged per row
+  auto stage = [&](int row, cplx<float>* dst) {
+    for (int t = threadIdx.x; t < nx; t += COOP_THREADS) {
+      const int d = t / (R * NS), rem = t - d * R * NS, r = rem / NS, c = rem - r * NS;
+      const cplx<float>* sp = src + (size_t)r * n + (size_t)__ldg(lnb + row * 8 + d) * NS + c;
+      const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + t);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(sp) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  // the block's column entries for this warp's direction (lane = output row), one row ahead
+  auto loadM = [&](int row, cplx<float> (&m)[NS]) {
+    const cplx<float>* Mb = Mc + ((size_t)__ldg(list + row) * 8 + w) * NS * NS;
+#pragma unroll
+    for (int c = 0; c < NS; ++c) m[c] = lane < NS ? Mb[c * NS + lane] : cplx<float>{0.f, 0.f};
+  };
+  auto compute = [&](int row, const cplx<float> (&m)[NS]) {
+    const int q = row - rb;
+    cplx<float>* xcur = xs + (size_t)(q & 1) * nx;
+    cplx<float>* hcur = hp + (size_t)(q & 1) * R * 8 * NS;
+    if (row + 1 < re) {
+      stage(row + 1, xs + (size_t)((q + 1) & 1) * nx);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    __syncthreads();
+    if (lane < NS) {
+      for (int r = 0; r < R; ++r) {
+        const cplx<float>* x = xcur + (size_t)(w * R + r) * NS;
+        cplx<float> acc = {0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < NS; ++c) acc += m[c] * x[c];
+        hcur[(r * 8 + w) * NS + lane] = acc;
+      }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < R * NS; t += COOP_THREADS) {
+      const int r = t / NS, k = t - r * NS;
+      cplx<float> sum = hcur[(r * 8) * NS + k];
+#pragma unroll
+      for (int d = 1; d < 8; ++d) sum += hcur[(r * 8 + d) * NS + k];
+      const size_t o = (size_t)r * n + (size_t)row * NS + k;
+      const cplx<float> bse = base ? base[o] : cplx<float>{0.f, 0.f};
+      const cplx<float> val = bse + sign * sum;
+      out[o] = val;
+      if (ymir) ymir[(size_t)r * (re - rb) * NS + (size_t)(row - rb) * NS + k] = val;
+    }
+  };
+  if (rb < re) {
+    stage(rb, xs);
+    cplx<float> mA[NS], mB[NS];
+    loadM(rb, mA);
+    for (int row = rb; row < re; row += 2) {
+      if (row + 1 < re) loadM(row + 1, mB);
+      compute(row, mA);
+      if (row + 1 < re) {
+        if (row + 2 < re) loadM(row + 2, mA);
+        compute(row + 1, mB);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <int NS>
+__global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_mrhs_kernel(CoopMArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ CoopMShared sh;
+  extern __shared__ __align__(16) unsigned char coop_mdyn[];
+  const int R = a.R, nkv = a.nkv;
+  float* bbm = reinterpret_cast<float*>(coop_mdyn);                           // [R][nkv][2 nkv]
+  float* tgm = bbm + (size_t)COOP_MAXR * COOP_NKV * 2 * COOP_NKV;               // [R][nkv][2 NS]
+  cplx<float>* xs = reinterpret_cast<cplx<float>*>(tgm + (size_t)COOP_MAXR * COOP_NKV * 2 * NS);
+  cplx<float>* hp = xs + (size_t)2 * 8 * COOP_MAXR * NS;
+  cplx<float>* ysm = hp + (size_t)2 * COOP_MAXR * 8 * NS;                     // [R][S] mirror of chi_k
+  auto BB = [&](int r, int j, int k) -> float* { return bbm + ((size_t)(r * COOP_NKV + j) * COOP_NKV + k) * 2; };
+  auto TG = [&](int r, int j, int l) -> float* { return tgm + ((size_t)(r * COOP_NKV + j) * NS + l) * 2; };
+  const size_t n = (size_t)a.Ne * NS;
+  const CoopSlice sl = coop_rows_slice(a.Ne, NS);
+  const size_t S = sl.s1 - sl.s0;
+  cplx<float>* ys = (size_t)a.R * S <= COOP_YS_CAP ? ysm : nullptr;             // mirror if it fits
+  const int na = a.a3 ? 2 * NS : 0;
+  if (a.a3)
+    for (int t = threadIdx.x; t < NS * NS; t += COOP_THREADS) {
+      sh.ainv[2 * t] = a.Ainv[2 * t];
+      sh.ainv[2 * t + 1] = a.Ainv[2 * t + 1];
+    }
+  if (threadIdx.x < R) { sh.its[threadIdx.x] = 0; sh.kr[threadIdx.x] = 0; }
+  __syncthreads();
+  cplx<float>* W = reinterpret_cast<cplx<float>*>(a.work);
+  const size_t vs = (size_t)R * n;                                   // one vector kind for all RHS
+  cplx<float>* rho = W + (size_t)2 * nkv * vs;
+  cplx<float>* tmpo = rho + vs;
+  cplx<float>* t = tmpo + vs;
+  cplx<float>* rhsd = t + vs;
+  const cplx<float>* b = reinterpret_cast<const cplx<float>*>(a.b);
+  const cplx<float>* g = reinterpret_cast<const cplx<float>*>(a.g);
+  const cplx<float>* Bg = reinterpret_cast<const cplx<float>*>(a.Bg);
+  cplx<float>* v = reinterpret_cast<cplx<float>*>(a.v);
+  auto chi = [&](int k) { return W + (size_t)k * vs; };
+  auto xi = [&](int k) { return W + (size_t)(nkv + k) * vs; };
+  auto slice = [&](auto&& f) {
+#pragma unroll
+    for (int r = 0; r < COOP_MAXR; ++r)
+      if (r < R)
+        for (size_t i = sl.s0 + threadIdx.x; i < sl.s1; i += COOP_THREADS) f(r, (size_t)r * n + i);
+  };
+  // z_r = A~^{-1} u_r with u_r at sh.res[off_r(r)..] (threads r * NS + l)
+  auto zsolve = [&](int stride, int off) {
+    for (int tt = threadIdx.x; tt < R * NS; tt += COOP_THREADS) {
+      const int r = tt / NS, l = tt - r * NS;
+      float zr = 0.f, zi = 0.f;
+      for (int qq = 0; qq < NS; ++qq) {
+        const float mr = sh.ainv[2 * (l * NS + qq)], mi = sh.ainv[2 * (l * NS + qq) + 1];
+        const float yr = sh.res[r * stride + off + 2 * qq], yi = sh.res[r * stride + off + 2 * qq + 1];
+        zr += mr * yr - mi * yi;
+        zi += mr * yi + mi * yr;
+      }
+      sh.z[r][2 * l] = zr;
+      sh.z[r][2 * l + 1] = zi;
+    }
+  };
+  // u <- u - sg * sum_l z_l vecs_l on the slice, for all r (vecs shared by the RHS)
+  auto zupdate = [&](cplx<float>* u, const cplx<float>* vecs, float sg) {
+    slice([&](int r, size_t i) {
+      const size_t il = i - (size_t)r * n;
+      cplx<float> x = u[i];
+#pragma unroll
+      for (int l = 0; l < NS; ++l) x -= sg * (cplx<float>{sh.z[r][2 * l], sh.z[r][2 * l + 1]} * vecs[(size_t)l * n + il]);
+      u[i] = x;
+    });
+  };
+  // P~_L on all RHS of u (in place)
+  auto PL = [&](cplx<float>* u) {
+    for (int r = 0; r < R; ++r) cta_mdots(sh, g, n, NS, u + (size_t)r * n, sl, r * 2 * NS);
+    coop_mreduce(grid, sh, R * 2 * NS, a.partial, a.red);
+    zsolve(2 * NS, 0);
+    __syncthreads();
+    zupdate(u, Bg, 1.f);
+  };
+  float acc[3][COOP_MAXR];
+  auto zero = [&]() {
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int r = 0; r < COOP_MAXR; ++r) acc[j][r] = 0.f;
+  };
+  float (&acc1)[1][COOP_MAXR] = reinterpret_cast<float (&)[1][COOP_MAXR]>(acc);
+
+  // rhsd = P~_L b, rho = rhsd, v = 0, bn
+  slice([&](int r, size_t i) { rhsd[i] = b[i]; });
+  if (a.a3) PL(rhsd);
+  zero();
+  slice([&](int r, size_t i) {
+    const cplx<float> x = rhsd[i];
+    rho[i] = x;
+    v[i] = {0.f, 0.f};
+    acc[0][r] += x.re * x.re + x.im * x.im;
+  });
+  cta_msum<1>(sh, acc1, R, 1);
+  coop_mreduce(grid, sh, R, a.partial, a.red);
+  if (threadIdx.x < R) {
+    const int r = threadIdx.x;
+    sh.bn[r] = sqrtf(sh.res[r]);
+    sh.rn[r] = sh.bn[r];
+    sh.live[r] = sh.bn[r] > 0.f && a.maxit > 0;
+  }
+  __syncthreads();
+  auto any_live = [&]() {
+    int x = 0;
+    for (int r = 0; r < R; ++r) x |= sh.live[r];
+    return x;
+  };
+  while (any_live()) {
+    if (threadIdx.x < R) sh.kr[threadIdx.x] = 0;
+    __syncthreads();
+    for (int k = 0; k < nkv && any_live(); ++k) {
+      cplx<float>* ck = chi(k);
+      cplx<float>* xk = xi(k);
+      slice([&](int r, size_t i) { xk[i] = rho[i]; });
+      coop_mhop<NS>(a.No, R, n, a.list_o, a.lnb_o, a.M, rho, nullptr, tmpo, 1.f, xs, hp);
+      grid.sync();
+      coop_mhop<NS>(a.Ne, R, n, a.list_e, a.lnb_e, a.M, tmpo, rho, ck, -1.f, xs, hp, ys);
+      // one reduction per step for u = g^+ chi_k and (chi_j, chi_k), j < k (per RHS block of na + 2k)
+      const int st = na + 2 * k;
+      for (int r = 0; r < R; ++r) {
+        if (a.a3) cta_mdots(sh, g, n, NS, ck + (size_t)r * n, sl, r * st);
+        if (k > 0) cta_mdots(sh, W + (size_t)r * n, vs, k, ck + (size_t)r * n, sl, r * st + na);
+      }
+      if (st > 0) coop_mreduce(grid, sh, R * st, a.partial, a.red);
+      if (a.a3) zsolve(st, 0);
+      __syncthreads();
+      for (int tt = threadIdx.x; tt < R * k; tt += COOP_THREADS) {
+        const int r = tt / k, j = tt - r * k;
+        float br = sh.res[r * st + na + 2 * j], bi = sh.res[r * st + na + 2 * j + 1];
+        if (a.a3)
+          for (int l = 0; l < NS; ++l) {
+            const float zr = sh.z[r][2 * l], zi = sh.z[r][2 * l + 1], tr = TG(r, j, l)[0], ti = TG(r, j, l)[1];
+            br -= zr * tr - zi * ti;
+            bi -= zr * ti + zi * tr;
+          }
+        BB(r, j, k)[0] = br;
+        BB(r, j, k)[1] = bi;
+      }
+      __syncthreads();
+      zero();
+      // chi_k <- P~_L chi_k - sum_j b_jk chi_j per RHS; the B^g entries of a site are loaded once
+      for (size_t i = sl.s0 + threadIdx.x; i < sl.s1; i += COOP_THREADS) {
+        const size_t ii = i - sl.s0;
+        cplx<float> bgv[NS];
+        if (a.a3) {
+#pragma unroll
+          for (int l = 0; l < NS; ++l) bgv[l] = Bg[(size_t)l * n + i];
+        }
+#pragma unroll
+        for (int r = 0; r < COOP_MAXR; ++r) {
+          if (r < R) {
+            const size_t ir = (size_t)r * n + i;
+            cplx<float> y = ys ? ys[(size_t)r * S + ii] : ck[ir];
+            if (a.a3) {
+#pragma unroll
+              for (int l = 0; l < NS; ++l) y -= cplx<float>{sh.z[r][2 * l], sh.z[r][2 * l + 1]} * bgv[l];
+            }
+#pragma unroll
+            for (int j = 0; j < COOP_NKV; ++j)
+              if (j < k) y -= cplx<float>{BB(r, j, k)[0], BB(r, j, k)[1]} * chi(j)[ir];
+            ck[ir] = y;
+            if (ys) ys[(size_t)r * S + ii] = y;
+            const cplx<float> q = rho[ir];
+            acc[0][r] += y.re * q.re + y.im * q.im;
+            acc[1][r] += y.re * q.im - y.im * q.re;
+            acc[2][r] += y.re * y.re + y.im * y.im;
+          }
+        }
+      }
+      // reduction: per RHS (chi_k, rho), |chi_k|^2 and (B^ g_l, chi_k)
+      const int sb = 3 + na;
+      cta_msum<3>(sh, acc, R, sb);
+      if (a.a3)
+        for (int r = 0; r < R; ++r) cta_mdots(sh, Bg, n, NS, ck + (size_t)r * n, sl, r * sb + 3);
+      coop_mreduce(grid, sh, R * sb, a.partial, a.red);
+      // per RHS: normalise chi_k, update rho (live RHS only)
+      for (int r = 0; r < R; ++r) {
+        const float cn = sqrtf(sh.res[r * sb + 2]);
+        const bool ok = sh.live[r] && cn > 0.f;
+        const float inv = ok ? 1.f / cn : 0.f;
+        if (threadIdx.x == 0) {
+          sh.c[r][k] = ok ? cn : 1.f;
+          sh.a[r][2 * k] = ok ? sh.res[r * sb] * inv : 0.f;
+          sh.a[r][2 * k + 1] = ok ? sh.res[r * sb + 1] * inv : 0.f;
+        }
+        if (a.a3 && threadIdx.x < NS) {
+          TG(r, k, threadIdx.x)[0] = sh.res[r * sb + 3 + 2 * threadIdx.x] * inv;
+          TG(r, k, threadIdx.x)[1] = -sh.res[r * sb + 3 + 2 * threadIdx.x + 1] * inv;
+        }
+      }
+      __syncthreads();
+      zero();
+      slice([&](int r, size_t i) {
+        if (sh.live[r]) {
+          const float inv = 1.f / sh.c[r][k];
+          const cplx<float> x = inv * ck[i];
+          ck[i] = x;
+          const cplx<float> y = rho[i] - cplx<float>{sh.a[r][2 * k], sh.a[r][2 * k + 1]} * x;
+          rho[i] = y;
+          acc[0][r] += y.re * y.re + y.im * y.im;
+        }
+      });
+      cta_msum<1>(sh, acc1, R, 1);
+      coop_mreduce(grid, sh, R, a.partial, a.red);
+      if (threadIdx.x < R) {
+        const int r = threadIdx.x;
+        if (sh.live[r]) {
+          sh.rn[r] = sqrtf(sh.res[r]);
+          sh.its[r] += 1;
+          sh.kr[r] = k + 1;
+          if (!(sh.c[r][k] > 0.f) || sh.a[r][2 * k] != sh.a[r][2 * k] ||
+              (double)sh.rn[r] <= (double)a.tol[r] * (double)sh.bn[r] || sh.its[r] >= a.maxit)
+            sh.live[r] = 0;
+        }
+      }
+      __syncthreads();
+    }
+    // back substitution per RHS (warp r), v_r += sum_j beta_j xi_j
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int r = w; r < R; r += COOP_WARPS) {
+      const int kk = sh.kr[r];
+      float br = lane < kk ? sh.a[r][2 * lane] : 0.f, bi = lane < kk ? sh.a[r][2 * lane + 1] : 0.f;
+      for (int j = kk - 1; j >= 0; --j) {
+        const float cj = sh.c[r][j];
+        const float yr = __shfl_sync(0xffffffffu, br, j) / cj, yi = __shfl_sync(0xffffffffu, bi, j) / cj;
+        if (lane == j) { sh.beta[r][2 * j] = yr; sh.beta[r][2 * j + 1] = yi; }
+        if (lane < j) {
+          const float mr = BB(r, lane, j)[0], mi = BB(r, lane, j)[1];
+          br -= mr * yr - mi * yi;
+          bi -= mr * yi + mi * yr;
+        }
+      }
+    }
+    __syncthreads();
+    slice([&](int r, size_t i) {
+      cplx<float> x = v[i];
+      const int kk = sh.kr[r];
+#pragma unroll
+      for (int j = 0; j < COOP_NKV; ++j)
+        if (j < kk) x += cplx<float>{sh.beta[r][2 * j], sh.beta[r][2 * j + 1]} * xi(j)[i];
+      v[i] = x;
+    });
+    grid.sync();
+    // true residuals of the deflated systems; RHS still live after their last step continue
+    int again = 0;
+    for (int r = 0; r < R; ++r) again |= sh.live[r];
+    if (!again) break;
+    coop_mhop<NS>(a.No, R, n, a.list_o, a.lnb_o, a.M, v, nullptr, tmpo, 1.f, xs, hp);
+    grid.sync();
+    coop_mhop<NS>(a.Ne, R, n, a.list_e, a.lnb_e, a.M, tmpo, v, t, -1.f, xs, hp);
+    grid.sync();
+    if (a.a3) PL(t);
+    zero();
+    slice([&](int r, size_t i) {
+      const cplx<float> y = rhsd[i] - t[i];
+      rho[i] = y;
+      acc[0][r] += y.re * y.re + y.im * y.im;
+    });
+    cta_msum<1>(sh, acc1, R, 1);
+    coop_mreduce(grid, sh, R, a.partial, a.red);
+    if (threadIdx.x < R) {
+      const int r = threadIdx.x;
+      sh.rn[r] = sqrtf(sh.res[r]);
+      if (sh.live[r] && (double)sh.rn[r] <= (double)a.tol[r] * (double)sh.bn[r]) sh.live[r] = 0;
+    }
+    __syncthreads();
+  }
+  if (a.a3) {
+    // v = chi + g A~^{-1} g^+ (b - B^ chi) for every RHS
+    grid.sync();
+    coop_mhop<NS>(a.No, R, n, a.list_o, a.lnb_o, a.M, v, nullptr, tmpo, 1.f, xs, hp);
+    grid.sync();
+    coop_mhop<NS>(a.Ne, R, n, a.list_e, a.lnb_e, a.M, tmpo, v, t, -1.f, xs, hp);
+    grid.sync();
+    slice([&](int r, size_t i) { t[i] = b[i] - t[i]; });
+    for (int r = 0; r < R; ++r) cta_mdots(sh, g, n, NS, t + (size_t)r * n, sl, r * 2 * NS);
+    coop_mreduce(grid, sh, R * 2 * NS, a.partial, a.red);
+    zsolve(2 * NS, 0);
+    __syncthreads();
+    zupdate(v, g, -1.f);
+  }
+  if (blockIdx.x == 0 && threadIdx.x < R) {
+    const int r = threadIdx.x;
+    a.out[2 * r] = sh.its[r];
+    a.out[2 * r + 1] = sh.bn[r] > 0.f ? (double)sh.rn[r] / (double)sh.bn[r] : 0.0;
+  }
+}
+
 // ====================================================================== host side
 template <typename T>
 static const T* Mp(dfl_ctx* d);
@@ -1245,7 +1740,8 @@ extern "C" void dfl_destroy(dfl_ctx* d) {
   void* ptrs[] = {d->d_sub, d->d_sap2dfl, d->d_bnb, d->d_list[0], d->d_list[1], d->d_lnb[0], d->d_lnb[1],
                   d->basis64, d->basis16, d->B64, d->Binv64, d->Binv32, d->M64, d->M32, d->g64, d->g32,
                   d->Bg64, d->Bg32, d->lw[0], d->lw[1], d->B32, d->fw[0], d->fw[1], d->Ainv64, d->Ainv32,
-                  d->coop_partial, d->coop_out, d->ref64, d->ref32, d->ddf, d->ddl};
+                  d->coop_partial, d->coop_out, d->ref64, d->ref32, d->ddf, d->ddl, d->mw, d->mio,
+                  d->meo, d->mpart, d->mred, d->mtol, d->mout};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete d;
@@ -1748,13 +2244,103 @@ int little_solve_refined(dfl_ctx* d, const double* w, double* v, double tol, int
 
 // nrhs FP32 little solves queued back to back; one host synchronisation collects the counts.
 // Uses the cooperative solver when available (otherwise each solve synchronises on its own).
+template <int NS>
+static bool launch_little_mrhs(dfl_ctx* d, CoopMArgs& a, cudaStream_t s, cudaError_t* err) {
+  if constexpr (NS == 0) {
+    return false;
+  } else {
+    void* args[] = {&a};
+    *err = cudaLaunchCooperativeKernel((void*)little_gcr_coop_mrhs_kernel<NS>, d->coop_grid, COOP_THREADS, args,
+                                       coop_m_dyn_bytes(NS), s);
+    return true;
+  }
+}
+
+// The R (<= COOP_MAXR) even-odd reduced little systems of a batch in one multi-RHS cooperative
+// launch: the per-RHS even-odd preparation and reconstruction (A.2) around it as in little_solve_t.
+static int little_solve_mrhs(dfl_ctx* d, const float* w, float* v, const double* tol, const int* idx, int R,
+                             int maxit, int nkv, int* iters, double* relres, cudaStream_t s) {
+  const int Ns = d->Ns;
+  const size_t n_e = (size_t)d->Ne * Ns, n_o = (size_t)d->No * Ns, N2 = (size_t)d->N * 2;
+  float* bE = d->mio;                                   // [R][n_e] complex right-hand sides
+  float* vE = d->mio + (size_t)COOP_MAXR * n_e * 2;     // [R][n_e] complex solutions
+  float* wO = d->meo;                                   // [R][n_o] complex
+  float* yO = d->meo + (size_t)COOP_MAXR * n_o * 2;
+  unsigned ge = (unsigned)((n_e + 255) / 256), go = (unsigned)((n_o + 255) / 256);
+  for (int q = 0; q < R; ++q) {
+    const float* wr = w + (size_t)idx[q] * N2;
+    float* be = bE + (size_t)q * n_e * 2;
+    float* wo = wO + (size_t)q * n_o * 2;
+    float* yo = yO + (size_t)q * n_o * 2;
+    float* wt = vE + (size_t)q * n_e * 2;               // scratch until the solve overwrites it
+    little_gather_kernel<float, float><<<ge, 256, 0, s>>>(d->Ne, Ns, d->d_list[0], wr, be); dw_note_launch();
+    little_gather_kernel<float, float><<<go, 256, 0, s>>>(d->No, Ns, d->d_list[1], wr, wo); dw_note_launch();
+    NS_DISPATCH(Ns, (little_bdiag_kernel<float, NSV><<<warps_grid(d->No), 128, 0, s>>>(d->No, Ns, d->d_list[1],
+                                                                                d->Binv32, wo, yo)));
+    NS_DISPATCH(Ns, (little_bdiag_kernel<float, NSV><<<warps_grid(d->Ne), 128, 0, s>>>(d->Ne, Ns, d->d_list[0],
+                                                                                d->Binv32, be, wt)));
+    NS_DISPATCH(Ns, (little_hop_kernel<float, NSV><<<d->Ne, 256, 0, s>>>(d->Ne, Ns, d->d_list[0], d->d_lnb[0],
+                                                                         d->M32, yo, wt, be)));
+    dw_note_launch(); dw_note_launch(); dw_note_launch();
+  }
+  float htol[COOP_MAXR];
+  for (int q = 0; q < R; ++q) htol[q] = (float)tol[idx[q]];
+  DW_CUDA(cudaMemcpyAsync(d->mtol, htol, R * sizeof(float), cudaMemcpyHostToDevice, s));
+  CoopMArgs a;
+  a.Ne = d->Ne; a.No = d->No; a.nkv = nkv; a.maxit = maxit; a.a3 = d->a3 ? 1 : 0; a.R = R;
+  a.list_e = d->d_list[0]; a.list_o = d->d_list[1]; a.lnb_e = d->d_lnb[0]; a.lnb_o = d->d_lnb[1];
+  a.M = d->M32; a.g = d->a3 ? d->g32 : nullptr; a.Bg = d->a3 ? d->Bg32 : nullptr; a.Ainv = d->a3 ? d->Ainv32 : nullptr;
+  a.b = bE; a.tol = d->mtol; a.v = vE; a.work = d->mw; a.partial = d->mpart; a.red = d->mred; a.out = d->mout;
+  cudaError_t le = cudaSuccess;
+  bool launched = false;
+  NS_DISPATCH(Ns, (launched = launch_little_mrhs<NSV>(d, a, s, &le)));
+  if (!launched) { dw_set_error("multi-RHS little solver: unsupported Ns"); return DW_EINVAL; }
+  DW_CUDA(le);
+  dw_note_launch();
+  for (int q = 0; q < R; ++q) {
+    float* vr = v + (size_t)idx[q] * N2;
+    float* ve = vE + (size_t)q * n_e * 2;
+    float* wo = wO + (size_t)q * n_o * 2;
+    float* yo = yO + (size_t)q * n_o * 2;
+    NS_DISPATCH(Ns, (little_hop_kernel<float, NSV><<<d->No, 256, 0, s>>>(d->No, Ns, d->d_list[1], d->d_lnb[1],
+                                                                         d->M32, ve, yo, wo)));
+    dw_note_launch();
+    little_scatter_kernel<float, float><<<ge, 256, 0, s>>>(d->Ne, Ns, d->d_list[0], ve, vr); dw_note_launch();
+    little_scatter_kernel<float, float><<<go, 256, 0, s>>>(d->No, Ns, d->d_list[1], wo, vr); dw_note_launch();
+  }
+  double h[2 * COOP_MAXR];
+  int rc = sync_read(d->c, d->mout, 2 * R, h, s);
+  if (rc) return rc;
+  for (int q = 0; q < R; ++q) {
+    iters[idx[q]] = (int)h[2 * q];
+    relres[idx[q]] = h[2 * q + 1];
+  }
+  DW_CUDA(cudaGetLastError());
+  return DW_OK;
+}
+
+static bool mrhs_enabled() {
+  const char* e = getenv("DW_LITTLE_MRHS");
+  return !(e && e[0] == '0');
+}
+
 int little_solve_batch_f32(dfl_ctx* d, const float* w, float* v, const double* tol, const int* use, int maxit,
                            int nkv, int nrhs, int* iters, double* relres, cudaStream_t s) {
   const size_t N2 = (size_t)d->N * 2;
+  for (int r = 0; r < nrhs; ++r) { iters[r] = 0; relres[r] = 0; }
+  if (d->coop_m && !d->illcond && nkv <= COOP_NKV && coop_enabled() && mrhs_enabled()) {
+    std::vector<int> idx;
+    for (int r = 0; r < nrhs; ++r)
+      if (use[r]) idx.push_back(r);
+    for (size_t q0 = 0; q0 < idx.size(); q0 += COOP_MAXR) {
+      const int R = (int)std::min<size_t>(COOP_MAXR, idx.size() - q0);
+      int rc = little_solve_mrhs(d, w, v, tol, idx.data() + q0, R, maxit, nkv, iters, relres, s);
+      if (rc < 0) return rc;
+    }
+    return DW_OK;
+  }
   const bool coop = d->coop_grid > 0 && nkv <= COOP_NKV && coop_enabled() && !d->illcond && nrhs <= 64;
   for (int r = 0; r < nrhs; ++r) {
-    iters[r] = 0;
-    relres[r] = 0;
     if (!use[r]) continue;
     d->defer_slot = coop ? r : -1;
     int rc = little_solve_t<float>(d, w + r * N2, v + r * N2, tol[r], maxit, nkv, iters + r, relres + r, s);
@@ -1771,6 +2357,78 @@ int little_solve_batch_f32(dfl_ctx* d, const float* w, float* v, const double* t
   return DW_OK;
 }
 
+
+// little_solve_refined for nrhs systems at once: FP64 residuals per right-hand side, the FP32
+// correction solves of every refinement step batched (multi-RHS cooperative solver).
+int little_solve_refined_batch(dfl_ctx* d, const double* w, double* v, double tol, const int* use, int maxit,
+                               int nkv, int nrhs, int* iters, double* relres, cudaStream_t s) {
+  const size_t N = d->N, N2 = N * 2;
+  double* r64 = nullptr;
+  double* t64 = nullptr;
+  float* w32 = nullptr;
+  float* v32 = nullptr;
+  DW_CUDA(cudaMallocAsync(&r64, nrhs * N2 * sizeof(double), s));
+  DW_CUDA(cudaMallocAsync(&t64, nrhs * N2 * sizeof(double), s));
+  DW_CUDA(cudaMallocAsync(&w32, nrhs * N2 * sizeof(float), s));
+  DW_CUDA(cudaMallocAsync(&v32, nrhs * N2 * sizeof(float), s));
+  double* dres = d->c->d_red + 65536 + 2048;
+  std::vector<double> h(3 * nrhs), wn(nrhs, 0.0), rn(nrhs, 0.0), t32(nrhs, 1e-6);
+  std::vector<int> act(nrhs, 0), it(nrhs, 0);
+  std::vector<double> rr(nrhs, 0.0);
+  int rc = DW_OK;
+  auto norms = [&](const double* x) -> int {
+    for (int r = 0; r < nrhs; ++r) blas_dot<double>(d->c, x + r * N2, x + r * N2, N, dres + 3 * r, s);
+    return sync_read(d->c, dres, 3 * nrhs, h.data(), s);
+  };
+  for (int r = 0; r < nrhs; ++r) {
+    iters[r] = 0;
+    relres[r] = 0.0;
+    DW_CUDA(cudaMemsetAsync(v + r * N2, 0, N2 * sizeof(double), s));
+  }
+  DW_CUDA(cudaMemcpyAsync(r64, w, nrhs * N2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if ((rc = norms(w))) goto done;
+  for (int r = 0; r < nrhs; ++r) { wn[r] = sqrt(h[3 * r + 2]); rn[r] = wn[r]; }
+  for (int step = 0; step < 8; ++step) {
+    int any = 0;
+    for (int r = 0; r < nrhs; ++r) {
+      act[r] = use[r] && wn[r] > 0.0 && rn[r] > tol * wn[r] && iters[r] < maxit;
+      any |= act[r];
+      if (act[r]) blas_convert<double, float>(r64 + r * N2, w32 + r * N2, 1.0 / rn[r], N, s);
+    }
+    if (!any) break;
+    int mx = maxit;
+    for (int r = 0; r < nrhs; ++r)
+      if (act[r]) mx = std::min(mx, maxit - iters[r]);
+    if ((rc = little_solve_batch_f32(d, w32, v32, t32.data(), act.data(), std::max(mx, 1), nkv, nrhs, it.data(),
+                                     rr.data(), s)) < 0)
+      goto done;
+    rc = DW_OK;
+    for (int r = 0; r < nrhs; ++r) {
+      if (!act[r]) continue;
+      iters[r] += it[r];
+      blas_convert<float, double>(v32 + r * N2, t64 + r * N2, rn[r], N, s);
+      blas_axpy<double>(t64 + r * N2, v + r * N2, 1.0, 0.0, N, s);
+      NS_DISPATCH(d->Ns, (little_full_t_kernel<double, NSV><<<warps_grid(d->Nb), 128, 0, s>>>(
+                              d->Nb, d->Ns, d->d_bnb, d->B64, v + r * N2, t64 + r * N2)));
+      dw_note_launch();
+      DW_CUDA(cudaMemcpyAsync(r64 + r * N2, w + r * N2, N2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      blas_axpy<double>(t64 + r * N2, r64 + r * N2, -1.0, 0.0, N, s);
+    }
+    if ((rc = norms(r64))) goto done;
+    for (int r = 0; r < nrhs; ++r)
+      if (act[r]) rn[r] = sqrt(h[3 * r + 2]);
+  }
+  for (int r = 0; r < nrhs; ++r) {
+    relres[r] = wn[r] > 0.0 ? rn[r] / wn[r] : 0.0;
+    if (use[r] && rn[r] > tol * wn[r]) rc = DW_ENOTCONV;
+  }
+done:
+  cudaFreeAsync(r64, s);
+  cudaFreeAsync(t64, s);
+  cudaFreeAsync(w32, s);
+  cudaFreeAsync(v32, s);
+  return rc;
+}
 
 extern "C" int little_dirac_solve(dfl_ctx* d, int prec, const void* w, void* v, double tol, int maxit, int* iters,
                                   double* relres, void* stream) {
@@ -2088,6 +2746,26 @@ static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_c
     if (d->coop_grid) {
       DW_CUDA(cudaMalloc(&d->coop_partial, (size_t)2 * coop_gpad(d->coop_grid) * COOP_NV * sizeof(double)));
       DW_CUDA(cudaMalloc(&d->coop_out, 2 * 64 * sizeof(double)));
+      // multi-RHS solver (batches of right-hand sides): Ns with a compiled kernel, all CTAs resident
+      int bm = 0;
+      const size_t dsmm = coop_m_dyn_bytes(Ns);
+      NS_DISPATCH(Ns, if constexpr (NSV > 0) {
+        if (cudaFuncSetAttribute(little_gcr_coop_mrhs_kernel<NSV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)dsmm) == cudaSuccess)
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bm, little_gcr_coop_mrhs_kernel<NSV>, COOP_THREADS, dsmm);
+      });
+      cudaGetLastError();
+      if (bm > 0) {
+        const size_t ne = (size_t)d->Ne * Ns, no = (size_t)d->No * Ns;
+        DW_CUDA(cudaMalloc(&d->mw, ((size_t)2 * COOP_NKV + 4) * COOP_MAXR * ne * 2 * sizeof(float)));
+        DW_CUDA(cudaMalloc(&d->mio, (size_t)2 * COOP_MAXR * ne * 2 * sizeof(float)));
+        DW_CUDA(cudaMalloc(&d->meo, (size_t)2 * COOP_MAXR * no * 2 * sizeof(float)));
+        DW_CUDA(cudaMalloc(&d->mpart, (size_t)COOP_MNV * coop_gpad(d->coop_grid) * sizeof(float)));
+        DW_CUDA(cudaMalloc(&d->mred, (size_t)COOP_MNV * sizeof(float)));
+        DW_CUDA(cudaMalloc(&d->mtol, COOP_MAXR * sizeof(float)));
+        DW_CUDA(cudaMalloc(&d->mout, 2 * COOP_MAXR * sizeof(double)));
+        d->coop_m = true;
+      }
     }
     if ((rc = ensure_little_work(d, DW_F64, COOP_NKV))) return rc;
   }

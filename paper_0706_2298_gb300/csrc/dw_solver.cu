@@ -40,6 +40,8 @@ int little_solve_batch_f32(dfl_ctx*, const float*, float*, const double*, const 
                            cudaStream_t);
 int little_solve_refined(dfl_ctx*, const double*, double*, double, int, int, int*, double*, cudaStream_t);
 int dfl_restrict_f64x(dfl_ctx*, const double*, double*, cudaStream_t);
+int little_solve_refined_batch(dfl_ctx*, const double*, double*, double, const int*, int, int, int, int*, double*,
+                               cudaStream_t);
 int dfl_prolong_f64x(dfl_ctx*, const double*, double*, int, cudaStream_t);
 int dfl_restrict_mrhs_f64(dfl_ctx*, const double*, double*, int, cudaStream_t);
 int dfl_prolong_mrhs_f64(dfl_ctx*, const double*, double*, int, int, cudaStream_t);
@@ -402,19 +404,15 @@ int solve_batch_f32(dw_ctx* c, dfl_ctx* d, const sol_params* p, int nrhs, const 
         if (!conv[r] && (rc = dfl_restrict_f64x(d, F64(W.r64, r), W.c64 + (size_t)r * Nl * 2, s))) return rc;
       tm.end();
       tm.begin(PH_LITTLE);
-      for (int r = 0; r < nrhs; ++r) {
-        double* vr = W.v64 + (size_t)r * Nl * 2;
-        if (conv[r]) {
-          DW_CUDA(cudaMemsetAsync(vr, 0, (size_t)Nl * 2 * sizeof(double), s));
-          continue;
-        }
-        int it = 0;
-        double rr = 0;
-        rc = little_solve_refined(d, W.c64 + (size_t)r * Nl * 2, vr, p->little_tol_out, p->little_maxit,
-                                  p->little_nkv, &it, &rr, s);
+      {
+        std::vector<int> use(nrhs), lit(nrhs);
+        std::vector<double> lrr2(nrhs);
+        for (int r = 0; r < nrhs; ++r) use[r] = !conv[r];
+        rc = little_solve_refined_batch(d, W.c64, W.v64, p->little_tol_out, use.data(), p->little_maxit,
+                                        p->little_nkv, nrhs, lit.data(), lrr2.data(), s);
         if (rc < 0) return rc;
-        litot[r] += it;
-        lsolves[r] += 1;
+        for (int r = 0; r < nrhs; ++r)
+          if (use[r]) { litot[r] += lit[r]; lsolves[r] += 1; }
       }
       tm.end();
       tm.begin(PH_PROJECT);
