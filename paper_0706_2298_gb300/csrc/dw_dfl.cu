@@ -1826,12 +1826,6 @@ int dfl_restrict_mrhs_f32(dfl_ctx* d, const float* psi, float* c, int nrhs, cuda
 int dfl_prolong_mrhs_f32(dfl_ctx* d, const float* c, float* psi, int mode, int nrhs, cudaStream_t s) {
   return prolong_t(d, c, psi, mode, s, nrhs);
 }
-int dfl_restrict_mrhs_f64(dfl_ctx* d, const double* psi, double* c, int nrhs, cudaStream_t s) {
-  return restrict_t(d, psi, c, s, nrhs);
-}
-int dfl_prolong_mrhs_f64(dfl_ctx* d, const double* c, double* psi, int mode, int nrhs, cudaStream_t s) {
-  return prolong_t(d, c, psi, mode, s, nrhs);
-}
 int dfl_restrict_f32(dfl_ctx* d, const float* psi, float* c, cudaStream_t s) { return restrict_t(d, psi, c, s); }
 int dfl_restrict_f64(dfl_ctx* d, const double* psi, double* c, cudaStream_t s) { return restrict_t(d, psi, c, s); }
 int dfl_prolong_f32(dfl_ctx* d, const float* c, float* psi, int mode, cudaStream_t s) {

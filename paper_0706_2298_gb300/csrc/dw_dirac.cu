@@ -10,6 +10,7 @@
 #include "dw_common.cuh"
 
 #include <cstdio>
+#include <cstdlib>
 #include <mutex>
 
 template <typename T>
@@ -162,9 +163,139 @@ void dirac_full(dw_ctx* c, const T* in, T* out, cudaStream_t st) {
 template void dirac_full<float>(dw_ctx*, const float*, float*, cudaStream_t);
 template void dirac_full<double>(dw_ctx*, const double*, double*, cudaStream_t);
 
+// D on double-float fields with two threads per site (warps 2m and 2m+1 take the same 32
+// sites): thread half q forms the spin-q component of every half-spinor projection, multiplies it
+// by the link and adds it to spin q and to the lower spin it feeds; the two halves exchange their
+// lower-spin partial sums through shared memory, and each applies rows 3q..3q+2 of both chiral
+// clover blocks.  Half the arithmetic and registers per thread of dirac_full_kernel<dd>.
+template <int MU, bool DAG>
+DW_D void dd_half_hop(const dd* __restrict__ links, const dd* __restrict__ in, size_t V, long long j,
+                      long long lk, int q, dd sg, cplx<dd>* au, cplx<dd>* al2, cplx<dd>* al3) {
+  // lower spin feeding / fed by component q: 2 + q for mu = 0, 3; 3 - q for mu = 1, 2
+  const int lo = (MU == 0 || MU == 3) ? 2 + q : 3 - q;
+  SU3<dd> U;
+  load_link(links, V, MU, lk, U);
+  cplx<dd> pu[3], pl[3];
+  const float4* P = reinterpret_cast<const float4*>(in);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    unpack_unit(__ldg(P + (size_t)(3 * q + c) * V + j), pu + c);
+    unpack_unit(__ldg(P + (size_t)(3 * lo + c) * V + j), pl + c);
+  }
+  // v_q = e_mu-part of the lower spins: mu 0: -psi_lo; 1: -i psi_lo; 2: (q ? +1 : -1) psi_lo;
+  // 3: (q ? +i : -i) psi_lo.  h = psi_q + S v_q with S = -1 forward (DAG = false), +1 backward.
+  const dd S = DAG ? dd(1) : dd(-1);
+  cplx<dd> h[3], w[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    cplx<dd> v;
+    if (MU == 0) v = -pl[c];
+    else if (MU == 1) v = -ti(pl[c]);
+    else if (MU == 2) v = q ? pl[c] : -pl[c];
+    else v = q ? ti(pl[c]) : -ti(pl[c]);
+    h[c] = pu[c] + S * v;
+  }
+  if (DAG) su3_dag_mul(U, h, w); else su3_mul(U, h, w);
+  // the lower-spin image of w_q: mu 0: -w; 1: i w; 2: (q ? +w : -w); 3: (q ? -i w : i w)
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    au[c] += sg * w[c];
+    cplx<dd> l;
+    if (MU == 0) l = -w[c];
+    else if (MU == 1) l = ti(w[c]);
+    else if (MU == 2) l = q ? w[c] : -w[c];
+    else l = q ? -ti(w[c]) : ti(w[c]);
+    const cplx<dd> add = (S * sg) * l;
+    if (lo == 2) al2[c] += add; else al3[c] += add;
+  }
+}
+
+// rows r0..r0+2 of one packed Hermitian 6x6 chiral block times x (6 components)
+template <int R0>
+DW_D void herm6_rows(const cplx<dd>* s, const cplx<dd>* x, cplx<dd>* y) {
+  const dd d[6] = {s[0].re, s[0].im, s[1].re, s[1].im, s[2].re, s[2].im};
+#pragma unroll
+  for (int r = 0; r < 3; ++r) y[r] = d[R0 + r] * x[R0 + r];
+  int k = 3;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+#pragma unroll
+    for (int j = i + 1; j < 6; ++j) {
+      if (i >= R0 && i < R0 + 3) y[i - R0] += s[k] * x[j];
+      if (j >= R0 && j < R0 + 3) y[j - R0] += cmulc(s[k], x[i]);
+      ++k;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(128) dirac_dd_split_kernel(Geom g, const dd* __restrict__ links,
+                                                             const dd* __restrict__ clov, const dd* __restrict__ in,
+                                                             dd* __restrict__ out) {
+  __shared__ cplx<dd> xch[2][3][64];          // lower-spin partials handed to the other half
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int q = w & 1, grp = w >> 1;           // warp-uniform half
+  const int sl = grp * 32 + lane;              // site slot in the CTA (0..63)
+  const long long i = (long long)blockIdx.x * 64 + sl;
+  const bool valid = i < g.V;
+  const size_t V = g.V;
+  cplx<dd> au[3], a2[3], a3[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) { au[c] = {dd(0), dd(0)}; a2[c] = au[c]; a3[c] = au[c]; }
+  if (valid) {
+    const SiteRef s = decode(g, i);
+    bool cr;
+#define DD_DIR(MU)                                                                        \
+    {                                                                                     \
+      long long j = neighbour(g, s, 2 * MU, &cr);                                         \
+      dd sg = time_wrap(g, s, 2 * MU) ? dd(-1) : dd(1);                                   \
+      dd_half_hop<MU, false>(links, in, V, j, i, q, sg, au, a2, a3);                      \
+      j = neighbour(g, s, 2 * MU + 1, &cr);                                               \
+      sg = time_wrap(g, s, 2 * MU + 1) ? dd(-1) : dd(1);                                  \
+      dd_half_hop<MU, true>(links, in, V, j, j, q, sg, au, a2, a3);                       \
+    }
+    DD_DIR(0) DD_DIR(1) DD_DIR(2) DD_DIR(3)
+#undef DD_DIR
+  }
+  // half q keeps lower spin 2 + q: hand the other lower spin to the partner half
+#pragma unroll
+  for (int c = 0; c < 3; ++c) xch[q][c][sl] = q ? a2[c] : a3[c];
+  __syncthreads();
+  if (!valid) return;
+  cplx<dd> al[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) al[c] = (q ? a3[c] : a2[c]) + xch[1 - q][c][sl];
+  // clover: rows 3q..3q+2 of both chiral blocks (block 0: spins 0, 1; block 1: spins 2, 3)
+  cplx<dd> x[6], sblk[18], y0[3], y1[3];
+  const float4* P = reinterpret_cast<const float4*>(in);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) unpack_unit(__ldg(P + (size_t)k * V + i), x + k);
+  load_site<dd, 18>(clov, V, i, sblk);
+  if (q) herm6_rows<3>(sblk, x, y0); else herm6_rows<0>(sblk, x, y0);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) unpack_unit(__ldg(P + (size_t)(6 + k) * V + i), x + k);
+  load_site<dd, 18>(clov + 36 * V, V, i, sblk);
+  if (q) herm6_rows<3>(sblk, x, y1); else herm6_rows<0>(sblk, x, y1);
+  // out spin q (block 0 rows 3q..) and spin 2 + q (block 1 rows 3q..)
+  float4* O = reinterpret_cast<float4*>(out);
+  const dd hf = dd(0.5f);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const cplx<dd> u = y0[c] - hf * au[c];
+    const cplx<dd> l = y1[c] - hf * al[c];
+    O[(size_t)(3 * q + c) * V + i] = pack_unit(&u);
+    O[(size_t)(3 * (2 + q) + c) * V + i] = pack_unit(&l);
+  }
+}
+
 void dirac_full_dd(dw_ctx* c, const dd* in, dd* out, cudaStream_t st) {
-  unsigned blocks = (unsigned)((c->V + 127) / 128);
-  dirac_full_kernel<dd><<<blocks, 128, 0, st>>>(c->g, (const dd*)c->links_dd, (const dd*)c->clov_dd, in, out);
+  const char* e = getenv("DW_DD_SPLIT");
+  if (e && e[0] == '0') {
+    unsigned blocks = (unsigned)((c->V + 127) / 128);
+    dirac_full_kernel<dd><<<blocks, 128, 0, st>>>(c->g, (const dd*)c->links_dd, (const dd*)c->clov_dd, in, out);
+  } else {
+    unsigned blocks = (unsigned)((c->V + 63) / 64);
+    dirac_dd_split_kernel<<<blocks, 128, 0, st>>>(c->g, (const dd*)c->links_dd, (const dd*)c->clov_dd, in, out);
+  }
   dw_note_launch();
 }
 

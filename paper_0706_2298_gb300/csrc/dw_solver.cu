@@ -43,8 +43,6 @@ int dfl_restrict_f64x(dfl_ctx*, const double*, double*, cudaStream_t);
 int little_solve_refined_batch(dfl_ctx*, const double*, double*, double, const int*, int, int, int, int*, double*,
                                cudaStream_t);
 int dfl_prolong_f64x(dfl_ctx*, const double*, double*, int, cudaStream_t);
-int dfl_restrict_mrhs_f64(dfl_ctx*, const double*, double*, int, cudaStream_t);
-int dfl_prolong_mrhs_f64(dfl_ctx*, const double*, double*, int, int, cudaStream_t);
 
 namespace {
 
