@@ -194,7 +194,8 @@ typedef struct {
   int nkv;                 /* Krylov vectors per GCR cycle (restart length) */
   int nmx;                 /* maximum total GCR steps */
   int ncy, nmr;            /* M_sap parameters */
-  int mixed;               /* 1: FP32 D/SAP/little + FP64 restarts; 0: everything FP64 */
+  int mixed;               /* 1: FP32 D/SAP/little, FP64-class restarts (double-float D, restriction
+                              and prolongation, FP64-refined little solves); 0: everything FP64 */
   double inner_rtol;       /* mixed: end a cycle when its residual drops by this factor */
   double little_tol_out;   /* little-solve tolerance outside cycles (A.5), e.g. 1e-12 */
   double little_tol_in;    /* inside cycles, scaled by ||rho_0|| / ||D xi_k|| (A.5), e.g. 1e-6 */
@@ -216,6 +217,9 @@ typedef struct {
 /* Solve D psi = eta (3.9) for nrhs right-hand sides: FGCR (Section 6.2)
  * right-preconditioned by M_sap, deflated by d (Sections 3.2, 6.1) with
  * adapted little-solve precision (A.5); d = NULL gives SAP+GCR.
+ * Mixed precision with nrhs > 1 runs the right-hand sides in lockstep (one batch through every
+ * kernel, M_sap from captured CUDA graphs, the little solves of each step in one multi-RHS
+ * launch of up to 12 systems); environment DW_BATCH=0 solves them one after the other.
  * eta, psi: canonical complex128[nrhs][V][4][3] on the device.
  * info: nrhs entries (may be NULL).  Synchronous. */
 int gcr_solve(dw_ctx* ctx, dfl_ctx* d, const sol_params* p, int nrhs, const double* eta_dev,
