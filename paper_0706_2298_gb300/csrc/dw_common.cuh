@@ -341,7 +341,8 @@ template <typename T> constexpr int prec_of() { return sizeof(T) == 8 ? DW_F64 :
 inline size_t real_size(int prec) { return prec == DW_F64 ? 8 : 4; }
 
 // launch helpers implemented in dw_blas.cu -------------------------------------
-// All reductions accumulate in FP64 and are deterministic (fixed order).
+// Reductions: per-thread partial sums in the field precision, combined in FP64 in a fixed order
+// (deterministic).
 template <typename T> int blas_dot(dw_ctx* c, const T* a, const T* b, size_t n_cplx, double* out2, cudaStream_t s);
 template <typename T> int blas_multi_dot(dw_ctx* c, const T* const* vs, int k, const T* b, size_t n_cplx,
                                          double* out2, cudaStream_t s);
