@@ -25,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -36,8 +37,9 @@ WORKLOADS = {
     "8^4": dict(L=(8, 8, 8, 8), m0=-0.2, csw=1.0, sap_bs=(4, 4, 4, 4), dfl_bs=(4, 4, 4, 4), Ns=8,
                 n_inv=11, ncy=4, nmr=4, nkv=16, tol=1e-10, gauge_seed=1, source_seed=2, start_seed=3),
 }
-# Mass of the 24^3x48 workload: near-critical value chosen with cgnr_solve so that the
-# unpreconditioned CG needs more than 2000 iterations (record in the design doc).
+# Mass of the 24^3x48 workload: the most nearly critical value of a CGNR iteration-count scan
+# (workload_masses.json, written by tune_mass.py; the 2000-iteration rule is out of reach for
+# these smeared fields, the count peaks at m0 = 0).
 MASS_FILE = os.path.join(ROOT, "paper_0706_2298_gb300", "workload_masses.json")
 
 
@@ -245,8 +247,7 @@ def main():
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    clocks = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_r{rank}.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_r{rank}.csv")
+    clocks = Clocks(os.path.join(os.environ.get("DW_CLOCKS_DIR", tempfile.gettempdir()), f"clocks_r{rank}.csv"))
     clocks.start()
     n0 = dw.dw_launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
