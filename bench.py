@@ -393,7 +393,7 @@ def main():
         line = {"metric": "s/solve to rel. residual 1e-10 (DFL+SAP+GCR, mixed precision) vs plain FP64 path",
                 "value": value, "unit": "s/solve", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32+bf16 (FP64 restarts)", "data": "synthetic",
+                "dtype": "f32+bf16 (double-float restarts)", "data": "synthetic",
                 "config": {"workload": args.workload, "L": list(L), "m0": wl["m0"], "csw": wl["csw"],
                            "sap_bs": list(wl["sap_bs"]), "dfl_bs": list(wl["dfl_bs"]), "Ns": wl["Ns"],
                            "n_inv": wl["n_inv"], "nkv": wl["nkv"], "ncy": wl["ncy"], "nmr": wl["nmr"],
