@@ -6,7 +6,14 @@
 //   (3.2), A.1   B_{LL'} = (phi^L_k, D phi^{L'}_l)  (L' = L or one of 8 neighbours)
 //   A.2          even-odd little operator  B^ = 1 - B_ee^{-1} B_eo B_oo^{-1} B_oe
 //   A.3          global-mode deflation of the little system
-//   A.4          GCR on the deflated even-odd little system
+//   A.4          GCR on the deflated even-odd little system: one persistent cooperative kernel
+//                per solve (FP32 or FP64), and a multi-RHS variant that solves up to 12
+//                systems in lockstep (FP32, batched right-hand sides)
+//   A.5          FP64-accurate restart solves by iterative refinement (FP32 solves, FP64
+//                residuals), single and batched
+//
+// Restriction and prolongation run in FP32, FP64 or double-float arithmetic (FP64 fields on the
+// FP32 pipes, for the restart steps of the mixed solver).
 //
 // Basis storage: Ns global fields (field l = sum_L phi^L_l) in the packed
 // layout; FP64 for the plain path, BF16 (3 x 16-byte units of 4 complex per

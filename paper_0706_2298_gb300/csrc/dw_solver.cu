@@ -4,9 +4,10 @@
 // (6.2), GCR with restarts and inexact preconditioning (Section 6.2),
 // adapted little-solve precision and high-precision restart residuals (A.5).
 //
-// Every restart:
-//   rho = eta - D psi                            FP64
-//   c = A^{-1} Phi^+ rho  (FP64 little solve, little_tol_out); psi += Phi c; rho = eta - D psi
+// Every restart (mixed precision: D, Phi^+ and Phi in double-float arithmetic on FP64 fields, the
+// little system by FP32 solves refined with FP64 residuals; plain: everything FP64):
+//   rho = eta - D psi                            (rho = eta at the first restart, psi = 0)
+//   c = A^{-1} Phi^+ rho  (little_tol_out); psi += Phi c; rho = eta - D psi
 //   stop if ||rho|| <= tol ||eta||
 //   one GCR cycle in the inner precision on  P_L D M_sap phi = rho / ||rho||:
 //       xi_k = M_sap rho_k,  w = D xi_k,  chi_k = P_L w = w - D Phi A^{-1} Phi^+ w
@@ -15,6 +16,8 @@
 //   psi += ||rho|| * sum_k beta_k xi_k           FP64 accumulation
 // The -Phi A^{-1} Phi^+ D zeta part of P_R zeta is supplied by the next
 // restart's deflation correction, so psi ends as psi + P_R zeta + Phi A^{-1} Phi^+ rho.
+// Several right-hand sides in mixed precision run the same algorithm in lockstep
+// (solve_batch_f32): one batch through every kernel, converged right-hand sides frozen.
 #include <chrono>
 #include <cmath>
 #include <complex>
