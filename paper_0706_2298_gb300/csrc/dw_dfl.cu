@@ -659,6 +659,16 @@ __global__ void little_bdiag_kernel(int n, int Ns, const int* __restrict__ list,
     default: { constexpr int NSV = 0; CALL; } break;              \
   }
 
+// the same for the largest kernels (FP64 cooperative solver, double-float restriction, multi-RHS
+// solver): specialised for Ns = 8 and the paper's Ns = 20 only, the generic kernel otherwise,
+// which keeps the library's compile time down
+#define NS_DISPATCH_FEW(NSRT, CALL)                               \
+  switch (NSRT) {                                                 \
+    case 8: { constexpr int NSV = 8; CALL; } break;               \
+    case 20: { constexpr int NSV = 20; CALL; } break;             \
+    default: { constexpr int NSV = 0; CALL; } break;              \
+  }
+
 // gather a parity part of a full little vector ([Nb][Ns]) into compact order / scatter back
 template <typename Tin, typename Tout>
 __global__ void little_gather_kernel(int n, int Ns, const int* __restrict__ list, const Tin* __restrict__ full,
@@ -1806,7 +1816,7 @@ int dfl_restrict_f64x(dfl_ctx* d, const double* psi, double* c, cudaStream_t s) 
   if (rc) return rc;
   f64_to_dd(psi, d->ddf, (size_t)d->c->V * 24, s);
   bool done = false;
-  NS_DISPATCH(d->Ns, (done = launch_restrict_dd<NSV>(d, d->ddf, d->ddl, s)));
+  NS_DISPATCH_FEW(d->Ns, (done = launch_restrict_dd<NSV>(d, d->ddf, d->ddl, s)));
   if (!done)
     restrict_kernel<dd><<<d->Nb, 128, 0, s>>>(d->c->g, d->d_sub, d->nsub, d->Ns, d->basis16 ? nullptr : d->basis64,
                                               d->basis16, d->ddf, d->ddl, 1, (size_t)d->c->V * 24, (size_t)d->N * 2);
@@ -2052,8 +2062,13 @@ static int little_gcr_coop(dfl_ctx* d, const T* b, T* v, double tol, int maxit, 
   void* args[] = {&a};
   cudaError_t le = cudaSuccess;
   const size_t dsm = coop_dyn_smem<T>(d->coop_grid);
-  NS_DISPATCH(d->Ns, (le = cudaLaunchCooperativeKernel((void*)little_gcr_coop_kernel<T, NSV>, d->coop_grid,
+  if constexpr (sizeof(T) == 8) {
+    NS_DISPATCH_FEW(d->Ns, (le = cudaLaunchCooperativeKernel((void*)little_gcr_coop_kernel<T, NSV>, d->coop_grid,
                                                        COOP_THREADS, args, dsm, s)));
+  } else {
+    NS_DISPATCH(d->Ns, (le = cudaLaunchCooperativeKernel((void*)little_gcr_coop_kernel<T, NSV>, d->coop_grid,
+                                                       COOP_THREADS, args, dsm, s)));
+  }
   DW_CUDA(le);
   dw_note_launch();
   if (d->defer_slot >= 0) {   // results collected later by little_collect
@@ -2294,7 +2309,7 @@ static int little_solve_mrhs(dfl_ctx* d, const float* w, float* v, const double*
   a.b = bE; a.tol = d->mtol; a.v = vE; a.work = d->mw; a.partial = d->mpart; a.red = d->mred; a.out = d->mout;
   cudaError_t le = cudaSuccess;
   bool launched = false;
-  NS_DISPATCH(Ns, (launched = launch_little_mrhs<NSV>(d, a, s, &le)));
+  NS_DISPATCH_FEW(Ns, (launched = launch_little_mrhs<NSV>(d, a, s, &le)));
   if (!launched) { dw_set_error("multi-RHS little solver: unsupported Ns"); return DW_EINVAL; }
   DW_CUDA(le);
   dw_note_launch();
@@ -2737,11 +2752,11 @@ static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_c
     const size_t dsm32 = coop_dyn_smem<float>(sms), dsm64 = coop_dyn_smem<double>(sms);
     NS_DISPATCH(Ns, (cudaFuncSetAttribute(little_gcr_coop_kernel<float, NSV>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm32)));
-    NS_DISPATCH(Ns, (cudaFuncSetAttribute(little_gcr_coop_kernel<double, NSV>,
+    NS_DISPATCH_FEW(Ns, (cudaFuncSetAttribute(little_gcr_coop_kernel<double, NSV>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm64)));
     NS_DISPATCH(Ns, (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, little_gcr_coop_kernel<float, NSV>,
                                                                    COOP_THREADS, dsm32)));
-    NS_DISPATCH(Ns, (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, little_gcr_coop_kernel<double, NSV>,
+    NS_DISPATCH_FEW(Ns, (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, little_gcr_coop_kernel<double, NSV>,
                                                                    COOP_THREADS, dsm64)));
     d->coop_grid = (coop && b32 > 0 && b64 > 0 && Ns <= 32) ? sms : 0;
     if (d->coop_grid) {
@@ -2750,7 +2765,7 @@ static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_c
       // multi-RHS solver (batches of right-hand sides): Ns with a compiled kernel, all CTAs resident
       int bm = 0;
       const size_t dsmm = coop_m_dyn_bytes(Ns);
-      NS_DISPATCH(Ns, if constexpr (NSV > 0) {
+      NS_DISPATCH_FEW(Ns, if constexpr (NSV > 0) {
         if (cudaFuncSetAttribute(little_gcr_coop_mrhs_kernel<NSV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)dsmm) == cudaSuccess)
           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bm, little_gcr_coop_mrhs_kernel<NSV>, COOP_THREADS, dsmm);
