@@ -31,6 +31,9 @@
  *  them in *_destroy.  Streams: `stream` is a cudaStream_t (NULL = legacy
  *  default stream); calls are stream-ordered unless documented as
  *  synchronous.  One context must not be used by two host threads at once.
+ *  A context belongs to the device that was current at dw_create; calls that
+ *  take it (dw_apply, dw_apply_schur_static, sap_precondition, deflation_build,
+ *  gcr_solve, cgnr_solve) return DW_EINVAL when another device is current.
  *
  *  Errors: functions return a dw_status.  Negative values are failures
  *  (nothing useful was written); positive values are successes with a

@@ -296,6 +296,7 @@ struct HostTimer;
 
 struct dw_ctx {
   dw_params p;
+  int device = -1;             // CUDA device the context's memory lives on (current device at dw_create)
   Geom g;                      // device pointers filled in
   long long V;
   int nsb[4];
@@ -324,6 +325,10 @@ struct dw_ctx {
   unsigned* d_count = nullptr;
   double* h_red = nullptr;                // pinned host mirror
 };
+
+// DW_OK when the calling thread's current device is the context's device; otherwise DW_EINVAL
+// with a message naming the entry point (kernels would mix memory of two devices).
+int dw_check_device(const dw_ctx* c, const char* who);
 
 // kernel launch counter (process-wide, all devices) ---------------------------
 void dw_note_launch();

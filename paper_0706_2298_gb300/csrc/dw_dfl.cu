@@ -2802,6 +2802,7 @@ static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_c
 extern "C" int deflation_build(dw_ctx* c, const dfl_params* p, const double* start, dfl_ctx** out, dfl_info* info) {
   if (!c || !p || !start || !out) { dw_set_error("deflation_build: null argument"); return DW_EINVAL; }
   *out = nullptr;
+  if (int rc = dw_check_device(c, "deflation_build")) return rc;
   if (p->Ns < 1 || p->Ns > NSMAX || p->n_inv < 0 || p->ncy < 0 || p->nmr < 0 ||
       (p->basis_prec != DW_BF16 && p->basis_prec != DW_F64)) {
     dw_set_error("deflation_build: Ns must be in 1..32, counts non-negative, basis_prec DW_BF16 or DW_F64");

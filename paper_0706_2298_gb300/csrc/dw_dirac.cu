@@ -334,6 +334,7 @@ extern "C" int dw_apply(dw_ctx* c, int prec, int op, int nrhs, const void* in, v
     dw_set_error("dw_apply: bad argument");
     return DW_EINVAL;
   }
+  if (int rc = dw_check_device(c, "dw_apply")) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   if (prec == DW_F64X) {
     int rc = dirac_full_f64x(c, (const double*)in, (double*)out, nrhs, st);
@@ -420,6 +421,7 @@ extern "C" int dw_apply_schur_static(dw_ctx* c, int prec, const void* in, void* 
     dw_set_error("dw_apply_schur_static: bad argument");
     return DW_EINVAL;
   }
+  if (int rc = dw_check_device(c, "dw_apply_schur_static")) return rc;
   const size_t need = dw_field_bytes(c, prec);
   if (need > kSchurStaticBytes) {
     char msg[256];

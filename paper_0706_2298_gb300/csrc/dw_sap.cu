@@ -737,6 +737,7 @@ extern "C" int sap_precondition(dw_ctx* c, int prec, int ncy, int nmr, int nrhs,
     dw_set_error("sap_precondition: bad argument");
     return DW_EINVAL;
   }
+  if (int rc = dw_check_device(c, "sap_precondition")) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   size_t n = (size_t)c->V * 24;
   if (prec == DW_F32 && nrhs > 1) return sap_apply_mrhs(c, ncy, nmr, (const float*)rho, (float*)xi, nrhs, st);

@@ -14,6 +14,18 @@
 static thread_local std::string g_err = "no error";
 
 void dw_set_error(const std::string& msg) { g_err = msg; }
+int dw_check_device(const dw_ctx* c, const char* who) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return dw_cuda_fail(e, who);
+  if (dev != c->device) {
+    char msg[200];
+    snprintf(msg, sizeof msg, "%s: the current device (%d) is not the context's device (%d)", who, dev, c->device);
+    dw_set_error(msg);
+    return DW_EINVAL;
+  }
+  return DW_OK;
+}
 int dw_cuda_fail(cudaError_t e, const char* what) {
   g_err = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
   return e == cudaErrorMemoryAllocation ? DW_ENOMEM : DW_ECUDA;
@@ -317,8 +329,14 @@ extern "C" int dw_create(const dw_params* p, const double* links_host, dw_ctx** 
     }
   }
 
+  int dev = -1;
+  {
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return dw_cuda_fail(e, "dw_create: cudaGetDevice");
+  }
   dw_ctx* c = new dw_ctx();
   c->p = *p;
+  c->device = dev;
   c->V = V;
   for (int mu = 0; mu < 4; ++mu) c->nsb[mu] = nsb[mu];
   Geom& g = c->g;

@@ -569,6 +569,7 @@ extern "C" int gcr_solve(dw_ctx* c, dfl_ctx* d, const sol_params* p, int nrhs, c
     dw_set_error("gcr_solve: bad argument");
     return DW_EINVAL;
   }
+  if (int rc = dw_check_device(c, "gcr_solve")) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   int worst = DW_OK;
   const size_t n = (size_t)c->V * 24;
@@ -598,6 +599,7 @@ extern "C" int cgnr_solve(dw_ctx* c, double tol, int maxit, const double* eta_ca
     dw_set_error("cgnr_solve: bad argument");
     return DW_EINVAL;
   }
+  if (int rc = dw_check_device(c, "cgnr_solve")) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t V = c->V, n = V * 12, fb = dw_field_bytes(c, DW_F64);
   Work<double> W;

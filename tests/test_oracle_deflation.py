@@ -157,3 +157,93 @@ def test_round_bf16_hand_values():
     x = np.array([1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -8, 1.0 / 3.0, -2.5, 0.0])
     expect = np.array([1.0, 1.0, 1 + 2 ** -6, 171.0 / 512.0, -2.5, 0.0])
     assert np.array_equal(round_bf16(x), expect)
+
+
+# ----------------------------------------------------------------------------- inverse iteration (5.1)
+class _LinearPreconditioner:
+    """Stand-in for M_sap with a known linear action (a dense matrix), so that the steps of
+    the inverse iteration can be checked against matrix powers."""
+
+    def __init__(self, A):
+        self.A = A
+        self.calls = 0
+
+    def apply(self, fields, ncy, nmr):
+        self.calls += 1
+        f = np.asarray(fields)
+        return (f.reshape(f.shape[0], -1) @ self.A.T).reshape(f.shape)
+
+
+def _plane_wave_span(L, p0):
+    """Orthonormal basis of {u exp(i p.x)}: momenta (+-p0, 0, 0, 0), u any spin-colour vector."""
+    x0 = np.indices(L)[0].reshape(-1)
+    cols = []
+    for s in (1, -1):
+        ph = np.exp(1j * s * p0 * x0) / np.sqrt(x0.size)
+        for k in range(12):
+            v = np.zeros((x0.size, 12), dtype=np.complex128)
+            v[:, k] = ph
+            cols.append(v.reshape(-1))
+    return np.array(cols).T
+
+
+def test_inverse_iteration_is_normalised_power():
+    """(5.1) with a linear stand-in M = D^{-1}: n steps give D^{-n} psi_l / ||D^{-n} psi_l||
+    for every field separately (each step normalises each field, not the set)."""
+    from oracle.deflation import inverse_iteration
+    L = (4, 4, 2, 2)
+    D = WilsonClover(L, synth.random_gauge(L, 31).numpy(), 0.3, 1.0)
+    Dm = D.dense()
+    M = _LinearPreconditioner(np.linalg.inv(Dm))
+    start = synth.start_fields(L, 3, 5).numpy()
+    start[1] *= 7.0                       # unequal norms: a joint normalisation would show
+    from scipy.linalg import lu_factor, lu_solve
+    lu = lu_factor(Dm)
+    for n in (0, 1, 3):
+        M.calls = 0
+        got = inverse_iteration(M, start, n, 4, 4)
+        assert M.calls == n
+        for l in range(3):
+            w = start[l].reshape(-1)
+            for _ in range(n):
+                w = lu_solve(lu, w)
+            if n:
+                w = w / np.linalg.norm(w)
+            assert np.linalg.norm(got[l].reshape(-1) - w) <= 1e-11 * np.linalg.norm(w)
+            if n:
+                assert abs(np.linalg.norm(got[l]) - 1.0) <= 1e-13
+
+
+def test_inverse_iteration_free_field_reaches_lowest_modes():
+    """Free field on 4^4 (antiperiodic time): the smallest |lambda| of D is taken on the plane
+    waves with p = (+-pi/4, 0, 0, 0), |lambda| = |m0 + 1 - cos(pi/4) + i sin(pi/4)|, and the next
+    |lambda| is 1.6415 (p0 = pi/4 with one spatial pi/2).  With M = D^{-1} the fields converge to
+    that 24-dimensional span at the rate (0.7132/1.6415)^n; with the Schwarz procedure itself
+    (4 cycles, 4 MR steps) they become dominated by it (deficit far below the start's 0.99) and
+    ||D psi|| approaches the lower end of the spectrum."""
+    from oracle.deflation import inverse_iteration
+    from oracle.sap import SchwarzOracle
+    L = (4, 4, 4, 4)
+    m0 = -0.2
+    D = WilsonClover(L, synth.unit_gauge(L).numpy(), m0, 1.0)
+    lam_min = abs(m0 + 1 - np.cos(np.pi / 4) + 1j * np.sin(np.pi / 4))
+    Q = _plane_wave_span(L, np.pi / 4)
+    # the span is an invariant subspace of D on which |lambda| = lam_min
+    DQ = D.apply(Q.T.reshape(24, D.V, 4, 3)).reshape(24, -1).T
+    assert np.linalg.norm(DQ - Q @ (Q.conj().T @ DQ)) <= 1e-12 * np.linalg.norm(DQ)
+    assert np.allclose(np.abs(np.linalg.eigvals(Q.conj().T @ DQ)), lam_min, atol=1e-12)
+
+    def deficit(f):
+        f = f.reshape(-1)
+        return np.linalg.norm(f - Q @ (Q.conj().T @ f)) / np.linalg.norm(f)
+
+    start = synth.start_fields(L, 2, 3).numpy()
+    assert min(deficit(s) for s in start) > 0.9
+    exact = inverse_iteration(_LinearPreconditioner(np.linalg.inv(D.dense())), start, 25, 0, 0)
+    bound = 10 * (lam_min / 1.6415) ** 25
+    assert max(deficit(s) for s in exact) <= bound
+    sap = SchwarzOracle(D, (2, 2, 2, 2))
+    got = inverse_iteration(sap, start, 11, 4, 4)
+    assert max(deficit(s) for s in got) <= 0.2
+    for s in got:
+        assert lam_min <= norm(D.apply(s)) / norm(s) <= 1.2 * lam_min

@@ -63,3 +63,17 @@ def test_static_schur_volume_limit():
     dw.dw_apply_schur_static(ctx, dw.DW_F32, x32, y)
     torch.cuda.synchronize()
     assert _rel(y, ref) <= TOL[dw.DW_F32]
+
+
+@pytest.mark.skipif(torch.cuda.device_count() < 2, reason="needs a second device to make the current device differ")
+def test_static_schur_rejects_other_device():
+    """A context lives on the device current at dw_create; with another device current the
+    entry point refuses instead of launching kernels on one device with memory of the other."""
+    L = (8, 8, 8, 8)
+    with torch.cuda.device(0):
+        ctx = dw.dw_create(L, -0.1, 1.3, synth.random_gauge(L, 11), (4, 4, 4, 4))
+        x = _packed(ctx, dw.DW_F32, L, 21)
+        y = ctx.empty_field(dw.DW_F32)
+    with torch.cuda.device(1):
+        with pytest.raises(dw.DwError, match="not the context's device"):
+            dw.dw_apply_schur_static(ctx, dw.DW_F32, x, y)
