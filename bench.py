@@ -43,6 +43,13 @@ WORKLOADS = {
 MASS_FILE = os.path.join(ROOT, "paper_0706_2298_gb300", "workload_masses.json")
 
 
+# The benchmark's metric, printed identically by both arms (ours and the oracle reference arm).
+METRIC = "s/solve to rel. residual 1e-10 vs plain FP64 path; D_w HBM GB/s & % of peak"
+# Measured run of the oracle's plain (unpreconditioned) GCR to 1e-10 on a workload, written by
+# oracle/plain_gcr_run.py: gives the oracle's iteration count for the reference arm.
+ORACLE_RUN = {"24^3x48": os.path.join(ROOT, "oracle", "plain_gcr_48x24c3.json"),
+              "8^4": os.path.join(ROOT, "oracle", "plain_gcr_8c4.json")}
+
 # DRAM bytes per little-GCR iteration of the cooperative kernel, from one ncu capture of the
 # current kernel (dram__bytes_read.sum + dram__bytes_write.sum of one launch / its iterations):
 # 48x24^3, Ns = 20: (84.87 + 4.76) MB over 42 iterations (cold cache: the first iteration reads
@@ -127,60 +134,204 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def oracle_d_time(U, L, m0, csw, reps=2):
-    """FP64 oracle D application time at the workload size (bounded CPU sample)."""
-    import numpy as np
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def oracle_gcr_sample(U, eta, wl, iterations, warmup=1):
+    """The oracle's own solve -- unpreconditioned restarted GCR on D, FP64 numpy, as it stands --
+    on the workload for a bounded number of GCR iterations (`warmup` untimed D applications
+    first).  Returns (seconds per GCR iteration, iterations run, true relative residual)."""
     from oracle.dirac import WilsonClover
+    from oracle.krylov import gcr
+    from oracle.lattice import norm
+    D = WilsonClover(wl["L"], U, wl["m0"], wl["csw"])
+    for _ in range(max(warmup, 0)):
+        D.apply(eta)
+    t0, c0 = time.perf_counter(), time.process_time()
+    x, info = gcr(D.apply, eta, tol=wl["tol"], nkv=wl["nkv"], maxit=iterations)
+    t, cpu = time.perf_counter() - t0, time.process_time() - c0
+    rel = norm(eta - D.apply(x)) / norm(eta)
+    ORACLE_THREADS.append(cpu / max(t, 1e-9))
+    return t / max(info.iterations, 1), info.iterations, float(rel)
+
+
+# threads busy on average during the oracle samples (process CPU time / wall time)
+ORACLE_THREADS = []
+
+
+def oracle_cores():
+    return max(1, round(max(ORACLE_THREADS))) if ORACLE_THREADS else 1
+
+
+def oracle_run_record(workload):
+    """The oracle's full plain-GCR run to 1e-10 on this workload (oracle/plain_gcr_run.py), if any."""
+    p = ORACLE_RUN.get(workload)
+    if p and os.path.exists(p):
+        with open(p) as f:
+            rec = json.load(f)
+        if rec.get("converged"):
+            return rec
+    return None
+
+
+def _oracle_small_solve(seed):
+    """One whole oracle solve at 8^4 (plain GCR to 1e-10); returns (seconds, iterations, residual)."""
+    sys.path.insert(0, ROOT)
+    from oracle.dirac import WilsonClover
+    from oracle.lattice import norm
+    from oracle.solver import solve_plain
     from paper_0706_2298_gb300 import synth
-    D = WilsonClover(L, U, m0, csw)
-    psi = synth.gaussian_source(L, 99).numpy()
-    D.apply(psi)
+    wl = WORKLOADS["8^4"]
+    D = WilsonClover(wl["L"], synth.random_gauge(wl["L"], wl["gauge_seed"]).numpy(), wl["m0"], wl["csw"])
+    eta = synth.gaussian_source(wl["L"], seed).numpy()
     t0 = time.perf_counter()
-    for _ in range(reps):
-        D.apply(psi)
-    return (time.perf_counter() - t0) / reps
+    x, info = solve_plain(D, eta, tol=wl["tol"], nkv=wl["nkv"])
+    t = time.perf_counter() - t0
+    return t, info.iterations, float(norm(eta - D.apply(x)) / norm(eta))
 
 
-def d_equivalents(iterations, ncy, nmr):
-    """D-application equivalents of a DFL+SAP+GCR solve: per GCR step one M_sap
-    (ncy cycles, each colour pass nmr+2 half-lattice block operator applications
-    -> ncy*(nmr+2) full applications), D xi and the D Phi v of P_L."""
-    return iterations * (ncy * (nmr + 2) + 2)
+def oracle_small_solves(nproc):
+    """Whole oracle solves at 8^4, measured: one on one core, then nproc independent solves in nproc
+    processes started with spawn (all cores); s/solve single-thread and all-cores."""
+    import multiprocessing as mp
+    t1, its, rel = _oracle_small_solve(1002)
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(nproc) as pool:
+        res = pool.map(_oracle_small_solve, [2000 + k for k in range(nproc)])
+    wall = time.perf_counter() - t0
+    return {"workload": "8^4, m0 = -0.2, c_sw = 1, plain GCR(16) to 1e-10 (whole solves, measured)",
+            "single_thread_s_per_solve": t1, "iterations": its, "true_relres": rel,
+            "all_cores_s_per_solve": wall / nproc, "all_cores_processes": nproc,
+            "all_cores_max_relres": max(r[2] for r in res)}
+
+
+def l2_copy_bandwidth(torch, mb=24, reps=200):
+    """Measured L2-resident copy bandwidth: a 2 x `mb` MB working set (well inside the 129 MB L2)
+    copied back and forth; bytes read + written per copy over the CUDA-event time."""
+    n = mb * (1 << 20) // 4
+    a = torch.ones(n, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    for _ in range(10):
+        b.copy_(a)
+    best = None
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps // 2):
+            b.copy_(a)
+            a.copy_(b)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / reps
+        best = t if best is None else min(best, t)
+    return {"gbs": 2 * n * 4 / best / 1e9,
+            "how": f"torch copy of a {mb} MB fp32 buffer back and forth, {reps} copies, best of 5 (CUDA events)"}
+
+
+def fp32_peak_tflops():
+    """FP32 CUDA-core peak from the unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop/FMA x
+    2.07 GHz (maximum SM clock) = 80.5 TFLOP/s."""
+    return {"tflops": 152 * 128 * 2 * 2.07e9 / 1e12, "how": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+
+
+def sap_flops_per_site(nmr):
+    """Algorithmic FP32 flops per lattice site of the colour a Schwarz pass processes (counting the
+    Wilson hop as 1320 and the clover term as 552 flops per site): even-odd preparation
+    (A_oo^-1, D_eo: 948 per block site), nmr MR steps (one D^ application 1884 + two inner products
+    and two updates 168 per block site), odd reconstruction (948) and the residual update (one D,
+    1872)."""
+    return 948 + nmr * (1884 + 168) + 948 + 1872
 
 
 def run_reference(args, wl, rank):
-    import numpy as np
+    """The reference arm: the oracle (plain FP64 numpy, as it stands) on the host cores.  A step is
+    one GCR iteration of the oracle's own solve (unpreconditioned GCR on D) at the workload's size;
+    s/solve = measured seconds per iteration x the iteration count of the oracle's full run to
+    1e-10 on this workload (oracle/plain_gcr_run.py, whose record names its host)."""
     from paper_0706_2298_gb300 import synth
     if rank != 0:
         return
     L = wl["L"]
+    rec = oracle_run_record(args.workload)
+    base = {"impl": "reference", "metric": METRIC, "unit": "s/solve", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": {"workload": args.workload, "L": list(L), "m0": wl["m0"]}}
+    if rec is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"no converged oracle run recorded for {args.workload}"}),
+              flush=True)
+        return
     U = synth.random_gauge(L, wl["gauge_seed"]).numpy()
-    n_it = wl.get("ref_iterations", 22)   # GCR steps of the FP64 path (measured on the GPU)
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        pass
-    t_steps = []
-    from oracle.dirac import WilsonClover
-    D = WilsonClover(L, U, wl["m0"], wl["csw"])
-    psi = synth.gaussian_source(L, 99).numpy()
-    D.apply(psi)
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        D.apply(psi)
-        t_steps.append(time.perf_counter() - t0)
-    t_d = statistics.median(t_steps)
-    neq = d_equivalents(n_it, wl["ncy"], wl["nmr"])
-    val = t_d * neq
-    line = {"impl": "reference", "metric": "s/solve to rel. residual 1e-10 (DFL+SAP+GCR)", "value": val,
-            "unit": "s/solve", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * t_d, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "L": list(L), "m0": wl["m0"]},
-            "cpu_baseline": {"value": val, "unit": "s/solve", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} FP64 oracle D applications at {args.workload} "
-                                       f"({t_d:.3f} s each) x {neq} D-equivalents of a solve with "
-                                       f"{n_it} GCR steps (the FP64 path's count on the GPU)"},
-            "e2e": {"value": val, "unit": "s/solve", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    eta = synth.gaussian_source(L, wl["source_seed"]).numpy()
+    t_it, n_it, rel = oracle_gcr_sample(U, eta, wl, max(args.steps, 1), warmup=args.warmup)
+    val = t_it * rec["iterations"]
+    sample = (f"{n_it} GCR iterations of the oracle's plain GCR({wl['nkv']}) on D at {args.workload} "
+              f"(true relres after them {rel:.3e}; {t_it:.3f} s per iteration, numpy) x "
+              f"{rec['iterations']} iterations of the oracle's full run to {wl['tol']:g} "
+              f"({rec['solve_s']:.0f} s on {rec.get('cpu_model', '?')})")
+    line = dict(base, value=val, ms_per_step=1e3 * t_it,
+                cpu_baseline={"value": val, "unit": "s/solve", "cores": oracle_cores(), "kind": "oracle", "sample": sample,
+                              "cpu_model": cpu_model(), "nproc": os.cpu_count()},
+                e2e={"value": val, "unit": "s/solve", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0})
     print(json.dumps(line), flush=True)
+
+
+def profile_case(args, wl):
+    """Small fixed launch sequences for ncu captures of single kernels (not a benchmark):
+    'dirac-sap': 3 D applications and 2 M_sap (ncy = 1) in --prec;  'little': --solves FP32
+    little solves to 1e-6 with an Ns-field subspace (4 inverse-iteration steps);  'batch12': one
+    batched solve of the 12 point sources."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_0706_2298_gb300 import dwsolve as dw
+    from paper_0706_2298_gb300 import synth
+    L = wl["L"]
+    U = synth.random_gauge(L, wl["gauge_seed"], device="cuda").cpu()
+    ctx = dw.dw_create(L, wl["m0"], wl["csw"], U, wl["sap_bs"])
+    if args.profile_case == "dirac-sap":
+        prec = dw.DW_F32 if args.prec == "f32" else dw.DW_F64
+        x, y = ctx.empty_field(prec), ctx.empty_field(prec)
+        dw.dw_pack(ctx, prec, 1, synth.gaussian_source(L, 2).cuda(), x)
+        for _ in range(3):
+            dw.dw_apply(ctx, prec, dw.DW_OP_FULL, 1, x, y)
+        for _ in range(2):
+            dw.sap_precondition(ctx, prec, 1, wl["nmr"], 1, x, y)
+    else:
+        n_inv = 4 if args.profile_case == "little" else wl["n_inv"]
+        d = dw.deflation_build(ctx, wl["dfl_bs"], wl["Ns"], n_inv, wl["ncy"], wl["nmr"],
+                               synth.start_fields(L, wl["Ns"], wl["start_seed"]).cuda())
+        if args.profile_case == "little":
+            w = torch.randn(d.Nb * d.Ns * 2, dtype=torch.float32, device="cuda")
+            v = torch.empty_like(w)
+            for _ in range(args.solves):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rc, it, rr = dw.little_dirac_solve(d, dw.DW_F32, w, v, 1e-6, 2000)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                print(f"little solve rc {rc} iterations {it} relres {rr:.3e} {dt * 1e6 / max(it, 1):.1f} us/iteration",
+                      flush=True)
+        else:
+            eta = synth.point_sources(L).cuda()
+            psi = torch.empty_like(eta)
+            rc, _ = dw.gcr_solve(ctx, d, dw.sol_params(tol=wl["tol"], nkv=wl["nkv"], mixed=1), 12, eta, psi)
+            print("batched solve rc", rc, flush=True)
+    torch.cuda.synchronize()
+    print("ok", flush=True)
 
 
 def main():
@@ -193,9 +344,16 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-batch", action="store_true", help="skip the 12 point-source batched solve")
+    ap.add_argument("--profile-case", choices=["dirac-sap", "little", "batch12"], default=None,
+                    help="run a small fixed launch sequence for an ncu capture and exit")
+    ap.add_argument("--prec", default="f32", choices=["f32", "f64"], help="--profile-case dirac-sap precision")
+    ap.add_argument("--solves", type=int, default=1, help="--profile-case little: number of little solves")
     args = ap.parse_args()
     load_masses()
     wl = WORKLOADS[args.workload]
+    if args.profile_case:
+        profile_case(args, wl)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -266,8 +424,18 @@ def main():
     ms_per_step = t_ms / args.steps
     iters = statistics.median([i.iterations for i in infos])
 
+    # ---- true residual of the last timed solve, by the library's FP64 D (not its double-float D)
+    x64, y64 = ctx.empty_field(dw.DW_F64), ctx.empty_field(dw.DW_F64)
+    dw.dw_pack(ctx, dw.DW_F64, 1, psi, x64)
+    dw.dw_apply(ctx, dw.DW_F64, dw.DW_OP_FULL, 1, x64, y64)
+    dw.dw_pack(ctx, dw.DW_F64, 1, eta, x64)
+    relres64 = float(torch.linalg.norm(x64 - y64) / torch.linalg.norm(x64))
+    del x64, y64
+
     # ---- rooflines from the library's CUDA-event phase timers over the timed solves
     hbm, peak_kind = peaks()
+    l2 = l2_copy_bandwidth(torch)
+    fp32_peak = fp32_peak_tflops()
     # dominant kernel: the cooperative little GCR (A.2-A.4).  Algorithmic bytes per little-GCR
     # iteration (FP32): the eight off-diagonal Ns x Ns blocks of every block row of the little
     # operator (both parities, read once by the two hops) and the 2 Ns global-mode vectors g, B^g
@@ -277,10 +445,11 @@ def main():
     t_little = sum(i.t_little for i in infos)
     n_lit = sum(i.little_iterations for i in infos)
     lit_s = t_little / max(n_lit, 1)
-    roof = {"kernel": f"little_gcr_coop_kernel<float,{Ns}>", "bound": "hbm", "achieved": lit_bytes / lit_s / 1e9,
-            "peak": hbm, "unit": "GB/s", "frac": lit_bytes / lit_s / 1e9 / hbm, "traffic": LITTLE_TRAFFIC.get(
-                (args.workload, Ns)), "peak_kind": peak_kind, "per": "little GCR iteration",
-            "us_per_iteration": lit_s * 1e6, "algorithmic_bytes": lit_bytes, "l2_resident": True,
+    roof = {"kernel": f"little_gcr_coop_kernel<float,{Ns}>", "bound": "l2", "achieved": lit_bytes / lit_s / 1e9,
+            "peak": l2["gbs"], "unit": "GB/s", "frac": lit_bytes / lit_s / 1e9 / l2["gbs"],
+            "traffic": LITTLE_TRAFFIC.get((args.workload, Ns)), "peak_kind": "measured here: " + l2["how"],
+            "per": "little GCR iteration", "us_per_iteration": lit_s * 1e6, "algorithmic_bytes": lit_bytes,
+            "l2_resident": True, "hbm_peak": hbm, "frac_of_hbm": lit_bytes / lit_s / 1e9 / hbm,
             "iterations_per_solve": n_lit / max(len(infos), 1)}
     # the Schwarz block kernel (second largest): 960 algorithmic bytes per site processed
     t_sap = sum(i.t_sap for i in infos)
@@ -288,9 +457,13 @@ def main():
     sap_launch_s = t_sap / max(n_sap_launch, 1)
     # per site processed (FP32): links 4 x 12 reals, clover (A or A^-1) 72 reals, r in/out, delta out, xi in/out
     sap_bytes = (V // 2) * 4 * (48 + 72 + 24 * 5)
-    roof_sap = {"kernel": "sap_staged_kernel<128>", "bound": "hbm", "achieved": sap_bytes / sap_launch_s / 1e9,
+    sap_flops = (V // 2) * sap_flops_per_site(wl["nmr"])
+    roof_sap = {"kernel": "sap_staged_kernel<128>", "bound": "hbm+alu", "achieved": sap_bytes / sap_launch_s / 1e9,
                 "peak": hbm, "unit": "GB/s", "frac": sap_bytes / sap_launch_s / 1e9 / hbm,
-                "launch_us": sap_launch_s * 1e6, "algorithmic_bytes_per_launch": sap_bytes}
+                "launch_us": sap_launch_s * 1e6, "algorithmic_bytes_per_launch": sap_bytes,
+                "alu": {"achieved": sap_flops / sap_launch_s / 1e12, "peak": fp32_peak["tflops"], "unit": "TFLOP/s",
+                        "frac": sap_flops / sap_launch_s / 1e12 / fp32_peak["tflops"],
+                        "peak_kind": fp32_peak["how"], "flops_per_launch": sap_flops}}
 
     # ---- D_w bandwidth: FP32 and FP64 applications, L2 flushed before each timed launch
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -379,18 +552,23 @@ def main():
                  "autotune": tune}
         del eta12, psi12
 
-    # ---- CPU oracle sample (rank 0, N = 1 only)
+    # ---- CPU oracle sample (rank 0, N = 1 only): the oracle's own solve on the host cores
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        import torch as _t
-        t_d = oracle_d_time(U.numpy(), L, wl["m0"], wl["csw"])
-        neq = d_equivalents(iters, wl["ncy"], wl["nmr"])
-        cpu = {"value": t_d * neq, "unit": "s/solve", "cores": 1, "kind": "oracle",
-               "sample": f"2 FP64 oracle D applications at {args.workload} ({t_d:.2f} s each, numpy, 1 thread) "
-                         f"x {neq} D-equivalents of this solve ({iters} GCR steps x (ncy*(nmr+2)+2))"}
+    rec = oracle_run_record(args.workload)
+    if rank == 0 and world == 1 and not args.no_cpu and rec is not None:
+        n_s = 4
+        t_it, n_it, rel = oracle_gcr_sample(U.numpy(), eta_h.numpy() if rank == 0 else None, wl, n_s)
+        cpu = {"value": t_it * rec["iterations"], "unit": "s/solve", "cores": oracle_cores(), "kind": "oracle",
+               "sample": f"{n_it} GCR iterations of the oracle's plain GCR({wl['nkv']}) on D at {args.workload} "
+                         f"({t_it:.2f} s per iteration, numpy, true relres after them {rel:.3e}) x "
+                         f"{rec['iterations']} iterations of the oracle's full run to {wl['tol']:g} "
+                         f"({rec['solve_s']:.0f} s wall on {rec.get('cpu_model', '?')})",
+               "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+               "oracle_full_run": {k: rec.get(k) for k in ("iterations", "solve_s", "cpu_model", "nproc")},
+               "whole_solves": oracle_small_solves(min(os.cpu_count() or 1, 16))}
 
     if rank == 0:
-        line = {"metric": "s/solve to rel. residual 1e-10 (DFL+SAP+GCR, mixed precision) vs plain FP64 path",
+        line = {"metric": METRIC,
                 "value": value, "unit": "s/solve", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32+bf16 (double-float restarts)", "data": "synthetic",
@@ -399,7 +577,7 @@ def main():
                            "n_inv": wl["n_inv"], "nkv": wl["nkv"], "ncy": wl["ncy"], "nmr": wl["nmr"],
                            "tol": wl["tol"], "l2": "inputs larger than L2 (solve working set > 2 GB)",
                            "parallelism": f"replicas x{world}"},
-                "gcr_iterations": iters, "relres": max(i.relres for i in infos),
+                "gcr_iterations": iters, "relres": max(i.relres for i in infos), "relres_fp64_check": relres64,
                 "little_iterations_per_solve": statistics.median([i.little_iterations for i in infos]),
                 "phase_s": {k: statistics.median([getattr(i, k) for i in infos])
                             for k in ("t_sap", "t_dirac", "t_project", "t_little", "t_orth", "t_restart")},

@@ -192,6 +192,17 @@ int little_apply(dfl_ctx* d, const double* v_dev, double* w_dev, void* stream);
 int little_dirac_solve(dfl_ctx* d, int prec, const void* w_dev, void* v_dev, double tol, int maxit,
                        int* iters, double* relres, void* stream);
 
+/* nrhs little systems A v_r = w_r at once (Appendix A.2-A.4, as little_dirac_solve), w/v:
+ * nrhs little vectors one after the other.  prec DW_F32: the FP32 systems run in lockstep in one
+ * cooperative launch per group of up to 12 right-hand sides (each with its own scalars and
+ * convergence), tol relative to each ||w_r|| on the even-odd deflated system.  prec DW_F64: FP64
+ * vectors, iterative refinement (FP64 residual of the full little system, FP32 lockstep correction
+ * solves) to ||w_r - A v_r|| <= tol ||w_r|| -- the restart solves of the batched mixed solver.
+ * 1 <= nrhs <= 64.  iters/relres: nrhs entries (may be NULL).  Returns DW_ENOTCONV when a system
+ * missed the tolerance.  Synchronous. */
+int little_dirac_solve_batch(dfl_ctx* d, int prec, int nrhs, const void* w_dev, void* v_dev, double tol,
+                             int maxit, int* iters, double* relres, void* stream);
+
 typedef struct {
   double tol;              /* stop when ||eta - D psi|| <= tol ||eta|| (FP64 residual) */
   int nkv;                 /* Krylov vectors per GCR cycle (restart length) */

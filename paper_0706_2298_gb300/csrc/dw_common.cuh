@@ -294,6 +294,34 @@ DW_D void clover_apply(const T* __restrict__ clov, size_t V, size_t i, const cpl
 // ---------------------------------------------------------------- contexts
 struct HostTimer;
 
+// Device buffers kept by a context between calls: a solver asks for the same sequence of sizes
+// on every call and gets the same buffers back (allocated on the first call, or when a larger
+// size is asked for), so repeated solves allocate and free nothing.
+struct WsArena {
+  std::vector<std::pair<size_t, void*>> bufs;
+  size_t next = 0;
+  void rewind() { next = 0; }
+  cudaError_t get(size_t bytes, void** p) {
+    if (next < bufs.size() && bufs[next].first >= bytes) { *p = bufs[next++].second; return cudaSuccess; }
+    if (next < bufs.size()) {        // too small: replace this buffer
+      cudaFree(bufs[next].second);
+      bufs[next] = {0, nullptr};
+    } else {
+      bufs.push_back({0, nullptr});
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return e;
+    bufs[next++] = {bytes, *p};
+    return cudaSuccess;
+  }
+  void release() {
+    for (auto& b : bufs)
+      if (b.second) cudaFree(b.second);
+    bufs.clear();
+    next = 0;
+  }
+};
+
 struct dw_ctx {
   dw_params p;
   int device = -1;             // CUDA device the context's memory lives on (current device at dw_create)
@@ -324,6 +352,7 @@ struct dw_ctx {
   double* d_red = nullptr;                // reduction scratch
   unsigned* d_count = nullptr;
   double* h_red = nullptr;                // pinned host mirror
+  WsArena ws_solve[3];                    // solver workspaces: [0] GCR, [1] batched GCR, [2] CGNR
 };
 
 // DW_OK when the calling thread's current device is the context's device; otherwise DW_EINVAL

@@ -2466,6 +2466,32 @@ extern "C" int little_dirac_solve(dfl_ctx* d, int prec, const void* w, void* v, 
   return rc;
 }
 
+extern "C" int little_dirac_solve_batch(dfl_ctx* d, int prec, int nrhs, const void* w, void* v, double tol,
+                                        int maxit, int* iters, double* relres, void* stream) {
+  if (!d || !w || !v || w == v || nrhs < 1 || nrhs > 64 || (prec != DW_F32 && prec != DW_F64) || maxit < 1 ||
+      !(tol > 0)) {
+    dw_set_error("little_dirac_solve_batch: bad argument");
+    return DW_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<int> use(nrhs, 1), it(nrhs, 0);
+  std::vector<double> rr(nrhs, 0.0), tl(nrhs, tol);
+  int rc = prec == DW_F32
+               ? little_solve_batch_f32(d, (const float*)w, (float*)v, tl.data(), use.data(), maxit, 24, nrhs,
+                                        it.data(), rr.data(), s)
+               : little_solve_refined_batch(d, (const double*)w, (double*)v, tol, use.data(), maxit, 24, nrhs,
+                                            it.data(), rr.data(), s);
+  if (rc < 0) return rc;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return dw_cuda_fail(e, "little_dirac_solve_batch");
+  for (int r = 0; r < nrhs; ++r) {
+    if (iters) iters[r] = it[r];
+    if (relres) relres[r] = rr[r];
+    if (prec == DW_F32 && !(rr[r] <= tol)) rc = DW_ENOTCONV;
+  }
+  return rc;
+}
+
 // ---------------------------------------------------------------------- build
 static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_ctx* d, dfl_info* info) {
   const Geom& g = c->g;

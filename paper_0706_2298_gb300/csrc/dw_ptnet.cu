@@ -121,9 +121,12 @@ __global__ void __launch_bounds__(256) ptnet_dw_kernel(Geom g, const float* __re
   const int d = blockIdx.y;
   const long long i0 = (long long)blockIdx.x * chunk, i1 = min(i0 + chunk, (long long)g.V);
   const size_t fs = (size_t)g.V * 24;
-  cplx<float> acc[EPT];
+  // per entry: the sum of a tile (S sites x 3 colours, 24 products) is formed in FP32 and
+  // folded into a compensated (Kahan) FP32 accumulator, so that the error of a chunk's sum does
+  // not grow with the number of sites it covers
+  cplx<float> acc[EPT], cmp[EPT];
 #pragma unroll
-  for (int k = 0; k < EPT; ++k) acc[k] = {0.f, 0.f};
+  for (int k = 0; k < EPT; ++k) { acc[k] = {0.f, 0.f}; cmp[k] = {0.f, 0.f}; }
   for (long long b0 = i0; b0 < i1; b0 += S) {
     __syncthreads();
     for (int w = threadIdx.x; w < S * (COUT + CIN); w += 256) {
@@ -152,12 +155,15 @@ __global__ void __launch_bounds__(256) ptnet_dw_kernel(Geom g, const float* __re
       const int e = threadIdx.x + 256 * k;
       if (e < E) {
         const int r = e / (4 * CIN), c = e % (4 * CIN);
-        cplx<float> sacc = acc[k];
+        cplx<float> tile = {0.f, 0.f};
 #pragma unroll
         for (int sl = 0; sl < S; ++sl)
 #pragma unroll
-          for (int a = 0; a < 3; ++a) sacc += cmulc(sx[sl][c][a], sg[sl][r][a]);
-        acc[k] = sacc;
+          for (int a = 0; a < 3; ++a) tile += cmulc(sx[sl][c][a], sg[sl][r][a]);
+        const float yr = tile.re - cmp[k].re, yi = tile.im - cmp[k].im;
+        const float tr = acc[k].re + yr, tq = acc[k].im + yi;
+        cmp[k] = {(tr - acc[k].re) - yr, (tq - acc[k].im) - yi};
+        acc[k] = {tr, tq};
       }
     }
   }

@@ -267,6 +267,7 @@ static void put_cplx(std::vector<char>& buf, int prec, size_t V, size_t field_of
 static void free_ctx(dw_ctx* c) {
   if (!c) return;
   sap_graphs_free(c);
+  for (auto& a : c->ws_solve) a.release();
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   void* ptrs[] = {c->d_canon_of, c->d_nbtab, c->d_blk_nb, c->d_blk_x0, c->d_loc, c->d_colour_list,
                   c->links[0], c->links[1], c->clov[0], c->clov[1], c->clovinv[0], c->clovinv[1],

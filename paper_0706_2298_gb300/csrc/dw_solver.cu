@@ -105,21 +105,20 @@ int read_host(dw_ctx* c, const double* dev, int n, double* host, cudaStream_t s)
   return DW_OK;
 }
 
+// Views of a solver's fields in the context's workspace arena: the first solve of a shape
+// allocates them, later solves of the same shape reuse them (no cudaMalloc/cudaFree per solve).
 template <typename T>
 struct Work {
   std::vector<T*> xi, chi;
   T *rho = nullptr, *w = nullptr, *t1 = nullptr, *lc = nullptr, *lv = nullptr;
   double *eta = nullptr, *psi = nullptr, *r64 = nullptr, *t64 = nullptr, *c64 = nullptr, *v64 = nullptr;
   dd *dda = nullptr, *ddb = nullptr;     // double-float fields of the mixed restarts
-  std::vector<void*> owned;
+  WsArena& arena;
+  explicit Work(WsArena& a) : arena(a) { arena.rewind(); }
   int alloc(size_t bytes, void** p) {
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = arena.get(bytes, p);
     if (e != cudaSuccess) return dw_cuda_fail(e, "gcr_solve workspace");
-    owned.push_back(*p);
     return DW_OK;
-  }
-  ~Work() {
-    for (void* p : owned) cudaFree(p);
   }
 };
 
@@ -132,7 +131,7 @@ int solve_one(dw_ctx* c, dfl_ctx* d, const sol_params* p, const double* eta_cano
   const size_t fbT = dw_field_bytes(c, P), fb64 = dw_field_bytes(c, DW_F64);
   const int nkv = p->nkv;
   const int Nl = d ? dfl_nlittle(d) : 0;
-  Work<T> W;
+  Work<T> W(c->ws_solve[0]);
   int rc;
   W.xi.resize(nkv);
   W.chi.resize(nkv);
@@ -331,7 +330,7 @@ int solve_batch_f32(dw_ctx* c, dfl_ctx* d, const sol_params* p, int nrhs, const 
   const size_t fb32 = dw_field_bytes(c, DW_F32) * nrhs, fb64 = dw_field_bytes(c, DW_F64) * nrhs;
   const int nkv = p->nkv;
   const int Nl = d ? dfl_nlittle(d) : 0;
-  Work<float> W;
+  Work<float> W(c->ws_solve[1]);
   int rc;
   W.xi.resize(nkv);
   W.chi.resize(nkv);
@@ -602,7 +601,7 @@ extern "C" int cgnr_solve(dw_ctx* c, double tol, int maxit, const double* eta_ca
   if (int rc = dw_check_device(c, "cgnr_solve")) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t V = c->V, n = V * 12, fb = dw_field_bytes(c, DW_F64);
-  Work<double> W;
+  Work<double> W(c->ws_solve[2]);
   double *b, *x, *r, *p, *q, *t;
   int rc;
   if ((rc = W.alloc(fb, (void**)&b)) || (rc = W.alloc(fb, (void**)&x)) || (rc = W.alloc(fb, (void**)&r)) ||

@@ -84,6 +84,8 @@ _SIGNATURES = {
     "little_apply": (C.c_int, [_P, _P, _P, _P]),
     "little_dirac_solve": (C.c_int, [_P, C.c_int, _P, _P, C.c_double, C.c_int, C.POINTER(C.c_int),
                                      C.POINTER(C.c_double), _P]),
+    "little_dirac_solve_batch": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_double, C.c_int, C.POINTER(C.c_int),
+                                           C.POINTER(C.c_double), _P]),
     "gcr_solve": (C.c_int, [_P, _P, C.POINTER(SolParams), C.c_int, _P, _P, C.POINTER(SolInfo), _P]),
     "dw_autotune": (C.c_int, [_P, C.c_int, C.c_char_p, C.c_size_t]),
     "cgnr_solve": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.POINTER(C.c_int), C.POINTER(C.c_double), _P]),
@@ -264,6 +266,13 @@ def little_dirac_solve(d: Dfl, prec, w_dev, v_dev, tol, maxit, stream=None):
     rc = _check(lib().little_dirac_solve(d.handle, prec, _ptr(w_dev), _ptr(v_dev), float(tol), int(maxit),
                                          C.byref(it), C.byref(rr), _stream(stream)), ok=(DW_OK, DW_ENOTCONV))
     return rc, it.value, rr.value
+
+
+def little_dirac_solve_batch(d: Dfl, prec, nrhs, w_dev, v_dev, tol, maxit, stream=None):
+    it, rr = (C.c_int * nrhs)(), (C.c_double * nrhs)()
+    rc = _check(lib().little_dirac_solve_batch(d.handle, prec, int(nrhs), _ptr(w_dev), _ptr(v_dev), float(tol),
+                                               int(maxit), it, rr, _stream(stream)), ok=(DW_OK, DW_ENOTCONV))
+    return rc, list(it), list(rr)
 
 
 def sol_params(tol=1e-10, nkv=16, nmx=2000, ncy=4, nmr=4, mixed=1, inner_rtol=1e-5, little_tol_out=1e-12,

@@ -19,3 +19,6 @@ def test_reference_arm_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
     assert line["e2e"]["value"] == line["value"] and line["e2e"]["h2d_bytes_per_step"] == 0
     assert line["config"]["workload"] == "8^4"
+    sys.path.insert(0, ROOT)
+    import bench
+    assert line["metric"] == bench.METRIC          # the two arms print the same metric
