@@ -147,6 +147,15 @@ typedef struct {
   int net_channels;          /* 16 */
   int net_k0;                /* plain steps before the network */
   double net_judge;          /* e.g. 0.95 */
+  /* bootstrapped generation (Section 5.3): after the n_inv plain steps, boot_steps further steps
+   * psi_l <- chi_l / ||chi_l|| with D chi_l = psi_l solved approximately by the mixed-precision
+   * DFL+SAP+GCR solver deflated by the block subspace of the current fields (relative tolerance
+   * boot_tol, at most boot_nmx GCR steps; the Ns fields as one batch).  0: plain procedure only.
+   * The generation runs with the context's operator; the paper recommends a bare mass close to the
+   * critical one for it -- build on such a context and move the subspace with dfl_retarget. */
+  int boot_steps;
+  double boot_tol;           /* e.g. 1e-2 */
+  int boot_nmx;              /* e.g. 16 */
 } dfl_params;
 
 typedef struct {
@@ -158,6 +167,9 @@ typedef struct {
   int learned_used;        /* 1: the network output was accepted */
   double rho_in;           /* mean ||D psi||/||psi|| at the network input (after net_k0 steps) */
   double rho_out;          /* ... of the network output (or of the fields after the plain fallback) */
+  int boot_steps;          /* bootstrapped steps done */
+  int boot_gcr_steps;      /* GCR steps of their approximate solves, summed over steps and fields */
+  int little_loaded;       /* dfl_load: 1 if the stored little operator was used (same operator) */
 } dfl_info;
 
 /* Build the deflation subspace (Sections 4.2, 5.3) and the little Dirac
@@ -173,6 +185,20 @@ int deflation_build(dw_ctx* ctx, const dfl_params* p, const double* start_canon_
                     dfl_ctx** out, dfl_info* info);
 void dfl_destroy(dfl_ctx* d);
 int dfl_dims(const dfl_ctx* d, int* Nb, int* Ns);
+
+/* Subspace reuse (Section 6.4, remark 1: one deflation subspace serves all valence masses): a new
+ * deflation context on operator ctx (same lattice and Schwarz blocks as the operator src was built
+ * on; another bare mass, c_sw or gauge field) with the basis and global-mode data of src, its own
+ * little operator (A.1) and A.2/A.3 data.  Synchronous; may return DW_ILLCOND like deflation_build. */
+int dfl_retarget(const dfl_ctx* src, dw_ctx* ctx, dfl_ctx** out, dfl_info* info);
+/* Checkpoint of a deflation subspace: lattice, block sizes, Ns, the stored basis (BF16 or FP64),
+ * the global-mode restriction coefficients (A.3) and the FP64 little operator with the identity
+ * of the operator it belongs to (gauge-field hash, m0, c_sw).  Binary file, host byte order.
+ * dfl_load rebuilds the context on ctx: the stored little operator is used when ctx is the same
+ * operator (info->little_loaded = 1), otherwise it is assembled anew.  DW_EINVAL on I/O errors or
+ * a lattice/block mismatch.  Synchronous. */
+int dfl_save(const dfl_ctx* d, const char* path);
+int dfl_load(dw_ctx* ctx, const char* path, dfl_ctx** out, dfl_info* info);
 
 /* Little vectors: complex[Nb][Ns] (re, im interleaved) of precision prec,
  * block index = lexicographic deflation-block coordinate (x0 slowest).
@@ -207,7 +233,7 @@ typedef struct {
   double tol;              /* stop when ||eta - D psi|| <= tol ||eta|| (FP64 residual) */
   int nkv;                 /* Krylov vectors per GCR cycle (restart length) */
   int nmx;                 /* maximum total GCR steps */
-  int ncy, nmr;            /* M_sap parameters */
+  int ncy, nmr;            /* M_sap parameters; ncy = 0: no preconditioner (M = 1), i.e. plain GCR */
   int mixed;               /* 1: FP32 D/SAP/little, FP64-class restarts (double-float D, restriction
                               and prolongation, FP64-refined little solves); 0: everything FP64 */
   double inner_rtol;       /* mixed: end a cycle when its residual drops by this factor */

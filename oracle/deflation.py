@@ -10,6 +10,8 @@
 * (5.1)  inverse iteration psi_l <- "D^-1" psi_l, the inverse replaced by
          M_sap (Section 5.3); normalised after every step [reading: the
          paper leaves the normalisation open; it only fixes the scale]
+* (5.1) bootstrapped (Section 5.3): later steps replace "D^-1" by the
+         deflated solver built on the current fields, stopped early
 * (A.1)  B_{LL'} = (phi^L_k, D phi^{L'}_l), nonzero for L' = L or a neighbour
 
 Basis layout: ``phi[L, l, s, spin, colour]`` with ``s`` the site within
@@ -168,3 +170,24 @@ def build_subspace(D: WilsonClover, sap_bs, dfl_bs, start, n_inv, ncy, nmr, bf16
     if bf16:
         phi = round_bf16(phi)
     return BlockSubspace(D, dfl_bs, phi, fields)
+
+
+def bootstrap_iteration(D: WilsonClover, sap_bs, dfl_bs, fields: np.ndarray, n_boot: int, tol: float,
+                        ncy: int = 4, nmr: int = 4, nkv: int = 16):
+    """The bootstrapped steps of the subspace generation (Section 5.3): n_boot times, the block
+    subspace of the current fields (restriction and Gram-Schmidt (4.2), little operator (A.1),
+    even-odd little system with global-mode deflation (A.2)-(A.3)) deflates the Dirac equation,
+    D chi_l = psi_l is solved by DFL+SAP+GCR (Section 6) to ||psi_l - D chi_l|| <= tol ||psi_l||,
+    and psi_l <- chi_l / ||chi_l||.  With tol -> 0 every step is exact inverse iteration."""
+    from .little import EOLittle
+    from .solver import solve_dfl_sap
+    sap = SchwarzOracle(D, sap_bs)
+    out = np.array(fields, dtype=np.complex128, copy=True)
+    for _ in range(n_boot):
+        phi = block_gram_schmidt(Blocking(D.L, dfl_bs), out)
+        sub = BlockSubspace(D, dfl_bs, phi, out)
+        little = EOLittle(sub)
+        for l in range(out.shape[0]):
+            chi, _ = solve_dfl_sap(D, sap, sub, little, out[l], tol=tol, nkv=nkv, ncy=ncy, nmr=nmr)
+            out[l] = chi / norm(chi)
+    return out

@@ -325,6 +325,7 @@ struct WsArena {
 struct dw_ctx {
   dw_params p;
   int device = -1;             // CUDA device the context's memory lives on (current device at dw_create)
+  uint64_t gauge_hash = 0;     // FNV-1a hash of the links given to dw_create (identifies the gauge field)
   Geom g;                      // device pointers filled in
   long long V;
   int nsb[4];

@@ -24,6 +24,8 @@
 #include <cmath>
 #include <complex>
 #include <cooperative_groups.h>
+#include <cstdio>
+#include <cstring>
 #include <type_traits>
 
 #include "dw_common.cuh"
@@ -62,6 +64,8 @@ struct dfl_ctx {
   double* g64 = nullptr; float* g32 = nullptr;         // [Ns][Ne*Ns]
   double* Bg64 = nullptr; float* Bg32 = nullptr;       // B^ g
   std::vector<cd> Atil_inv;                            // Ns x Ns row-major
+  std::vector<int> hlist0;                             // even blocks (host copy of d_list[0])
+  std::vector<cd> graw;                                // [Ns][Ne*Ns] (phi^L_k, psi_l) on even blocks (A.3 input)
   double* Ainv64 = nullptr; float* Ainv32 = nullptr;   // device copies of A~^{-1}
   int coop_grid = 0;                                   // CTAs of the cooperative little solver (0: not possible)
   bool coop_m = false;                                 // multi-RHS cooperative little solver available
@@ -219,6 +223,21 @@ __global__ void quantize_kernel(size_t V, int Ns, double* b64, uint4* b16) {
       z = {(double)f.x, (double)f.y};
     }
     b16[((size_t)l * 3 + u) * V + i] = q;
+  }
+  store_site<double, 12>(b64 + (size_t)l * 24 * V, V, i, a);
+}
+
+// b64 = the BF16 basis b16 in FP64 (inverse of the storage step of quantize_kernel)
+__global__ void dequantize_kernel(size_t V, int Ns, const uint4* __restrict__ b16, double* b64) {
+  size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= V * Ns) return;
+  int l = (int)(t / V);
+  size_t i = t % V;
+  cplx<double> a[12];
+  for (int u = 0; u < 3; ++u) {
+    cplx<float> c4[4];
+    bf16_unpack4(b16[((size_t)l * 3 + u) * V + i], c4);
+    for (int j = 0; j < 4; ++j) a[4 * u + j] = {(double)c4[j].re, (double)c4[j].im};
   }
   store_site<double, 12>(b64 + (size_t)l * 24 * V, V, i, a);
 }
@@ -2493,12 +2512,10 @@ extern "C" int little_dirac_solve_batch(dfl_ctx* d, int prec, int nrhs, const vo
 }
 
 // ---------------------------------------------------------------------- build
-static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_ctx* d, dfl_info* info) {
+// Block tables of the deflation blocks (neighbours, Schwarz blocks of each block, parity lists
+// and neighbour positions) on the device; the host keeps the even-block list.
+static int build_tables(dw_ctx* c, dfl_ctx* d) {
   const Geom& g = c->g;
-  const size_t V = c->V;
-  const int Ns = p->Ns;
-  cudaStream_t s = 0;
-  auto t0 = std::chrono::steady_clock::now();
   // ---- tables
   std::vector<int> bcoord((size_t)d->Nb * 4), sap2dfl(g.nsap), sub((size_t)d->Nb * d->nsub, -1), fill(d->Nb, 0),
       bnb((size_t)d->Nb * 8);
@@ -2545,113 +2562,30 @@ static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_c
       (rc = up(&d->d_lnb[1], lnb[1])))
     return rc;
 
-  // ---- inverse iteration (5.1) in the requested precision
-  const int ip = p->iter_prec == DW_F64 ? DW_F64 : DW_F32;
-  const size_t fb = dw_field_bytes(c, ip);
-  void* work = nullptr;
-  void* tmp = nullptr;
-  DW_CUDA(cudaMalloc(&work, fb * Ns));
-  DW_CUDA(cudaMalloc(&tmp, fb));
-  struct Free { void* a; void* b; ~Free() { if (a) cudaFree(a); if (b) cudaFree(b); } } guard{work, tmp};
-  if ((rc = dw_pack(c, ip, Ns, start, work, s))) return rc;
-  const size_t n = V * 12;
-  std::vector<double> h(3);
-  const bool use_net = p->net_weights != nullptr;
-  if (use_net && (ip != DW_F32 || p->net_channels != 16 || p->net_k0 < 0 || p->net_k0 > p->n_inv)) {
-    dw_set_error("deflation_build: the network needs iter_prec DW_F32, 16 channels and 0 <= net_k0 <= n_inv");
-    return DW_EINVAL;
-  }
-  // mean ||D psi_l|| / ||psi_l|| of the FP32 work fields, the relaxation measure of (5.2)
-  auto rho_measure = [&](const float* fields, double* out) -> int {
-    double sum = 0;
-    for (int l = 0; l < Ns; ++l) {
-      const float* f = fields + (size_t)l * 24 * V;
-      dirac_full<float>(c, f, (float*)tmp, s);
-      blas_dot<float>(c, (float*)tmp, (float*)tmp, n, c->d_red + 65536, s);
-      blas_dot<float>(c, f, f, n, c->d_red + 65536 + 3, s);
-      double hh[6];
-      int e = sync_read(c, c->d_red + 65536, 6, hh, s);
-      if (e) return e;
-      sum += sqrt(hh[2] / hh[5]);
-    }
-    *out = sum / Ns;
-    return DW_OK;
-  };
-  int learned = 0;
-  double rho_in = 0, rho_out = 0;
-  const int n_first = use_net ? p->net_k0 : p->n_inv;
-  for (int it = 0; it < n_first; ++it)
-    for (int l = 0; l < Ns; ++l) {
-      if (ip == DW_F64) {
-        double* w = (double*)work + (size_t)l * 24 * V;
-        if ((rc = sap_apply<double>(c, p->ncy, p->nmr, w, (double*)tmp, s))) return rc;
-        blas_dot<double>(c, (double*)tmp, (double*)tmp, n, c->d_red + 65536, s);
-        if ((rc = sync_read(c, c->d_red + 65536, 3, h.data(), s))) return rc;
-        blas_convert<double, double>((double*)tmp, w, 1.0 / sqrt(h[2]), n, s);
-      } else {
-        float* w = (float*)work + (size_t)l * 24 * V;
-        if ((rc = sap_apply<float>(c, p->ncy, p->nmr, w, (float*)tmp, s))) return rc;
-        blas_dot<float>(c, (float*)tmp, (float*)tmp, n, c->d_red + 65536, s);
-        if ((rc = sync_read(c, c->d_red + 65536, 3, h.data(), s))) return rc;
-        blas_convert<float, float>((float*)tmp, w, 1.0 / sqrt(h[2]), n, s);
-      }
-    }
-  if (use_net) {
-    // learned generation: network on the fields after net_k0 plain steps, judged by (5.2)
-    if ((rc = rho_measure((const float*)work, &rho_in))) return rc;
-    float* out = nullptr;
-    DW_CUDA(cudaMalloc(&out, fb * Ns));
-    struct F1 { void* p; ~F1() { if (p) cudaFree(p); } } g2{out};
-    if ((rc = ptnet_forward(c, p->net_channels, p->net_weights, Ns, work, out, s))) return rc;
-    for (int l = 0; l < Ns; ++l) {
-      float* f = out + (size_t)l * 24 * V;
-      blas_dot<float>(c, f, f, n, c->d_red + 65536, s);
-      if ((rc = sync_read(c, c->d_red + 65536, 3, h.data(), s))) return rc;
-      blas_scale<float>(f, h[2] > 0 ? 1.0 / sqrt(h[2]) : 0.0, 0.0, n, s);
-    }
-    if ((rc = rho_measure(out, &rho_out))) return rc;
-    if (std::isfinite(rho_out) && rho_out <= p->net_judge * rho_in) {
-      learned = 1;
-      DW_CUDA(cudaMemcpyAsync(work, out, fb * Ns, cudaMemcpyDeviceToDevice, s));
-    } else {
-      // fallback: the plain procedure finishes the generation
-      for (int it = p->net_k0; it < p->n_inv; ++it)
-        for (int l = 0; l < Ns; ++l) {
-          float* w = (float*)work + (size_t)l * 24 * V;
-          if ((rc = sap_apply<float>(c, p->ncy, p->nmr, w, (float*)tmp, s))) return rc;
-          blas_dot<float>(c, (float*)tmp, (float*)tmp, n, c->d_red + 65536, s);
-          if ((rc = sync_read(c, c->d_red + 65536, 3, h.data(), s))) return rc;
-          blas_convert<float, float>((float*)tmp, w, 1.0 / sqrt(h[2]), n, s);
-        }
-      if ((rc = rho_measure((const float*)work, &rho_out))) return rc;
-    }
-  }
-  // ---- block Gram-Schmidt in FP64
-  DW_CUDA(cudaMalloc(&d->basis64, (size_t)Ns * 24 * V * sizeof(double)));
-  if (ip == DW_F64) DW_CUDA(cudaMemcpyAsync(d->basis64, work, fb * Ns, cudaMemcpyDeviceToDevice, s));
-  else
-    for (int l = 0; l < Ns; ++l)
-      field_convert<float, double>((const float*)work + (size_t)l * 24 * V, d->basis64 + (size_t)l * 24 * V, 1.0,
-                                   V, s);
-  int* d_flag = (int*)(c->d_count + 40);
-  DW_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), s));
-  block_gs_kernel<<<d->Nb, 256, 0, s>>>(g, d->d_sub, d->nsub, Ns, d->basis64, d_flag); dw_note_launch();
-  int flag = 0;
-  DW_CUDA(cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-  DW_CUDA(cudaStreamSynchronize(s));
-  if (flag) { dw_set_error("deflation_build: rank loss in the block Gram-Schmidt"); return DW_EINVAL; }
-  if (p->basis_prec == DW_BF16) {
-    DW_CUDA(cudaMalloc(&d->basis16, (size_t)Ns * 3 * V * sizeof(uint4)));
-    size_t tot = V * Ns;
-    quantize_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(V, Ns, d->basis64, d->basis16); dw_note_launch();
-  }
-  auto t1 = std::chrono::steady_clock::now();
+  d->hlist0 = list[0];
+  return DW_OK;
+}
+
+// Little Dirac operator (A.1) of the operator of c on the basis held in d (basis64, and basis16 when
+// stored in BF16): assembly in FP64 (or the given host copy B64_given), diagonal-block inverses with
+// the condition check (A.2), B_LL^{-1} B_LL' products, global-mode deflation (A.3) from the
+// restriction coefficients d->graw, and the set-up of the cooperative little solvers.
+static int little_setup(dw_ctx* c, dfl_ctx* d, const double* B64_given) {
+  const Geom& g = c->g;
+  const int Ns = d->Ns;
+  const dfl_params* p = &d->p;
+  cudaStream_t s = 0;
+  int rc;
   // ---- little operator (A.1) from the stored basis, FP64
   const size_t mat = (size_t)Ns * Ns * 2;
   DW_CUDA(cudaMalloc(&d->B64, d->Nb * 9 * mat * sizeof(double)));
-  assemble_kernel<<<(unsigned)(d->Nb * 9 * Ns), 128, 0, s>>>(g, d->d_sub, d->nsub, d->d_sap2dfl, Ns,
-                                                            (const double*)c->links[DW_F64],
-                                                            (const double*)c->clov[DW_F64], d->basis64, d->B64); dw_note_launch();
+  if (B64_given) {
+    DW_CUDA(cudaMemcpy(d->B64, B64_given, d->Nb * 9 * mat * sizeof(double), cudaMemcpyHostToDevice));
+  } else {
+    assemble_kernel<<<(unsigned)(d->Nb * 9 * Ns), 128, 0, s>>>(g, d->d_sub, d->nsub, d->d_sap2dfl, Ns,
+                                                              (const double*)c->links[DW_F64],
+                                                              (const double*)c->clov[DW_F64], d->basis64, d->B64); dw_note_launch();
+  }
   DW_CUDA(cudaGetLastError());
   DW_CUDA(cudaMalloc(&d->B32, d->Nb * 9 * mat * sizeof(float)));
   blas_convert<double, float>(d->B64, d->B32, 1.0, (size_t)d->Nb * 9 * Ns * Ns, s);
@@ -2675,33 +2609,9 @@ static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_c
 
   // ---- global-mode deflation (A.3): g_l = even-block part of Phi^+ psi_l, orthonormalised
   d->a3 = false;
-  if (!d->illcond) {
+  if (!d->illcond && d->graw.size() == (size_t)Ns * d->Ne * Ns) {
     const size_t ne = (size_t)d->Ne * Ns;
-    std::vector<cd> G((size_t)Ns * ne);
-    double* cfull;
-    DW_CUDA(cudaMalloc(&cfull, (size_t)d->N * 2 * sizeof(double)));
-    double* f64 = nullptr;
-    if (ip == DW_F32) DW_CUDA(cudaMalloc(&f64, fb * 2));
-    std::vector<double> hc((size_t)d->N * 2);
-    for (int l = 0; l < Ns; ++l) {
-      const double* src;
-      if (ip == DW_F64) src = (const double*)work + (size_t)l * 24 * V;
-      else {
-        field_convert<float, double>((const float*)work + (size_t)l * 24 * V, f64, 1.0, V, s);
-        src = f64;
-      }
-      restrict_kernel<double><<<d->Nb, 128, 0, s>>>(g, d->d_sub, d->nsub, Ns, d->basis64, nullptr, src, cfull, 1,
-                                                    0, 0); dw_note_launch();
-      DW_CUDA(cudaMemcpyAsync(hc.data(), cfull, hc.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-      DW_CUDA(cudaStreamSynchronize(s));
-      for (int i = 0; i < d->Ne; ++i)
-        for (int k = 0; k < Ns; ++k) {
-          size_t o = ((size_t)list[0][i] * Ns + k) * 2;
-          G[(size_t)l * ne + (size_t)i * Ns + k] = cd(hc[o], hc[o + 1]);
-        }
-    }
-    cudaFree(cfull);
-    if (f64) cudaFree(f64);
+    std::vector<cd> G = d->graw;
     // modified Gram-Schmidt with re-orthogonalisation (host, FP64)
     bool ok = true;
     for (int l = 0; l < Ns && ok; ++l) {
@@ -2811,6 +2721,213 @@ static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_c
     }
     if ((rc = ensure_little_work(d, DW_F64, COOP_NKV))) return rc;
   }
+  return DW_OK;
+}
+
+// The bootstrapped steps of the subspace generation (Section 5.3): the Ns fields (packed, precision ip,
+// in `work`) are replaced boot_steps times by approximate solutions of D chi_l = psi_l, normalised; each
+// approximate solve is the mixed-precision DFL+SAP+GCR solver deflated by the block subspace of the
+// current fields (built without further inverse iteration), stopped at ||psi_l - D chi_l|| <=
+// boot_tol ||psi_l|| or after boot_nmx GCR steps, the Ns fields in one batch.
+static int bootstrap_steps(dw_ctx* c, const dfl_params* p, void* work, int ip, int* steps_done, int* gcr_total) {
+  const size_t V = c->V, n = V * 12, fs = V * 24;
+  const int Ns = p->Ns;
+  cudaStream_t s = 0;
+  double *canon = nullptr, *sol = nullptr;
+  DW_CUDA(cudaMalloc(&canon, (size_t)Ns * fs * sizeof(double)));
+  DW_CUDA(cudaMalloc(&sol, (size_t)Ns * fs * sizeof(double)));
+  struct Free { void* a; void* b; ~Free() { cudaFree(a); cudaFree(b); } } guard{canon, sol};
+  dfl_params q = *p;
+  q.n_inv = 0;
+  q.boot_steps = 0;
+  q.net_weights = nullptr;
+  q.basis_prec = DW_BF16;
+  sol_params sp{};
+  sp.tol = p->boot_tol;
+  sp.nkv = 16;
+  sp.nmx = p->boot_nmx > 0 ? p->boot_nmx : 1000;
+  sp.ncy = p->ncy;
+  sp.nmr = p->nmr;
+  sp.mixed = 1;
+  sp.inner_rtol = 1e-5;
+  sp.little_tol_out = 1e-12;
+  sp.little_tol_in = 1e-6;
+  sp.little_tol_cap = 1e-1;
+  sp.little_nkv = 24;
+  sp.little_maxit = 2000;
+  std::vector<sol_info> inf(Ns);
+  double* dres = c->d_red + 65536 + 20480;
+  int rc;
+  for (int step = 0; step < p->boot_steps; ++step) {
+    if ((rc = dw_unpack(c, ip, Ns, work, canon, s))) return rc;
+    dfl_ctx* dt = nullptr;
+    rc = deflation_build(c, &q, canon, &dt, nullptr);
+    if (rc < 0) return rc;
+    rc = gcr_solve(c, dt, &sp, Ns, canon, sol, inf.data(), s);
+    dfl_destroy(dt);
+    if (rc < 0) return rc;
+    for (int l = 0; l < Ns; ++l) {
+      *gcr_total += inf[l].iterations;
+      blas_dot<double>(c, sol + (size_t)l * fs, sol + (size_t)l * fs, n, dres + 3 * l, s);
+    }
+    std::vector<double> h(3 * Ns);
+    if ((rc = sync_read(c, dres, 3 * Ns, h.data(), s))) return rc;
+    for (int l = 0; l < Ns; ++l)
+      blas_scale<double>(sol + (size_t)l * fs, h[3 * l + 2] > 0 ? 1.0 / sqrt(h[3 * l + 2]) : 0.0, 0.0, n, s);
+    if ((rc = dw_pack(c, ip, Ns, sol, work, s))) return rc;
+    ++*steps_done;
+  }
+  DW_CUDA(cudaStreamSynchronize(s));
+  return DW_OK;
+}
+
+static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_ctx* d, dfl_info* info) {
+  const Geom& g = c->g;
+  const size_t V = c->V;
+  const int Ns = p->Ns;
+  cudaStream_t s = 0;
+  auto t0 = std::chrono::steady_clock::now();
+  int rc;
+  if ((rc = build_tables(c, d))) return rc;
+
+  // ---- inverse iteration (5.1) in the requested precision
+  const int ip = p->iter_prec == DW_F64 ? DW_F64 : DW_F32;
+  const size_t fb = dw_field_bytes(c, ip);
+  void* work = nullptr;
+  void* tmp = nullptr;
+  DW_CUDA(cudaMalloc(&work, fb * Ns));
+  DW_CUDA(cudaMalloc(&tmp, fb));
+  struct Free { void* a; void* b; ~Free() { if (a) cudaFree(a); if (b) cudaFree(b); } } guard{work, tmp};
+  if ((rc = dw_pack(c, ip, Ns, start, work, s))) return rc;
+  const size_t n = V * 12;
+  std::vector<double> h(3);
+  const bool use_net = p->net_weights != nullptr;
+  if (use_net && (ip != DW_F32 || p->net_channels != 16 || p->net_k0 < 0 || p->net_k0 > p->n_inv)) {
+    dw_set_error("deflation_build: the network needs iter_prec DW_F32, 16 channels and 0 <= net_k0 <= n_inv");
+    return DW_EINVAL;
+  }
+  // mean ||D psi_l|| / ||psi_l|| of the FP32 work fields, the relaxation measure of (5.2)
+  auto rho_measure = [&](const float* fields, double* out) -> int {
+    double sum = 0;
+    for (int l = 0; l < Ns; ++l) {
+      const float* f = fields + (size_t)l * 24 * V;
+      dirac_full<float>(c, f, (float*)tmp, s);
+      blas_dot<float>(c, (float*)tmp, (float*)tmp, n, c->d_red + 65536, s);
+      blas_dot<float>(c, f, f, n, c->d_red + 65536 + 3, s);
+      double hh[6];
+      int e = sync_read(c, c->d_red + 65536, 6, hh, s);
+      if (e) return e;
+      sum += sqrt(hh[2] / hh[5]);
+    }
+    *out = sum / Ns;
+    return DW_OK;
+  };
+  int learned = 0;
+  double rho_in = 0, rho_out = 0;
+  const int n_first = use_net ? p->net_k0 : p->n_inv;
+  for (int it = 0; it < n_first; ++it)
+    for (int l = 0; l < Ns; ++l) {
+      if (ip == DW_F64) {
+        double* w = (double*)work + (size_t)l * 24 * V;
+        if ((rc = sap_apply<double>(c, p->ncy, p->nmr, w, (double*)tmp, s))) return rc;
+        blas_dot<double>(c, (double*)tmp, (double*)tmp, n, c->d_red + 65536, s);
+        if ((rc = sync_read(c, c->d_red + 65536, 3, h.data(), s))) return rc;
+        blas_convert<double, double>((double*)tmp, w, 1.0 / sqrt(h[2]), n, s);
+      } else {
+        float* w = (float*)work + (size_t)l * 24 * V;
+        if ((rc = sap_apply<float>(c, p->ncy, p->nmr, w, (float*)tmp, s))) return rc;
+        blas_dot<float>(c, (float*)tmp, (float*)tmp, n, c->d_red + 65536, s);
+        if ((rc = sync_read(c, c->d_red + 65536, 3, h.data(), s))) return rc;
+        blas_convert<float, float>((float*)tmp, w, 1.0 / sqrt(h[2]), n, s);
+      }
+    }
+  if (use_net) {
+    // learned generation: network on the fields after net_k0 plain steps, judged by (5.2)
+    if ((rc = rho_measure((const float*)work, &rho_in))) return rc;
+    float* out = nullptr;
+    DW_CUDA(cudaMalloc(&out, fb * Ns));
+    struct F1 { void* p; ~F1() { if (p) cudaFree(p); } } g2{out};
+    if ((rc = ptnet_forward(c, p->net_channels, p->net_weights, Ns, work, out, s))) return rc;
+    for (int l = 0; l < Ns; ++l) {
+      float* f = out + (size_t)l * 24 * V;
+      blas_dot<float>(c, f, f, n, c->d_red + 65536, s);
+      if ((rc = sync_read(c, c->d_red + 65536, 3, h.data(), s))) return rc;
+      blas_scale<float>(f, h[2] > 0 ? 1.0 / sqrt(h[2]) : 0.0, 0.0, n, s);
+    }
+    if ((rc = rho_measure(out, &rho_out))) return rc;
+    if (std::isfinite(rho_out) && rho_out <= p->net_judge * rho_in) {
+      learned = 1;
+      DW_CUDA(cudaMemcpyAsync(work, out, fb * Ns, cudaMemcpyDeviceToDevice, s));
+    } else {
+      // fallback: the plain procedure finishes the generation
+      for (int it = p->net_k0; it < p->n_inv; ++it)
+        for (int l = 0; l < Ns; ++l) {
+          float* w = (float*)work + (size_t)l * 24 * V;
+          if ((rc = sap_apply<float>(c, p->ncy, p->nmr, w, (float*)tmp, s))) return rc;
+          blas_dot<float>(c, (float*)tmp, (float*)tmp, n, c->d_red + 65536, s);
+          if ((rc = sync_read(c, c->d_red + 65536, 3, h.data(), s))) return rc;
+          blas_convert<float, float>((float*)tmp, w, 1.0 / sqrt(h[2]), n, s);
+        }
+      if ((rc = rho_measure((const float*)work, &rho_out))) return rc;
+    }
+  }
+  // ---- bootstrapped inverse iteration (Section 5.3): after the plain steps, boot_steps further
+  // steps psi_l <- "D^{-1}" psi_l in which D^{-1} is the deflated SAP-GCR solver on the subspace of
+  // the current fields, stopped at the loose relative tolerance boot_tol (or boot_nmx GCR steps)
+  int boot_steps_done = 0, boot_gcr = 0;
+  if (p->boot_steps > 0) {
+    if ((rc = bootstrap_steps(c, p, work, ip, &boot_steps_done, &boot_gcr))) return rc;
+  }
+  // ---- block Gram-Schmidt in FP64
+  DW_CUDA(cudaMalloc(&d->basis64, (size_t)Ns * 24 * V * sizeof(double)));
+  if (ip == DW_F64) DW_CUDA(cudaMemcpyAsync(d->basis64, work, fb * Ns, cudaMemcpyDeviceToDevice, s));
+  else
+    for (int l = 0; l < Ns; ++l)
+      field_convert<float, double>((const float*)work + (size_t)l * 24 * V, d->basis64 + (size_t)l * 24 * V, 1.0,
+                                   V, s);
+  int* d_flag = (int*)(c->d_count + 40);
+  DW_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), s));
+  block_gs_kernel<<<d->Nb, 256, 0, s>>>(g, d->d_sub, d->nsub, Ns, d->basis64, d_flag); dw_note_launch();
+  int flag = 0;
+  DW_CUDA(cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DW_CUDA(cudaStreamSynchronize(s));
+  if (flag) { dw_set_error("deflation_build: rank loss in the block Gram-Schmidt"); return DW_EINVAL; }
+  if (p->basis_prec == DW_BF16) {
+    DW_CUDA(cudaMalloc(&d->basis16, (size_t)Ns * 3 * V * sizeof(uint4)));
+    size_t tot = V * Ns;
+    quantize_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(V, Ns, d->basis64, d->basis16); dw_note_launch();
+  }
+  // ---- A.3 input: restriction coefficients (phi^L_k, psi_l) of the generated fields on the even blocks
+  {
+    const size_t ne = (size_t)d->Ne * Ns;
+    d->graw.assign((size_t)Ns * ne, cd(0.0, 0.0));
+    double* cfull;
+    DW_CUDA(cudaMalloc(&cfull, (size_t)d->N * 2 * sizeof(double)));
+    double* f64 = nullptr;
+    if (ip == DW_F32) DW_CUDA(cudaMalloc(&f64, fb * 2));
+    std::vector<double> hc((size_t)d->N * 2);
+    for (int l = 0; l < Ns; ++l) {
+      const double* src;
+      if (ip == DW_F64) src = (const double*)work + (size_t)l * 24 * V;
+      else {
+        field_convert<float, double>((const float*)work + (size_t)l * 24 * V, f64, 1.0, V, s);
+        src = f64;
+      }
+      restrict_kernel<double><<<d->Nb, 128, 0, s>>>(g, d->d_sub, d->nsub, Ns, d->basis64, nullptr, src, cfull, 1,
+                                                    0, 0); dw_note_launch();
+      DW_CUDA(cudaMemcpyAsync(hc.data(), cfull, hc.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+      DW_CUDA(cudaStreamSynchronize(s));
+      for (int i = 0; i < d->Ne; ++i)
+        for (int k = 0; k < Ns; ++k) {
+          size_t o = ((size_t)d->hlist0[i] * Ns + k) * 2;
+          d->graw[(size_t)l * ne + (size_t)i * Ns + k] = cd(hc[o], hc[o + 1]);
+        }
+    }
+    cudaFree(cfull);
+    if (f64) cudaFree(f64);
+  }
+  auto t1 = std::chrono::steady_clock::now();
+  if ((rc = little_setup(c, d, nullptr))) return rc;
   auto t2 = std::chrono::steady_clock::now();
   if (info) {
     info->seconds = std::chrono::duration<double>(t2 - t0).count();
@@ -2821,15 +2938,16 @@ static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_c
     info->learned_used = learned;
     info->rho_in = rho_in;
     info->rho_out = rho_out;
+    info->boot_steps = boot_steps_done;
+    info->boot_gcr_steps = boot_gcr;
   }
   return d->illcond ? DW_ILLCOND : DW_OK;
 }
 
-extern "C" int deflation_build(dw_ctx* c, const dfl_params* p, const double* start, dfl_ctx** out, dfl_info* info) {
-  if (!c || !p || !start || !out) { dw_set_error("deflation_build: null argument"); return DW_EINVAL; }
+// a deflation context for operator c with the block geometry of p (validated)
+static int dfl_alloc(dw_ctx* c, const dfl_params* p, dfl_ctx** out) {
   *out = nullptr;
-  if (int rc = dw_check_device(c, "deflation_build")) return rc;
-  if (p->Ns < 1 || p->Ns > NSMAX || p->n_inv < 0 || p->ncy < 0 || p->nmr < 0 ||
+  if (p->Ns < 1 || p->Ns > NSMAX || p->n_inv < 0 || p->ncy < 0 || p->nmr < 0 || p->boot_steps < 0 ||
       (p->basis_prec != DW_BF16 && p->basis_prec != DW_F64)) {
     dw_set_error("deflation_build: Ns must be in 1..32, counts non-negative, basis_prec DW_BF16 or DW_F64");
     return DW_EINVAL;
@@ -2837,6 +2955,7 @@ extern "C" int deflation_build(dw_ctx* c, const dfl_params* p, const double* sta
   dfl_ctx* d = new dfl_ctx();
   d->c = c;
   d->p = *p;
+  d->p.net_weights = nullptr;
   d->Ns = p->Ns;
   d->Nb = 1;
   d->nsub = 1;
@@ -2853,8 +2972,184 @@ extern "C" int deflation_build(dw_ctx* c, const dfl_params* p, const double* sta
     d->nsub *= b / c->g.sb[mu];
   }
   d->N = d->Nb * d->Ns;
-  int rc = build_impl(c, p, start, d, info);
+  *out = d;
+  return DW_OK;
+}
+
+extern "C" int deflation_build(dw_ctx* c, const dfl_params* p, const double* start, dfl_ctx** out, dfl_info* info) {
+  if (!c || !p || !start || !out) { dw_set_error("deflation_build: null argument"); return DW_EINVAL; }
+  *out = nullptr;
+  if (int rc = dw_check_device(c, "deflation_build")) return rc;
+  if (p->boot_steps > 0 && (!(p->boot_tol > 0) || p->boot_nmx < 0)) {
+    dw_set_error("deflation_build: boot_tol must be positive and boot_nmx non-negative");
+    return DW_EINVAL;
+  }
+  dfl_ctx* d = nullptr;
+  int rc = dfl_alloc(c, p, &d);
+  if (rc) return rc;
+  rc = build_impl(c, p, start, d, info);
   if (rc < 0) { dfl_destroy(d); return rc; }
   *out = d;
   return rc;
+}
+
+static bool same_geometry(const dw_ctx* a, const dw_ctx* b) {
+  for (int mu = 0; mu < 4; ++mu)
+    if (a->p.L[mu] != b->p.L[mu] || a->p.sap_bs[mu] != b->p.sap_bs[mu]) return false;
+  return true;
+}
+
+static void fill_info(dfl_ctx* d, dfl_info* info, double secs, double secs_little, int loaded) {
+  if (!info) return;
+  *info = dfl_info{};
+  info->seconds = secs;
+  info->seconds_little = secs_little;
+  info->max_block_cond = d->max_cond;
+  info->Nb = d->Nb;
+  info->N = d->N;
+  info->little_loaded = loaded;
+}
+
+extern "C" int dfl_retarget(const dfl_ctx* src, dw_ctx* c, dfl_ctx** out, dfl_info* info) {
+  if (!src || !c || !out) { dw_set_error("dfl_retarget: null argument"); return DW_EINVAL; }
+  *out = nullptr;
+  if (int rc = dw_check_device(c, "dfl_retarget")) return rc;
+  if (!same_geometry(src->c, c)) {
+    dw_set_error("dfl_retarget: the operator has another lattice or Schwarz block size");
+    return DW_EINVAL;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  dfl_ctx* d = nullptr;
+  int rc = dfl_alloc(c, &src->p, &d);
+  if (rc) return rc;
+  const size_t V = c->V, Ns = d->Ns;
+  auto fail = [&](int r) { dfl_destroy(d); return r; };
+  if ((rc = build_tables(c, d))) return fail(rc);
+  cudaError_t e = cudaMalloc(&d->basis64, Ns * 24 * V * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(d->basis64, src->basis64, Ns * 24 * V * sizeof(double), cudaMemcpyDeviceToDevice);
+  if (e == cudaSuccess && src->basis16) {
+    e = cudaMalloc(&d->basis16, Ns * 3 * V * sizeof(uint4));
+    if (e == cudaSuccess) e = cudaMemcpy(d->basis16, src->basis16, Ns * 3 * V * sizeof(uint4), cudaMemcpyDeviceToDevice);
+  }
+  if (e != cudaSuccess) return fail(dw_cuda_fail(e, "dfl_retarget"));
+  d->graw = src->graw;
+  if ((rc = little_setup(c, d, nullptr))) return fail(rc);
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  fill_info(d, info, secs, secs, 0);
+  *out = d;
+  return d->illcond ? DW_ILLCOND : DW_OK;
+}
+
+// checkpoint file layout: header, basis (BF16 units or FP64 field), A.3 coefficients, FP64 little operator
+struct DflFileHeader {
+  char magic[8];           // "DWDFL01\0"
+  int L[4], sap_bs[4], bs[4];
+  int Ns, basis_prec, antiperiodic, Ne;
+  double m0, csw, cond_max;
+  uint64_t gauge_hash;
+  uint64_t V, n_graw, n_B;
+};
+
+extern "C" int dfl_save(const dfl_ctx* d, const char* path) {
+  if (!d || !path) { dw_set_error("dfl_save: null argument"); return DW_EINVAL; }
+  const dw_ctx* c = d->c;
+  if (int rc = dw_check_device(c, "dfl_save")) return rc;
+  DflFileHeader h{};
+  memcpy(h.magic, "DWDFL01", 8);
+  for (int mu = 0; mu < 4; ++mu) { h.L[mu] = c->p.L[mu]; h.sap_bs[mu] = c->p.sap_bs[mu]; h.bs[mu] = d->bs[mu]; }
+  h.Ns = d->Ns;
+  h.basis_prec = d->basis16 ? DW_BF16 : DW_F64;
+  h.antiperiodic = c->p.antiperiodic;
+  h.Ne = d->Ne;
+  h.m0 = c->p.m0;
+  h.csw = c->p.csw;
+  h.cond_max = d->p.cond_max;
+  h.gauge_hash = c->gauge_hash;
+  h.V = (uint64_t)c->V;
+  h.n_graw = d->graw.size();
+  h.n_B = (uint64_t)d->Nb * 9 * d->Ns * d->Ns * 2;
+  const size_t nbasis = d->basis16 ? (size_t)d->Ns * 3 * c->V * sizeof(uint4) : (size_t)d->Ns * 24 * c->V * sizeof(double);
+  std::vector<unsigned char> basis(nbasis);
+  std::vector<double> B(h.n_B);
+  cudaError_t e = cudaMemcpy(basis.data(), d->basis16 ? (const void*)d->basis16 : (const void*)d->basis64, nbasis,
+                             cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(B.data(), d->B64, h.n_B * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return dw_cuda_fail(e, "dfl_save");
+  FILE* f = fopen(path, "wb");
+  if (!f) { dw_set_error(std::string("dfl_save: cannot open ") + path); return DW_EINVAL; }
+  bool ok = fwrite(&h, sizeof h, 1, f) == 1 && fwrite(basis.data(), 1, nbasis, f) == nbasis &&
+            fwrite(d->graw.data(), sizeof(cd), d->graw.size(), f) == d->graw.size() &&
+            fwrite(B.data(), sizeof(double), B.size(), f) == B.size();
+  ok = (fclose(f) == 0) && ok;
+  if (!ok) { dw_set_error(std::string("dfl_save: write error on ") + path); return DW_EINVAL; }
+  return DW_OK;
+}
+
+extern "C" int dfl_load(dw_ctx* c, const char* path, dfl_ctx** out, dfl_info* info) {
+  if (!c || !path || !out) { dw_set_error("dfl_load: null argument"); return DW_EINVAL; }
+  *out = nullptr;
+  if (int rc = dw_check_device(c, "dfl_load")) return rc;
+  auto t0 = std::chrono::steady_clock::now();
+  FILE* f = fopen(path, "rb");
+  if (!f) { dw_set_error(std::string("dfl_load: cannot open ") + path); return DW_EINVAL; }
+  struct Close { FILE* f; ~Close() { fclose(f); } } closer{f};
+  DflFileHeader h{};
+  if (fread(&h, sizeof h, 1, f) != 1 || memcmp(h.magic, "DWDFL01", 8) != 0) {
+    dw_set_error("dfl_load: not a deflation subspace file");
+    return DW_EINVAL;
+  }
+  for (int mu = 0; mu < 4; ++mu)
+    if (h.L[mu] != c->p.L[mu] || h.sap_bs[mu] != c->p.sap_bs[mu]) {
+      dw_set_error("dfl_load: the file belongs to another lattice or Schwarz block size");
+      return DW_EINVAL;
+    }
+  dfl_params p{};
+  for (int mu = 0; mu < 4; ++mu) p.bs[mu] = h.bs[mu];
+  p.Ns = h.Ns;
+  p.basis_prec = h.basis_prec;
+  p.iter_prec = DW_F32;
+  p.cond_max = h.cond_max;
+  p.ncy = 4;
+  p.nmr = 4;
+  dfl_ctx* d = nullptr;
+  int rc = dfl_alloc(c, &p, &d);
+  if (rc) return rc;
+  auto fail = [&](int r) { dfl_destroy(d); return r; };
+  if ((rc = build_tables(c, d))) return fail(rc);
+  const size_t V = c->V, Ns = d->Ns;
+  if (h.V != (uint64_t)V || h.Ne != d->Ne || h.n_graw != (uint64_t)Ns * d->Ne * Ns ||
+      h.n_B != (uint64_t)d->Nb * 9 * Ns * Ns * 2) {
+    dw_set_error("dfl_load: inconsistent sizes in the file");
+    return fail(DW_EINVAL);
+  }
+  const bool bf16 = h.basis_prec == DW_BF16;
+  const size_t nbasis = bf16 ? Ns * 3 * V * sizeof(uint4) : Ns * 24 * V * sizeof(double);
+  std::vector<unsigned char> basis(nbasis);
+  std::vector<double> B(h.n_B);
+  d->graw.resize(h.n_graw);
+  if (fread(basis.data(), 1, nbasis, f) != nbasis || fread(d->graw.data(), sizeof(cd), h.n_graw, f) != h.n_graw ||
+      fread(B.data(), sizeof(double), h.n_B, f) != h.n_B) {
+    dw_set_error("dfl_load: file too short");
+    return fail(DW_EINVAL);
+  }
+  cudaError_t e = cudaMalloc(&d->basis64, Ns * 24 * V * sizeof(double));
+  if (e == cudaSuccess && bf16) {
+    e = cudaMalloc(&d->basis16, nbasis);
+    if (e == cudaSuccess) e = cudaMemcpy(d->basis16, basis.data(), nbasis, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+      dequantize_kernel<<<(unsigned)((V * Ns + 255) / 256), 256>>>(V, (int)Ns, d->basis16, d->basis64); dw_note_launch();
+      e = cudaGetLastError();
+    }
+  } else if (e == cudaSuccess) {
+    e = cudaMemcpy(d->basis64, basis.data(), nbasis, cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(dw_cuda_fail(e, "dfl_load"));
+  const bool same_op = h.gauge_hash == c->gauge_hash && h.m0 == c->p.m0 && h.csw == c->p.csw &&
+                       h.antiperiodic == c->p.antiperiodic;
+  if ((rc = little_setup(c, d, same_op ? B.data() : nullptr))) return fail(rc);
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  fill_info(d, info, secs, secs, same_op ? 1 : 0);
+  *out = d;
+  return d->illcond ? DW_ILLCOND : DW_OK;
 }

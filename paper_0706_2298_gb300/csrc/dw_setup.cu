@@ -338,6 +338,13 @@ extern "C" int dw_create(const dw_params* p, const double* links_host, dw_ctx** 
   dw_ctx* c = new dw_ctx();
   c->p = *p;
   c->device = dev;
+  {
+    uint64_t h = 1469598103934665603ull;       // FNV-1a over the bytes of the canonical links
+    const unsigned char* b = reinterpret_cast<const unsigned char*>(links_host);
+    const size_t nb = (size_t)V * 4 * 18 * sizeof(double);
+    for (size_t k = 0; k < nb; ++k) { h ^= b[k]; h *= 1099511628211ull; }
+    c->gauge_hash = h;
+  }
   c->V = V;
   for (int mu = 0; mu < 4; ++mu) c->nsb[mu] = nsb[mu];
   Geom& g = c->g;

@@ -240,7 +240,11 @@ int solve_one(dw_ctx* c, dfl_ctx* d, const sol_params* p, const double* eta_cano
     double rk = 1.0;
     for (; k < nkv && inf.iterations < p->nmx; ++k) {
       tm.begin(PH_SAP);
-      if ((rc = sap_apply<T>(c, p->ncy, p->nmr, W.rho, W.xi[k], s))) return rc;
+      if (p->ncy > 0) {
+        if ((rc = sap_apply<T>(c, p->ncy, p->nmr, W.rho, W.xi[k], s))) return rc;
+      } else {   // no preconditioner (M = 1): plain GCR
+        DW_CUDA(cudaMemcpyAsync(W.xi[k], W.rho, fbT, cudaMemcpyDeviceToDevice, s));
+      }
       tm.end();
       tm.begin(PH_DIRAC);
       dirac_full<T>(c, W.xi[k], W.chi[k], s);
@@ -573,7 +577,7 @@ extern "C" int gcr_solve(dw_ctx* c, dfl_ctx* d, const sol_params* p, int nrhs, c
   int worst = DW_OK;
   const size_t n = (size_t)c->V * 24;
   const char* be = getenv("DW_BATCH");
-  if (p->mixed && nrhs > 1 && !(be && be[0] == '0') && p->nkv <= 64) {
+  if (p->mixed && nrhs > 1 && !(be && be[0] == '0') && p->nkv <= 64 && p->ncy > 0) {
     if (nrhs > 64) { dw_set_error("gcr_solve: at most 64 right-hand sides per batch"); return DW_EINVAL; }
     return solve_batch_f32(c, d, p, nrhs, eta, psi, info, s);
   }

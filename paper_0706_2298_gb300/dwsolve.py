@@ -35,13 +35,15 @@ class DflParams(C.Structure):
     _fields_ = [("bs", C.c_int * 4), ("Ns", C.c_int), ("n_inv", C.c_int), ("ncy", C.c_int), ("nmr", C.c_int),
                 ("basis_prec", C.c_int), ("iter_prec", C.c_int), ("cond_max", C.c_double),
                 ("net_weights", C.c_void_p), ("net_channels", C.c_int), ("net_k0", C.c_int),
-                ("net_judge", C.c_double)]
+                ("net_judge", C.c_double), ("boot_steps", C.c_int), ("boot_tol", C.c_double),
+                ("boot_nmx", C.c_int)]
 
 
 class DflInfo(C.Structure):
     _fields_ = [("seconds", C.c_double), ("seconds_little", C.c_double), ("max_block_cond", C.c_double),
                 ("Nb", C.c_int), ("N", C.c_int), ("learned_used", C.c_int), ("rho_in", C.c_double),
-                ("rho_out", C.c_double)]
+                ("rho_out", C.c_double), ("boot_steps", C.c_int), ("boot_gcr_steps", C.c_int),
+                ("little_loaded", C.c_int)]
 
 
 class SolParams(C.Structure):
@@ -78,6 +80,9 @@ _SIGNATURES = {
     "deflation_build": (C.c_int, [_P, C.POINTER(DflParams), _P, C.POINTER(_P), C.POINTER(DflInfo)]),
     "dfl_destroy": (None, [_P]),
     "dfl_dims": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "dfl_retarget": (C.c_int, [_P, _P, C.POINTER(_P), C.POINTER(DflInfo)]),
+    "dfl_save": (C.c_int, [_P, C.c_char_p]),
+    "dfl_load": (C.c_int, [_P, C.c_char_p, C.POINTER(_P), C.POINTER(DflInfo)]),
     "dfl_restrict": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "dfl_prolong": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "dfl_basis_export": (C.c_int, [_P, _P, _P]),
@@ -229,8 +234,10 @@ def sap_precondition(ctx: Ctx, prec, ncy, nmr, nrhs, rho_dev, xi_dev, stream=Non
 
 
 def deflation_build(ctx: Ctx, bs, Ns, n_inv, ncy, nmr, start_canon_dev, basis_prec=DW_BF16, iter_prec=DW_F32,
-                    cond_max=1e8, net_weights=None, net_k0=2, net_judge=0.95, net_channels=16):
+                    cond_max=1e8, net_weights=None, net_k0=2, net_judge=0.95, net_channels=16, boot_steps=0,
+                    boot_tol=1e-2, boot_nmx=16):
     p = DflParams()
+    p.boot_steps, p.boot_tol, p.boot_nmx = int(boot_steps), float(boot_tol), int(boot_nmx)
     p.bs = (C.c_int * 4)(*bs)
     p.Ns, p.n_inv, p.ncy, p.nmr = Ns, n_inv, ncy, nmr
     p.basis_prec, p.iter_prec, p.cond_max = basis_prec, iter_prec, float(cond_max)
@@ -240,6 +247,28 @@ def deflation_build(ctx: Ctx, bs, Ns, n_inv, ncy, nmr, start_canon_dev, basis_pr
     h = C.c_void_p()
     rc = _check(lib().deflation_build(ctx.handle, C.byref(p), _ptr(_as_f64(start_canon_dev)), C.byref(h),
                                       C.byref(info)), ok=(DW_OK, DW_ILLCOND))
+    d = Dfl(h, info)
+    d.status = rc
+    return d
+
+
+def dfl_retarget(src: Dfl, ctx: Ctx) -> Dfl:
+    info = DflInfo()
+    h = C.c_void_p()
+    rc = _check(lib().dfl_retarget(src.handle, ctx.handle, C.byref(h), C.byref(info)), ok=(DW_OK, DW_ILLCOND))
+    d = Dfl(h, info)
+    d.status = rc
+    return d
+
+
+def dfl_save(d: Dfl, path):
+    _check(lib().dfl_save(d.handle, str(path).encode()))
+
+
+def dfl_load(ctx: Ctx, path) -> Dfl:
+    info = DflInfo()
+    h = C.c_void_p()
+    rc = _check(lib().dfl_load(ctx.handle, str(path).encode(), C.byref(h), C.byref(info)), ok=(DW_OK, DW_ILLCOND))
     d = Dfl(h, info)
     d.status = rc
     return d

@@ -202,7 +202,7 @@ def test_little_solve_batch(case, prec, tol, cmp):
     for r in range(R):
         assert rel(v[r], ref[r]) <= cmp, r
     if prec == dw.DW_F32:
-        w1 = wt[: 2 * d.Nb * d.Ns]
+        w1 = wt[0].contiguous()
         v1 = torch.empty_like(w1)
         dw.little_dirac_solve(d, prec, w1, v1, tol, 2000)
         assert rel(v1.double().cpu().numpy().view(np.complex128), v[0]) <= cmp
@@ -240,6 +240,27 @@ def test_gcr_solve(solve_case, mixed, dfl):
     assert infos[0].relres <= 1e-10 and infos[0].iterations > 0
 
 
+def test_plain_gcr_is_the_oracles_solve(solve_case):
+    """ncy = 0: gcr_solve without deflation and preconditioner in FP64 is plain restarted GCR(16),
+    the oracle's own solve; it reaches the tolerance with the iteration count of the oracle's full
+    run on the same inputs (recorded by oracle/plain_gcr_run.py)."""
+    import json
+    import os
+    L, ctx, D, eta, x = solve_case
+    with open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle",
+                           "plain_gcr_8c4.json")) as f:
+        rec = json.load(f)
+    assert rec["L"] == list(L) and rec["m0"] == -0.2 and rec["gauge_seed"] == 1 and rec["source_seed"] == 2
+    p = dw.sol_params(tol=1e-10, nkv=16, nmx=20000, ncy=0, nmr=0, mixed=0)
+    psi = torch.empty_like(eta, device="cuda")
+    rc, infos = dw.gcr_solve(ctx, None, p, 1, eta.cuda(), psi)
+    assert rc == dw.DW_OK
+    psi = psi.cpu().numpy()
+    assert np.linalg.norm(eta.numpy() - D.apply(psi)) / np.linalg.norm(eta.numpy()) <= 1.05e-10
+    assert abs(infos[0].iterations - rec["iterations"]) <= max(3, 0.01 * rec["iterations"]), \
+        (infos[0].iterations, rec["iterations"])
+
+
 def test_inverse_iteration_fp32(case):
     """FP32 subspace generation (the mixed path) tracks the FP64 oracle to FP32 accuracy."""
     L, sb, db, Ns, ctx, D, start = case
@@ -270,3 +291,100 @@ def test_little_solve_cooperative_matches_host_driven(case):
     assert rel(res[("1", dw.DW_F64)][0], res[("0", dw.DW_F64)][0]) <= 1e-8
     assert rel(res[("1", dw.DW_F32)][0], res[("0", dw.DW_F32)][0]) <= 1e-4
     assert abs(res[("1", dw.DW_F64)][1] - res[("0", dw.DW_F64)][1]) <= 2
+
+
+# ----------------------------------------------------------------------------- bootstrapped generation,
+# subspace reuse across operators, checkpoints
+@pytest.fixture(scope="module")
+def boot_case():
+    L = (4, 4, 4, 4)
+    U = synth.random_gauge(L, 32)
+    ctx = dw.dw_create(L, -0.1, 1.0, U, (2, 2, 2, 2))
+    D = WilsonClover(L, U.numpy(), -0.1, 1.0)
+    return L, U, ctx, D, synth.start_fields(L, 3, 6)
+
+
+def test_bootstrap_exact_steps(boot_case):
+    """Section 5.3: 2 plain steps, then a bootstrapped step solved to 1e-10 by the deflated solver of
+    the current fields = exact inverse iteration psi <- D^{-1} psi / |.|; the basis equals the
+    oracle's (plain steps by the oracle, the exact step by the dense LU inverse)."""
+    from scipy.linalg import lu_factor, lu_solve
+    L, U, ctx, D, start = boot_case
+    d = dw.deflation_build(ctx, (2, 2, 2, 2), 3, 2, 4, 4, start.cuda(), basis_prec=dw.DW_F64, iter_prec=dw.DW_F64,
+                           boot_steps=1, boot_tol=1e-10, boot_nmx=400)
+    assert d.info.boot_steps == 1 and d.info.boot_gcr_steps > 0
+    f0 = inverse_iteration(SchwarzOracle(D, (2, 2, 2, 2)), start.numpy(), 2, 4, 4)
+    lu = lu_factor(D.dense())
+    f1 = np.array([lu_solve(lu, f.reshape(-1)).reshape(D.V, 4, 3) for f in f0])
+    f1 /= np.linalg.norm(f1.reshape(3, -1), axis=1)[:, None, None, None]
+    sub = BlockSubspace(D, (2, 2, 2, 2), block_gram_schmidt(Blocking(L, (2, 2, 2, 2)), f1))
+    out = torch.empty((3, ctx.V, 4, 3), dtype=torch.complex128, device="cuda")
+    dw.dfl_basis_export(d, out)
+    torch.cuda.synchronize()
+    assert rel(out.cpu().numpy(), basis_fields(sub)) <= 1e-7
+
+
+def test_bootstrap_beats_plain_at_equal_steps():
+    """Bootstrapped steps (loose tolerance) give a better subspace than the same number of plain
+    Schwarz steps: fewer DFL+SAP+GCR steps for the same source."""
+    L = (8, 8, 8, 8)
+    U = synth.random_gauge(L, 1)
+    ctx = dw.dw_create(L, -0.2, 1.0, U, (4, 4, 4, 4))
+    start = synth.start_fields(L, 8, 3).cuda()
+    plain = dw.deflation_build(ctx, (4, 4, 4, 4), 8, 4, 4, 4, start)
+    boot = dw.deflation_build(ctx, (4, 4, 4, 4), 8, 2, 4, 4, start, boot_steps=2, boot_tol=1e-2, boot_nmx=16)
+    eta = synth.gaussian_source(L, 2).cuda()
+    its = {}
+    for name, d in (("plain", plain), ("boot", boot)):
+        psi = torch.empty_like(eta)
+        rc, infos = dw.gcr_solve(ctx, d, dw.sol_params(tol=1e-10, mixed=1), 1, eta, psi)
+        assert rc == dw.DW_OK
+        its[name] = infos[0].iterations
+    assert its["boot"] <= its["plain"], its
+
+
+def test_retarget_to_other_mass(boot_case, tmp_path):
+    """One subspace for several operators (Section 6.4): the little operator of the retargeted
+    context is Phi^+ D' Phi of the same basis with the other operator D' (bare mass and c_sw
+    changed), and DFL+SAP+GCR with it solves D' psi = eta; a checkpoint reloads the subspace,
+    with the stored little operator for the same operator and a new one for another."""
+    L, U, ctx, D, start = boot_case
+    d = dw.deflation_build(ctx, (2, 2, 2, 2), 3, 3, 4, 4, start.cuda(), basis_prec=dw.DW_BF16)
+    ctx2 = dw.dw_create(L, 0.05, 1.2, U, (2, 2, 2, 2))
+    D2 = WilsonClover(L, U.numpy(), 0.05, 1.2)
+    d2 = dw.dfl_retarget(d, ctx2)
+    basis = torch.empty((3, ctx.V, 4, 3), dtype=torch.complex128, device="cuda")
+    dw.dfl_basis_export(d2, basis)
+    b2 = torch.empty_like(basis)
+    dw.dfl_basis_export(d, b2)
+    torch.cuda.synchronize()
+    assert torch.equal(basis, b2)
+    bl = basis.cpu().numpy()
+    phi = np.stack([bl[:, Blocking(L, (2, 2, 2, 2)).sites[Lb]] for Lb in range(d.Nb)])
+    sub2 = BlockSubspace(D2, (2, 2, 2, 2), phi)
+    v = synth.complex_gaussian((d.Nb * d.Ns,), 19).numpy()
+
+    def lapply(dd):
+        w = torch.empty(dd.Nb * dd.Ns, dtype=torch.complex128, device="cuda")
+        dw.little_apply(dd, torch.from_numpy(v).cuda(), w)
+        torch.cuda.synchronize()
+        return w.cpu().numpy()
+
+    w2 = lapply(d2)
+    assert rel(w2, sub2.A @ v) <= 1e-13
+    eta = synth.gaussian_source(L, 7)
+    psi = torch.empty_like(eta, device="cuda")
+    rc, _ = dw.gcr_solve(ctx2, d2, dw.sol_params(tol=1e-10, mixed=1), 1, eta.cuda(), psi)
+    assert rc == dw.DW_OK
+    assert np.linalg.norm(eta.numpy() - D2.apply(psi.cpu().numpy())) / np.linalg.norm(eta.numpy()) <= 1.05e-10
+    # checkpoint
+    path = str(tmp_path / "subspace.dwdfl")
+    dw.dfl_save(d, path)
+    d_same = dw.dfl_load(ctx, path)
+    assert d_same.info.little_loaded == 1
+    assert np.array_equal(lapply(d_same), lapply(d))
+    d_other = dw.dfl_load(ctx2, path)
+    assert d_other.info.little_loaded == 0
+    assert np.array_equal(lapply(d_other), w2)
+    with pytest.raises(dw.DwError):
+        dw.dfl_load(dw.dw_create((8, 8, 8, 8), -0.1, 1.0, synth.random_gauge((8, 8, 8, 8), 1), (2, 2, 2, 2)), path)

@@ -247,3 +247,26 @@ def test_inverse_iteration_free_field_reaches_lowest_modes():
     assert max(deficit(s) for s in got) <= 0.2
     for s in got:
         assert lam_min <= norm(D.apply(s)) / norm(s) <= 1.2 * lam_min
+
+
+def test_bootstrap_iteration_tight_tolerance_is_exact_inverse_iteration():
+    """Section 5.3 bootstrapped steps: solved to 1e-11, each step is psi <- D^{-1} psi / |.| (the
+    dense LU inverse), whatever the subspace used to deflate the solver; a loose tolerance gives a
+    field nearer the low modes than one plain Schwarz step (smaller ||D psi|| / ||psi||, (5.2))."""
+    from scipy.linalg import lu_factor, lu_solve
+    from oracle.deflation import bootstrap_iteration, inverse_iteration
+    from oracle.sap import SchwarzOracle
+    L = (4, 4, 4, 4)
+    D = WilsonClover(L, synth.random_gauge(L, 32).numpy(), -0.1, 1.0)
+    start = synth.start_fields(L, 3, 6).numpy()
+    f0 = inverse_iteration(SchwarzOracle(D, (2, 2, 2, 2)), start, 2, 4, 4)
+    got = bootstrap_iteration(D, (2, 2, 2, 2), (2, 2, 2, 2), f0, 1, 1e-11)
+    lu = lu_factor(D.dense())
+    for l in range(3):
+        w = lu_solve(lu, f0[l].reshape(-1))
+        w /= np.linalg.norm(w)
+        assert np.linalg.norm(got[l].reshape(-1) - w) <= 1e-8
+    loose = bootstrap_iteration(D, (2, 2, 2, 2), (2, 2, 2, 2), f0, 1, 1e-2)
+    plain = inverse_iteration(SchwarzOracle(D, (2, 2, 2, 2)), f0, 1, 4, 4)
+    for l in range(3):
+        assert norm(D.apply(loose[l])) < norm(D.apply(plain[l]))
