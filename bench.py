@@ -367,6 +367,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-batch", action="store_true", help="skip the 12 point-source batched solve")
+    ap.add_argument("--no-table1", action="store_true",
+                    help="skip the solver comparison over masses and the subspace generation variants")
     ap.add_argument("--profile-case", choices=["dirac-sap", "little", "batch12"], default=None,
                     help="run a small fixed launch sequence for an ncu capture and exit")
     ap.add_argument("--prec", default="f32", choices=["f32", "f64"], help="--profile-case dirac-sap precision")
@@ -575,6 +577,55 @@ def main():
                  "autotune": tune}
         del eta12, psi12
 
+    # ---- subspace generation variants (Section 5.3): plain inverse iteration vs bootstrapped steps
+    gen = None
+    if not args.no_table1:
+        gen = {}
+        for name, kw in (("plain n_inv=11", dict(n_inv=11)), ("plain n_inv=5", dict(n_inv=5)),
+                         ("bootstrap 3 plain + 2 boot (tol 1e-2)", dict(n_inv=3, boot_steps=2, boot_tol=1e-2,
+                                                                          boot_nmx=16))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dv = dw.deflation_build(ctx, wl["dfl_bs"], wl["Ns"], kw.pop("n_inv"), wl["ncy"], wl["nmr"], start,
+                                    basis_prec=dw.DW_BF16, iter_prec=dw.DW_F32, **kw)
+            tb = time.perf_counter() - t0
+            rc, inf = dw.gcr_solve(ctx, dv, p_mixed, 1, eta, psi)
+            gen[name] = {"build_s": tb, "solve_gcr_steps": inf[0].iterations, "solve_s": inf[0].seconds,
+                         "boot_gcr_steps_per_field": dv.info.boot_gcr_steps / wl["Ns"], "converged": rc == dw.DW_OK}
+            del dv
+
+    # ---- Table 1 analogue (Section 6.3): three solvers at several bare masses, one deflation
+    # subspace generated at the workload mass and reused at the others (Section 6.4)
+    table1 = None
+    if not args.no_table1:
+        table1 = []
+        for dm in (0.0, 0.02, 0.05, 0.1):
+            m = wl["m0"] + dm
+            cm = ctx if dm == 0.0 else dw.dw_create(L, m, wl["csw"], U, wl["sap_bs"])
+            t0 = time.perf_counter()
+            dm_ = dfl if dm == 0.0 else dw.dfl_retarget(dfl, cm)
+            t_rt = time.perf_counter() - t0
+            row = {"m0": m, "retarget_s": t_rt if dm else 0.0}
+            for name, fn in (
+                    ("DFL+SAP+GCR mixed", lambda: dw.gcr_solve(cm, dm_, p_mixed, 1, eta, psi)),
+                    ("SAP+GCR mixed", lambda: dw.gcr_solve(cm, None, dw.sol_params(tol=wl["tol"], nkv=32,
+                                                                                   ncy=wl["ncy"], nmr=wl["nmr"],
+                                                                                   mixed=1, nmx=20000), 1, eta, psi)),
+                    ("EO+BiCGstab FP64", lambda: dw.bicgstab_solve(cm, wl["tol"], 20000, eta, psi))):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                res = fn()
+                torch.cuda.synchronize()
+                ts = time.perf_counter() - t0
+                if name.startswith("EO"):
+                    row[name] = {"iterations": res[1], "s": ts, "relres": res[2], "converged": res[0] == dw.DW_OK}
+                else:
+                    row[name] = {"iterations": res[1][0].iterations, "s": ts, "relres": res[1][0].relres,
+                                 "converged": res[0] == dw.DW_OK}
+            table1.append(row)
+            if dm:
+                del dm_, cm
+
     # ---- CPU oracle sample (rank 0, N = 1 only): the oracle's own solve on the host cores
     cpu = None
     rec = oracle_run_record(args.workload)
@@ -606,7 +657,8 @@ def main():
                 "dfl_build_s": t_build, "plain_fp64": plain,
                 "speedup_vs_plain_fp64": (plain["s_per_solve"] / value) if plain else None,
                 "dirac": dirac, "roofline": roof, "roofline_sap": roof_sap, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clk, "batch12": batch}
+                "gpu_launches": launches, "clocks": clk, "batch12": batch, "subspace_generation": gen,
+                "table1": table1}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

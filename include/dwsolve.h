@@ -298,6 +298,14 @@ int dfl_inverse_iteration(dw_ctx* ctx, int ncy, int nmr, int nsteps, int nf, voi
 int cgnr_solve(dw_ctx* ctx, double tol, int maxit, const double* eta_dev, double* psi_dev, int* iters,
                double* relres, void* stream);
 
+/* EO+BiCGstab, the first comparison solver of Table 1 (Section 6.3): BiCGstab on the even-odd
+ * preconditioned operator A_ee - D_eo A_oo^{-1} D_oe (the DW_OP_SCHUR operator), FP64, with the
+ * odd part reconstructed exactly.  Stops at ||eta - D psi|| <= tol ||eta|| (checked with D) or
+ * after maxit iterations (DW_ENOTCONV); iters counts BiCGstab iterations (two even-odd operator
+ * applications each).  eta, psi: canonical complex128[V][4][3] on the device.  Synchronous. */
+int bicgstab_solve(dw_ctx* ctx, double tol, int maxit, const double* eta_dev, double* psi_dev, int* iters,
+                   double* relres, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

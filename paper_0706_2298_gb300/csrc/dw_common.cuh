@@ -409,6 +409,11 @@ int dw_make_dd(dw_ctx* c, cudaStream_t s);
 void dirac_full_dd(dw_ctx* c, const dd* in, dd* out, cudaStream_t s);
 
 // dirac / sap entry points used by the solver ---------------------------------------
+// even-odd Schur operator (odd sites of out zero; uses the context's scratch field) and the
+// preparation / reconstruction of the even-odd system
+template <typename T> int dirac_schur(dw_ctx* c, const T* in, T* out, cudaStream_t s);
+template <typename T> void eo_prepare(dw_ctx* c, const T* eta, T* bhat, T* t, cudaStream_t s);
+template <typename T> void eo_reconstruct(dw_ctx* c, const T* eta, const T* x, T* psi, cudaStream_t s);
 template <typename T> void dirac_full(dw_ctx* c, const T* in, T* out, cudaStream_t s);
 // nrhs fields stored consecutively; rgroup right-hand sides share one pass over the links
 template <typename T> void dirac_mrhs(dw_ctx* c, const T* in, T* out, int nrhs, int rgroup, cudaStream_t s);

@@ -82,6 +82,74 @@ __global__ void __launch_bounds__(128) schur_even_kernel(Geom g, const T* __rest
   store_site<T, 12>(out, V, site_index(g, s.b, 1, s.h), y);
 }
 
+// Even-odd preparation and reconstruction of D psi = eta (the Schur complement system
+// (A_ee - D_eo A_oo^{-1} D_oe) psi_e = eta_e - D_eo A_oo^{-1} eta_o, psi_o = A_oo^{-1}(eta_o - D_oe psi_e)).
+// t_o = A_oo^{-1} in_o on the odd sites
+template <typename T>
+__global__ void __launch_bounds__(128) clover_inv_odd_kernel(Geom g, const T* __restrict__ clovinv,
+                                                             const T* __restrict__ in, T* __restrict__ t) {
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= g.V / 2) return;
+  const size_t V = g.V;
+  const int b = (int)(tid >> g.lshv), h = (int)(tid & (g.shv - 1));
+  long long i = site_index(g, b, 1, h);
+  cplx<T> x[12], y[12];
+  load_site<T, 12>(in, V, i, x);
+  clover_apply(clovinv, V, i, x, y);
+  store_site<T, 12>(t, V, i, y);
+}
+
+// out_e = in_e - D_eo t_o = in_e + (1/2) hop(t) on the even sites, out_o = 0
+template <typename T>
+__global__ void __launch_bounds__(128) eo_rhs_kernel(Geom g, const T* __restrict__ links, const T* __restrict__ in,
+                                                     const T* __restrict__ t, T* __restrict__ out) {
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= g.V / 2) return;
+  const size_t V = g.V;
+  SiteRef s;
+  s.b = (int)(tid >> g.lshv);
+  s.p = 0;
+  s.h = (int)(tid & (g.shv - 1));
+  long long i = site_index(g, s.b, 0, s.h);
+  cplx<T> y[12], acc[12];
+  load_site<T, 12>(in, V, i, y);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = {T(0), T(0)};
+  hop_all(g, s, i, links, t, acc);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) y[k] += T(0.5) * acc[k];
+  store_site<T, 12>(out, V, i, y);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) y[k] = {T(0), T(0)};
+  store_site<T, 12>(out, V, site_index(g, s.b, 1, s.h), y);
+}
+
+// out_o = A_oo^{-1} (in_o - D_oe x_e) = A_oo^{-1} (in_o + (1/2) hop(x)) on the odd sites, out_e = x_e
+template <typename T>
+__global__ void __launch_bounds__(128) eo_reconstruct_kernel(Geom g, const T* __restrict__ links,
+                                                             const T* __restrict__ clovinv, const T* __restrict__ in,
+                                                             const T* __restrict__ x, T* __restrict__ out) {
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= g.V / 2) return;
+  const size_t V = g.V;
+  SiteRef s;
+  s.b = (int)(tid >> g.lshv);
+  s.p = 1;
+  s.h = (int)(tid & (g.shv - 1));
+  long long io = site_index(g, s.b, 1, s.h), ie = site_index(g, s.b, 0, s.h);
+  cplx<T> y[12], acc[12], z[12];
+  load_site<T, 12>(in, V, io, y);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = {T(0), T(0)};
+  hop_all(g, s, io, links, x, acc);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) y[k] += T(0.5) * acc[k];
+  clover_apply(clovinv, V, io, y, z);
+  store_site<T, 12>(out, V, io, z);
+  load_site<T, 12>(x, V, ie, y);
+  store_site<T, 12>(out, V, ie, y);
+}
+
 // Multi-RHS D: one thread per site applies D to all right-hand sides (fields stored one after the
 // other, stride fstride reals).  RHS are processed R at a time; the links and clover of the site are
 // loaded for each group but come from L1/L2 after the first, so HBM sees them once per site.
@@ -317,8 +385,27 @@ static int dirac_full_f64x(dw_ctx* c, const double* in, double* out, int nrhs, c
   return DW_OK;
 }
 
+// bhat_e = eta_e - D_eo A_oo^{-1} eta_o, bhat_o = 0 (t: scratch field)
 template <typename T>
-static int dirac_schur(dw_ctx* c, const T* in, T* out, cudaStream_t st) {
+void eo_prepare(dw_ctx* c, const T* eta, T* bhat, T* t, cudaStream_t st) {
+  constexpr int P = prec_of<T>();
+  unsigned blocks = (unsigned)((c->V / 2 + 127) / 128);
+  clover_inv_odd_kernel<T><<<blocks, 128, 0, st>>>(c->g, (const T*)c->clovinv[P], eta, t); dw_note_launch();
+  eo_rhs_kernel<T><<<blocks, 128, 0, st>>>(c->g, (const T*)c->links[P], eta, t, bhat); dw_note_launch();
+}
+// psi_e = x_e, psi_o = A_oo^{-1}(eta_o - D_oe x_e)
+template <typename T>
+void eo_reconstruct(dw_ctx* c, const T* eta, const T* x, T* psi, cudaStream_t st) {
+  constexpr int P = prec_of<T>();
+  unsigned blocks = (unsigned)((c->V / 2 + 127) / 128);
+  eo_reconstruct_kernel<T><<<blocks, 128, 0, st>>>(c->g, (const T*)c->links[P], (const T*)c->clovinv[P], eta, x,
+                                                   psi); dw_note_launch();
+}
+template void eo_prepare<double>(dw_ctx*, const double*, double*, double*, cudaStream_t);
+template void eo_reconstruct<double>(dw_ctx*, const double*, const double*, double*, cudaStream_t);
+
+template <typename T>
+int dirac_schur(dw_ctx* c, const T* in, T* out, cudaStream_t st) {
   constexpr int P = prec_of<T>();
   if (!c->sap_d[P]) DW_CUDA(cudaMalloc(&c->sap_d[P], dw_field_bytes(c, P)));
   T* t = (T*)c->sap_d[P];
@@ -327,6 +414,8 @@ static int dirac_schur(dw_ctx* c, const T* in, T* out, cudaStream_t st) {
   schur_even_kernel<T><<<blocks, 128, 0, st>>>(c->g, (const T*)c->links[P], (const T*)c->clov[P], in, t, out); dw_note_launch();
   return DW_OK;
 }
+template int dirac_schur<float>(dw_ctx*, const float*, float*, cudaStream_t);
+template int dirac_schur<double>(dw_ctx*, const double*, double*, cudaStream_t);
 
 extern "C" int dw_apply(dw_ctx* c, int prec, int op, int nrhs, const void* in, void* out, void* stream) {
   if (!c || !in || !out || in == out || nrhs < 1 || (prec != DW_F64 && prec != DW_F32 && prec != DW_F64X) ||

@@ -94,6 +94,7 @@ _SIGNATURES = {
     "gcr_solve": (C.c_int, [_P, _P, C.POINTER(SolParams), C.c_int, _P, _P, C.POINTER(SolInfo), _P]),
     "dw_autotune": (C.c_int, [_P, C.c_int, C.c_char_p, C.c_size_t]),
     "cgnr_solve": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.POINTER(C.c_int), C.POINTER(C.c_double), _P]),
+    "bicgstab_solve": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.POINTER(C.c_int), C.POINTER(C.c_double), _P]),
     "ptnet_weight_count": (C.c_size_t, [C.c_int]),
     "ptnet_forward": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, _P, _P]),
     "ptnet_loss_grad": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, _P, _P, C.POINTER(C.c_double), _P]),
@@ -326,6 +327,13 @@ def cgnr_solve(ctx: Ctx, tol, maxit, eta_dev, psi_dev, stream=None):
     it, rr = C.c_int(), C.c_double()
     rc = _check(lib().cgnr_solve(ctx.handle, float(tol), int(maxit), _ptr(_as_f64(eta_dev)), _ptr(_as_f64(psi_dev)),
                                  C.byref(it), C.byref(rr), _stream(stream)), ok=(DW_OK, DW_ENOTCONV))
+    return rc, it.value, rr.value
+
+
+def bicgstab_solve(ctx: Ctx, tol, maxit, eta_dev, psi_dev, stream=None):
+    it, rr = C.c_int(), C.c_double()
+    rc = _check(lib().bicgstab_solve(ctx.handle, float(tol), int(maxit), _ptr(_as_f64(eta_dev)), _ptr(_as_f64(psi_dev)),
+                                     C.byref(it), C.byref(rr), _stream(stream)), ok=(DW_OK, DW_ENOTCONV))
     return rc, it.value, rr.value
 
 

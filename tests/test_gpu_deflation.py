@@ -240,6 +240,19 @@ def test_gcr_solve(solve_case, mixed, dfl):
     assert infos[0].relres <= 1e-10 and infos[0].iterations > 0
 
 
+def test_eo_bicgstab(solve_case):
+    """EO+BiCGstab (Table 1's first comparison solver): the even-odd preconditioned system solved by
+    BiCGstab in FP64 with the odd part reconstructed; the solution meets the tolerance with the
+    oracle's D and equals the oracle's solution."""
+    L, ctx, D, eta, x = solve_case
+    psi = torch.empty_like(eta, device="cuda")
+    rc, it, rr = dw.bicgstab_solve(ctx, 1e-10, 5000, eta.cuda(), psi)
+    assert rc == dw.DW_OK and rr <= 1e-10 and it > 0
+    psi = psi.cpu().numpy()
+    assert np.linalg.norm(eta.numpy() - D.apply(psi)) / np.linalg.norm(eta.numpy()) <= 1.05e-10
+    assert rel(psi, x) <= 1e-8
+
+
 def test_plain_gcr_is_the_oracles_solve(solve_case):
     """ncy = 0: gcr_solve without deflation and preconditioner in FP64 is plain restarted GCR(16),
     the oracle's own solve; it reaches the tolerance with the iteration count of the oracle's full
