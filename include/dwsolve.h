@@ -166,7 +166,8 @@ typedef struct {
   int N;                   /* little dimension Nb * Ns */
   int learned_used;        /* 1: the network output was accepted */
   double rho_in;           /* mean ||D psi||/||psi|| at the network input (after net_k0 steps) */
-  double rho_out;          /* ... of the network output (or of the fields after the plain fallback) */
+  double rho_out;          /* ... of the network output (or of the fields after the plain fallback); without a
+                              network: of the generated fields (FP32 generation only, else 0) */
   int boot_steps;          /* bootstrapped steps done */
   int boot_gcr_steps;      /* GCR steps of their approximate solves, summed over steps and fields */
   int little_loaded;       /* dfl_load: 1 if the stored little operator was used (same operator) */

@@ -79,7 +79,7 @@ struct dfl_ctx {
   int defer_slot = -1;                                 // >= 0: write results to coop_out[2*slot], no host sync
   double* ref64 = nullptr;                             // refinement work: 3 FP64 little vectors
   float* ref32 = nullptr;                              //                  2 FP32 little vectors
-  double* coop_partial = nullptr;                      // [coop_grid][64]
+  double* coop_partial = nullptr;                      // reduction accumulators of the cooperative solver
   double* coop_out = nullptr;                          // iterations, relative residual
   dd* ddf = nullptr;                                   // double-float field (restriction/prolongation)
   dd* ddl = nullptr;                                   // double-float little vector
@@ -741,13 +741,20 @@ inline unsigned warps_grid(int n, int threads = 128) { return (unsigned)((n * 32
 // each parity, and with its even rows the entries of every even-site little
 // vector on them, so the even hop and all elementwise work and inner products
 // that follow it stay inside the CTA.  Reductions: per-CTA sums in shared
-// memory -> one partial per CTA in global memory -> after the barrier every
-// CTA adds the partials in CTA order (identical, deterministic values in every
-// CTA).  Inner products with many vectors are CTA-slice GEMVs: warp w owns the
-// vectors j = w, w + 8, ...  One GCR step takes four grid barriers: after the
-// odd hop, and three reductions (the A.3 projection and the Gram-Schmidt
-// coefficients share one, with the coefficients of the projected vector
-// obtained from those of the raw vector and a table of (chi_j, B^ g_l)).
+// memory, added in FP64 into one of three rotating global accumulators, a grid
+// barrier, then every CTA reads the totals (the FP64 sum of FP32 partials is
+// exact enough that the FP32 results do not depend on the order of the adds).
+// Inner products with many vectors are CTA-slice GEMVs: warp w owns the vectors
+// j = w, w + 8, ...  One GCR step takes three grid barriers: after the odd hop,
+// and two reductions (the A.3 projection and the Gram-Schmidt coefficients share
+// one, with the coefficients of the projected vector obtained from those of the
+// raw vector and a table of (chi_j, B^ g_l); the second gives c_k, a_k and the
+// table row).  The residual rho_{k+1} = rho_k - (a_k / c_k) chi'_k is not
+// published before the next step: rho is double-buffered and chi'_k kept
+// unnormalised, so the next odd hop forms rho_{k+1} on the fly from two vectors
+// every CTA can read after the second reduction; |rho_{k+1}|^2 is folded into
+// the next step's first reduction (the stopping test of a step uses
+// |rho_k|^2 - |a_k|^2 and the cycle end recomputes the true residual).
 constexpr int COOP_THREADS = 256;
 constexpr int COOP_WARPS = COOP_THREADS / 32;
 constexpr int COOP_NV = 128;         // values per grid reduction
@@ -763,8 +770,8 @@ struct CoopArgs {
   const int *list_e, *list_o, *lnb_e, *lnb_o;
   const T *M, *g, *Bg, *Ainv, *b;
   T* v;
-  T* work;            // (2 nkv + 4) vectors of Ne*Ns complex
-  T* partial;         // [2][COOP_NV][coop_gpad(gridDim)]
+  T* work;            // (2 nkv + 5) vectors of Ne*Ns complex
+  double* acc;        // [3][COOP_NV] reduction accumulators, zero at launch
   double* out;        // [0] iterations, [1] relative residual
   double tol;
 };
@@ -779,23 +786,21 @@ struct CoopShared {
   T res[COOP_NV];            // grid-wide sums
   T a[2 * COOP_NKV], c[COOP_NKV], beta[2 * COOP_NKV];
   T bb[COOP_NKV][2 * COOP_NKV];
-  T tg[COOP_NKV][2 * 32];    // (chi_j, B^ g_l) of the current cycle's chi_j
+  T tg[COOP_NKV][2 * 32];    // (chi_j, B^ g_l) of the current cycle's chi_j (normalised chi_j)
   T z[2 * 32];
   T ainv[2 * 32 * 32];       // A~^{-1}, row-major
+  T ac[2];                   // a_{k-1} / c_{k-1}: rho_k = rho_{k-1} - ac chi'_{k-1}
+  T rr;                      // this CTA's share of |rho_k|^2 (folded into the next reduction)
   int phase;
 };
 
-// row stride of the partial-sum table: a multiple of 4 so that it is read with 16-byte loads
+// row stride of the partial-sum table of the multi-RHS solver: a multiple of 4 (16-byte loads)
 DW_HD int coop_gpad(int grid) { return (grid + 3) & ~3; }
 
-// values staged in shared memory at a time by a grid reduction
+// dynamic shared memory of the cooperative kernel: hop partial sums
 template <typename T>
-__host__ __device__ constexpr int coop_stage_v() { return sizeof(T) == 4 ? 128 : 64; }
-
-// dynamic shared memory of the cooperative kernel: reduction staging + hop partial sums
-template <typename T>
-inline size_t coop_dyn_smem(int grid) {
-  return ((size_t)coop_stage_v<T>() * coop_gpad(grid) + (size_t)COOP_CH * 8 * 64) * sizeof(T);
+inline size_t coop_dyn_smem(int) {
+  return (size_t)COOP_CH * 8 * 64 * sizeof(T);
 }
 
 struct CoopSlice {
@@ -816,52 +821,20 @@ DW_D T warp_allsum(T y) {
   return y;
 }
 
-template <typename T> struct Vec16;
-template <> struct Vec16<float> { using t = float4; static constexpr int n = 4; };
-template <> struct Vec16<double> { using t = double2; static constexpr int n = 2; };
-
-// Sum the nv values sh.cta[0..nv) over all CTAs; result in sh.res (all CTAs).
-// Two partial buffers used alternately: a CTA that runs ahead into the next
-// reduction cannot overwrite partials another CTA is still adding up.
+// Sum the nv values sh.cta[0..nv) over all CTAs; result in sh.res (all CTAs).  Each CTA adds
+// its values in FP64 into accumulator set (phase mod 3); after the barrier every CTA reads the
+// totals past L1.  CTA 0 clears the set used two reductions ahead: that set was last read
+// before this barrier and is next added to after the following one.
 template <typename T>
-DW_D void coop_reduce(cg::grid_group& grid, CoopShared<T>& sh, int nv, T* partial_base, T* stage) {
-  const int G = gridDim.x, Gp = coop_gpad(G);
-  T* partial = partial_base + (size_t)(sh.phase & 1) * Gp * COOP_NV;
+DW_D void coop_reduce(cg::grid_group& grid, CoopShared<T>& sh, int nv, double* acc_base) {
   __syncthreads();
-  if (threadIdx.x < nv) partial[threadIdx.x * Gp + blockIdx.x] = sh.cta[threadIdx.x];
+  double* acc = acc_base + (size_t)(sh.phase % 3) * COOP_NV;
+  if (threadIdx.x < nv) atomicAdd(acc + threadIdx.x, (double)sh.cta[threadIdx.x]);
+  __syncthreads();
   grid.sync();
-  using V = typename Vec16<T>::t;
-  constexpr int VN = Vec16<T>::n;
-  constexpr int SV = coop_stage_v<T>();
-  for (int v0 = 0; v0 < nv; v0 += SV) {
-    const int cv = min(SV, nv - v0);
-    // copy the cv x Gp partials into shared memory: 16-byte asynchronous copies, all in flight
-    const int tot = cv * Gp / VN;
-    const V* src = reinterpret_cast<const V*>(partial + (size_t)v0 * Gp);
-    V* dst = reinterpret_cast<V*>(stage);
-    for (int idx = threadIdx.x; idx < tot; idx += COOP_THREADS) {
-      const unsigned saddr = (unsigned)__cvta_generic_to_shared(dst + idx);
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(src + idx) : "memory");
-    }
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-    __syncthreads();
-    // tpv threads per value (neighbouring lanes), each adding every tpv-th partial with two
-    // accumulators, then a butterfly over the tpv lanes: a fixed order in every CTA
-    int tpv = 32;
-    while (tpv > 1 && tpv * cv > COOP_THREADS) tpv >>= 1;
-    const int j = threadIdx.x / tpv, sub = threadIdx.x - j * tpv;
-    T y0 = 0, y1 = 0;
-    if (j < cv) {
-      const T* row = stage + j * Gp;
-      int q = sub;
-      for (; q + tpv < G; q += 2 * tpv) { y0 += row[q]; y1 += row[q + tpv]; }
-      if (q < G) y0 += row[q];
-    }
-    T y = y0 + y1;
-    for (int o = tpv >> 1; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
-    if (j < cv && sub == 0) sh.res[v0 + j] = y;
-    __syncthreads();
-  }
+  if (threadIdx.x < nv) sh.res[threadIdx.x] = (T)__ldcg(acc + threadIdx.x);
+  if (blockIdx.x == 0 && threadIdx.x < COOP_NV) acc_base[(size_t)((sh.phase + 2) % 3) * COOP_NV + threadIdx.x] = 0.0;
+  __syncthreads();
   if (threadIdx.x == 0) sh.phase += 1;
   __syncthreads();
 }
@@ -922,15 +895,18 @@ DW_D void cta_dots(CoopShared<T>& sh, const cplx<T>* X, size_t xstride, int nvec
   }
 }
 
-// Ns x Ns block times vector, loads issued up front: lane = output row, x broadcast by shuffles
+// Ns x Ns block times vector, loads issued up front: lane = output row, x broadcast by shuffles.
+// The vector is src - cs * corr when corr is given (the residual formed on the fly).
 template <typename T, int NS>
 struct RowLoad {
   cplx<T> m[NS];
   cplx<T> x;
-  DW_D void load(const cplx<T>* __restrict__ Mb, const cplx<T>* __restrict__ sv, int lane) {
+  DW_D void load(const cplx<T>* __restrict__ Mb, const cplx<T>* __restrict__ sv, const cplx<T>* __restrict__ cv,
+                 cplx<T> cs, int lane) {
 #pragma unroll
     for (int c = 0; c < NS; ++c) m[c] = lane < NS ? Mb[c * NS + lane] : cplx<T>{T(0), T(0)};
     x = lane < NS ? sv[lane] : cplx<T>{T(0), T(0)};
+    if (cv && lane < NS) x -= cs * cv[lane];
   }
   DW_D cplx<T> mv() const {
     cplx<T> acc = {T(0), T(0)};
@@ -943,13 +919,13 @@ struct RowLoad {
   }
 };
 
-// out[r] = base[r] + out_sign * sum_d M[list[r]][d] src[lnb[r][d]] for this CTA's block rows.
-// Rows in chunks of COOP_CH; warp d computes direction d of every row of the chunk (FP32:
-// the next row's block is loaded while the current one is multiplied), the 8 partial sums
-// meet in shared memory (hp, COOP_CH x 8 x 32 complex).
+// out[r] = base[r] + out_sign * sum_d M[list[r]][d] (src - cs corr)[lnb[r][d]] for this CTA's block
+// rows (corr may be null).  Rows in chunks of COOP_CH; warp d computes direction d of every row of
+// the chunk (FP32: the next row's block is loaded while the current one is multiplied), the 8
+// partial sums meet in shared memory (hp, COOP_CH x 8 x 32 complex).
 template <typename T, int NS>
 DW_D void coop_hop(int nrow, int Ns, const int* list, const int* lnb, const T* M, const cplx<T>* src,
-                   const cplx<T>* base, cplx<T>* out, T out_sign, cplx<T>* hp) {
+                   const cplx<T>* corr, cplx<T> cs, const cplx<T>* base, cplx<T>* out, T out_sign, cplx<T>* hp) {
   const int ns = NS ? NS : Ns;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const cplx<T>* Mc = reinterpret_cast<const cplx<T>*>(M);
@@ -966,8 +942,9 @@ DW_D void coop_hop(int nrow, int Ns, const int* list, const int* lnb, const T* M
       constexpr int NB = COOP_HOP_DEPTH;
       RowLoad<T, (PIPE ? NS : 1)> buf[NB];
       auto load_row = [&](RowLoad<T, (PIPE ? NS : 1)>& b, int q) {
-        b.load(Mc + ((size_t)__shfl_sync(0xffffffffu, myL, q) * 8 + w) * NS * NS,
-               src + (size_t)__shfl_sync(0xffffffffu, myj, q) * NS, lane);
+        const size_t j = (size_t)__shfl_sync(0xffffffffu, myj, q) * NS;
+        b.load(Mc + ((size_t)__shfl_sync(0xffffffffu, myL, q) * 8 + w) * NS * NS, src + j, corr ? corr + j : nullptr,
+               cs, lane);
       };
 #pragma unroll
       for (int u = 0; u < NB - 1; ++u)
@@ -985,8 +962,15 @@ DW_D void coop_hop(int nrow, int Ns, const int* list, const int* lnb, const T* M
     } else {
       for (int q = 0; q < nr; ++q) {
         const int L = __shfl_sync(0xffffffffu, myL, q), j = __shfl_sync(0xffffffffu, myj, q);
-        hp[(q * 8 + w) * 32 + lane] = warp_mv<T, NS>(Mc + ((size_t)L * 8 + w) * ns * ns, src + (size_t)j * ns, ns,
-                                                     lane, cplx<T>{T(0), T(0)});
+        const cplx<T>* m = Mc + ((size_t)L * 8 + w) * ns * ns;
+        cplx<T> x = lane < ns ? src[(size_t)j * ns + lane] : cplx<T>{T(0), T(0)};
+        if (corr && lane < ns) x -= cs * corr[(size_t)j * ns + lane];
+        cplx<T> acc = {T(0), T(0)};
+        for (int col = 0; col < ns; ++col) {
+          const cplx<T> xc = {__shfl_sync(0xffffffffu, x.re, col), __shfl_sync(0xffffffffu, x.im, col)};
+          if (lane < ns) acc += m[(size_t)col * ns + lane] * xc;
+        }
+        hp[(q * 8 + w) * 32 + lane] = acc;
       }
     }
     __syncthreads();
@@ -1009,11 +993,12 @@ DW_D void coop_hop(int nrow, int Ns, const int* list, const int* lnb, const T* M
 template <typename T, int NS>
 DW_D void coop_bhat(cg::grid_group& grid, const CoopArgs<T>& a, const cplx<T>* x, cplx<T>* tmpo, cplx<T>* y,
                     cplx<T>* hp) {
-  coop_hop<T, NS>(a.No, a.Ns, a.list_o, a.lnb_o, a.M, x, nullptr, tmpo, T(1), hp);    // tmpo = M_oe x
+  const cplx<T> zero = {T(0), T(0)};
+  coop_hop<T, NS>(a.No, a.Ns, a.list_o, a.lnb_o, a.M, x, nullptr, zero, nullptr, tmpo, T(1), hp);   // tmpo = M_oe x
   __syncthreads();
   grid.sync();
   __syncthreads();
-  coop_hop<T, NS>(a.Ne, a.Ns, a.list_e, a.lnb_e, a.M, tmpo, x, y, T(-1), hp);       // y = x - M_eo tmpo
+  coop_hop<T, NS>(a.Ne, a.Ns, a.list_e, a.lnb_e, a.M, tmpo, nullptr, zero, x, y, T(-1), hp);      // y = x - M_eo tmpo
   __syncthreads();
   grid.sync();
   __syncthreads();
@@ -1039,12 +1024,12 @@ DW_D void coop_z(CoopShared<T>& sh, int Ns) {
 // add_to += g z is applied instead.  Elementwise parts on the CTA's rows, no trailing barrier.
 template <typename T, int NS>
 DW_D void coop_PL(cg::grid_group& grid, CoopShared<T>& sh, const CoopArgs<T>& a, cplx<T>* u, const cplx<T>* gsrc,
-                  const cplx<T>* bgsrc, cplx<T>* add_to, T* stage, const CoopSlice& sl) {
+                  const cplx<T>* bgsrc, cplx<T>* add_to, const CoopSlice& sl) {
   constexpr int NSM = NS ? NS : 32;
   const size_t n = (size_t)a.Ne * a.Ns;
   const int Ns = NS ? NS : a.Ns;
   cta_dots<T>(sh, gsrc, n, Ns, u, sl, 0);
-  coop_reduce(grid, sh, 2 * Ns, a.partial, stage);
+  coop_reduce(grid, sh, 2 * Ns, a.acc);
   coop_z(sh, Ns);
   __syncthreads();
   cplx<T>* tgt = add_to ? add_to : u;
@@ -1069,13 +1054,13 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_kernel(CoopAr
   cg::grid_group grid = cg::this_grid();
   __shared__ CoopShared<T> sh;
   extern __shared__ __align__(16) unsigned char coop_dyn[];
-  T* stage = reinterpret_cast<T*>(coop_dyn);                                          // [stage_v][Gp]
-  cplx<T>* hp = reinterpret_cast<cplx<T>*>(stage + (size_t)coop_stage_v<T>() * coop_gpad(gridDim.x));  // [COOP_CH][8][32]
+  cplx<T>* hp = reinterpret_cast<cplx<T>*>(coop_dyn);                // [COOP_CH][8][32]
   const int ns = NS ? NS : a.Ns;
   const size_t n = (size_t)a.Ne * ns;
   const CoopSlice sl = coop_rows_slice(a.Ne, ns);
   const int nkv = a.nkv;
   const int na = a.a3 ? 2 * ns : 0;          // reduced values of the A.3 projection
+  const cplx<T> zero = {T(0), T(0)};
   if (threadIdx.x == 0) sh.phase = 0;
   if (a.a3) {
     const cplx<T>* Ai = reinterpret_cast<const cplx<T>*>(a.Ainv);
@@ -1086,58 +1071,72 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_kernel(CoopAr
   }
   __syncthreads();
   cplx<T>* W = reinterpret_cast<cplx<T>*>(a.work);
-  cplx<T>* rho = W + (size_t)2 * nkv * n;
-  cplx<T>* tmpo = rho + n;
-  cplx<T>* t = tmpo + n;
-  cplx<T>* rhsd = t + n;
+  cplx<T>* rhob[2] = {W + (size_t)2 * nkv * n, W + (size_t)(2 * nkv + 1) * n};
+  cplx<T>* tmpo = W + (size_t)(2 * nkv + 2) * n;
+  cplx<T>* t = W + (size_t)(2 * nkv + 3) * n;
+  cplx<T>* rhsd = W + (size_t)(2 * nkv + 4) * n;
   const cplx<T>* b = reinterpret_cast<const cplx<T>*>(a.b);
   const cplx<T>* g = reinterpret_cast<const cplx<T>*>(a.g);
   const cplx<T>* Bg = reinterpret_cast<const cplx<T>*>(a.Bg);
   cplx<T>* v = reinterpret_cast<cplx<T>*>(a.v);
-  auto chi = [&](int k) { return W + (size_t)k * n; };
+  auto chi = [&](int k) { return W + (size_t)k * n; };      // chi'_k, unnormalised (norm c_k)
   auto xi = [&](int k) { return W + (size_t)(nkv + k) * n; };
   auto slice = [&](auto&& f) {
     for (size_t i = sl.s0 + threadIdx.x; i < sl.s1; i += COOP_THREADS) f(i);
   };
 
   // rhsd = P~_L b, rho = rhsd, v = 0
+  int cur = 0;                               // rhob[cur] holds rho_k on this CTA's rows
   slice([&](size_t i) { rhsd[i] = b[i]; });
-  if (a.a3) coop_PL<T, NS>(grid, sh, a, rhsd, g, Bg, nullptr, stage, sl);
+  if (a.a3) coop_PL<T, NS>(grid, sh, a, rhsd, g, Bg, nullptr, sl);
   T s1[1] = {0};
   slice([&](size_t i) {
     const cplx<T> x = rhsd[i];
-    rho[i] = x;
-    v[i] = {T(0), T(0)};
+    rhob[0][i] = x;
+    v[i] = zero;
     s1[0] += x.re * x.re + x.im * x.im;
   });
   cta_sum<T, 1>(sh, s1);
-  coop_reduce(grid, sh, 1, a.partial, stage);
+  if (threadIdx.x == 0) sh.rr = sh.cta[0];
+  coop_reduce(grid, sh, 1, a.acc);
   const T bn = sqrt(sh.res[0]);
   T rn = bn;
   int total = 0;
   while (bn > 0 && (double)rn > a.tol * (double)bn && total < a.maxit) {
     int k = 0;
+    T rn2 = rn * rn;                         // |rho_k|^2 (exact at the start of a cycle)
     for (; k < nkv && total < a.maxit; ++k) {
       cplx<T>* ck = chi(k);
       cplx<T>* xk = xi(k);
-      // xi_k = rho;  chi_k = B^ rho  (rho is stable until the update below); the even hop
-      // writes this CTA's own rows, so no grid barrier follows it
-      slice([&](size_t i) { xk[i] = rho[i]; });
-      coop_hop<T, NS>(a.No, ns, a.list_o, a.lnb_o, a.M, rho, nullptr, tmpo, T(1), hp);
+      cplx<T>* rk = rhob[cur];
+      // xi_k = rho_k;  chi_k = B^ rho_k.  The odd hop reads rho_k of other CTAs as
+      // rho_{k-1} - ac chi'_{k-1} (both final since the last reduction); the even hop writes
+      // this CTA's own rows, so no grid barrier follows it
+      slice([&](size_t i) { xk[i] = rk[i]; });
+      const cplx<T> acs = k > 0 ? cplx<T>{sh.ac[0], sh.ac[1]} : zero;
+      coop_hop<T, NS>(a.No, ns, a.list_o, a.lnb_o, a.M, k > 0 ? rhob[cur ^ 1] : rk, k > 0 ? chi(k - 1) : nullptr,
+                      acs, nullptr, tmpo, T(1), hp);
       __syncthreads();
       grid.sync();
       __syncthreads();
-      coop_hop<T, NS>(a.Ne, ns, a.list_e, a.lnb_e, a.M, tmpo, rho, ck, T(-1), hp);
-      // one reduction: u = g^+ chi_k (A.3) and the raw coefficients (chi_j, chi_k), j < k
+      coop_hop<T, NS>(a.Ne, ns, a.list_e, a.lnb_e, a.M, tmpo, nullptr, zero, rk, ck, T(-1), hp);
+      // one reduction: u = g^+ chi_k (A.3), the raw coefficients (chi'_j, chi_k), j < k, and |rho_k|^2
       if (a.a3) cta_dots<T>(sh, g, n, ns, ck, sl, 0);
       if (k > 0) cta_dots<T>(sh, W, n, k, ck, sl, na);
-      if (na + 2 * k > 0) coop_reduce(grid, sh, na + 2 * k, a.partial, stage);
+      __syncthreads();
+      if (threadIdx.x == 0) sh.cta[na + 2 * k] = sh.rr;
+      coop_reduce(grid, sh, na + 2 * k + 1, a.acc);
+      rn2 = sh.res[na + 2 * k];
+      rn = sqrt(rn2);
+      if ((double)rn <= a.tol * (double)bn) break;    // rho_k already converged: chi_k unused
       if (a.a3) coop_z(sh, ns);
       __syncthreads();
-      // coefficients of the projected vector P~_L chi_k: (chi_j, chi_k) - sum_l z_l (chi_j, B^ g_l)
+      // coefficients of the projected vector P~_L chi_k on the normalised chi_j:
+      // (chi'_j, chi_k) / c_j - sum_l z_l (chi_j, B^ g_l)
       if (threadIdx.x < k) {
         const int j = threadIdx.x;
-        T br = sh.res[na + 2 * j], bi = sh.res[na + 2 * j + 1];
+        const T ic = T(1) / sh.c[j];
+        T br = sh.res[na + 2 * j] * ic, bi = sh.res[na + 2 * j + 1] * ic;
         if (a.a3) {
           for (int l = 0; l < ns; ++l) {
             const T zr = sh.z[2 * l], zi = sh.z[2 * l + 1], tr = sh.tg[j][2 * l], ti = sh.tg[j][2 * l + 1];
@@ -1149,7 +1148,7 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_kernel(CoopAr
         sh.bb[j][2 * k + 1] = bi;
       }
       __syncthreads();
-      // chi_k <- P~_L chi_k - sum_j b_jk chi_j ; then (chi_k, rho), |chi_k|^2 and (B^ g_l, chi_k)
+      // chi'_k = P~_L chi_k - sum_j b_jk chi'_j / c_j ; then (chi'_k, rho_k), |chi'_k|^2, (B^ g_l, chi'_k)
       T s3[3] = {0, 0, 0};
       slice([&](size_t i) {
         cplx<T> y = ck[i];
@@ -1160,38 +1159,53 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_kernel(CoopAr
         }
 #pragma unroll
         for (int j = 0; j < COOP_NKV; ++j)
-          if (j < k) y -= cplx<T>{sh.bb[j][2 * k], sh.bb[j][2 * k + 1]} * chi(j)[i];
+          if (j < k) {
+            const T ic = T(1) / sh.c[j];
+            y -= cplx<T>{sh.bb[j][2 * k] * ic, sh.bb[j][2 * k + 1] * ic} * chi(j)[i];
+          }
         ck[i] = y;
-        const cplx<T> r = rho[i];
+        const cplx<T> r = rk[i];
         s3[0] += y.re * r.re + y.im * r.im;
         s3[1] += y.re * r.im - y.im * r.re;
         s3[2] += y.re * y.re + y.im * y.im;
       });
       cta_sum<T, 3>(sh, s3);
       if (a.a3) cta_dots<T>(sh, Bg, n, ns, ck, sl, 3);
-      coop_reduce(grid, sh, 3 + na, a.partial, stage);
+      coop_reduce(grid, sh, 3 + na, a.acc);
       const T cn = sqrt(sh.res[2]);
       if (!(cn > 0)) break;
       const T inv = T(1) / cn;
-      const T ar = sh.res[0] * inv, ai = sh.res[1] * inv;
-      if (threadIdx.x == 0) { sh.c[k] = cn; sh.a[2 * k] = ar; sh.a[2 * k + 1] = ai; }
-      if (a.a3 && threadIdx.x < ns) {     // (chi_k, B^ g_l) = conj((B^ g_l, chi_k)) / c_k
+      const T ar = sh.res[0] * inv, ai = sh.res[1] * inv;       // a_k = (chi_k, rho_k), chi_k = chi'_k / c_k
+      if (threadIdx.x == 0) {
+        sh.c[k] = cn;
+        sh.a[2 * k] = ar;
+        sh.a[2 * k + 1] = ai;
+      }
+      if (a.a3 && threadIdx.x < ns) {     // (chi_k, B^ g_l) = conj((B^ g_l, chi'_k)) / c_k
         sh.tg[k][2 * threadIdx.x] = sh.res[3 + 2 * threadIdx.x] * inv;
         sh.tg[k][2 * threadIdx.x + 1] = -sh.res[3 + 2 * threadIdx.x + 1] * inv;
       }
+      // rho_{k+1} = rho_k - (a_k / c_k) chi'_k on this CTA's rows, into the other buffer
+      const cplx<T> ack = {ar * inv, ai * inv};
       s1[0] = 0;
-      const cplx<T> ak = {ar, ai};
+      cplx<T>* rn1 = rhob[cur ^ 1];
       slice([&](size_t i) {
-        const cplx<T> x = inv * ck[i];
-        ck[i] = x;
-        const cplx<T> y = rho[i] - ak * x;
-        rho[i] = y;
+        const cplx<T> y = rk[i] - ack * ck[i];
+        rn1[i] = y;
         s1[0] += y.re * y.re + y.im * y.im;
       });
       cta_sum<T, 1>(sh, s1);
-      coop_reduce(grid, sh, 1, a.partial, stage);
-      rn = sqrt(sh.res[0]);
+      if (threadIdx.x == 0) {
+        sh.rr = sh.cta[0];
+        sh.ac[0] = ack.re;
+        sh.ac[1] = ack.im;
+      }
+      __syncthreads();
+      cur ^= 1;
       ++total;
+      // |rho_{k+1}|^2 = |rho_k|^2 - |a_k|^2 (one step of the recursion from the exact |rho_k|^2)
+      const T est = rn2 - (ar * ar + ai * ai);
+      rn = est > 0 ? sqrt(est) : T(0);
       if ((double)rn <= a.tol * (double)bn) { ++k; break; }
     }
     // back substitution by warp 0 (lane i holds row i), then v += sum beta_k xi_k
@@ -1221,15 +1235,17 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_kernel(CoopAr
     if (k == 0) break;
     // true residual of the deflated system
     coop_bhat<T, NS>(grid, a, v, tmpo, t, hp);
-    if (a.a3) coop_PL<T, NS>(grid, sh, a, t, g, Bg, nullptr, stage, sl);
+    if (a.a3) coop_PL<T, NS>(grid, sh, a, t, g, Bg, nullptr, sl);
     s1[0] = 0;
+    cplx<T>* r0 = rhob[cur];
     slice([&](size_t i) {
       const cplx<T> y = rhsd[i] - t[i];
-      rho[i] = y;
+      r0[i] = y;
       s1[0] += y.re * y.re + y.im * y.im;
     });
     cta_sum<T, 1>(sh, s1);
-    coop_reduce(grid, sh, 1, a.partial, stage);
+    if (threadIdx.x == 0) sh.rr = sh.cta[0];
+    coop_reduce(grid, sh, 1, a.acc);
     rn = sqrt(sh.res[0]);
   }
   if (a.a3) {
@@ -1237,7 +1253,7 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_kernel(CoopAr
     grid.sync();
     coop_bhat<T, NS>(grid, a, v, tmpo, t, hp);
     slice([&](size_t i) { t[i] = b[i] - t[i]; });
-    coop_PL<T, NS>(grid, sh, a, t, g, g, v, stage, sl);     // v += g z,  z = A~^{-1} g^+ t
+    coop_PL<T, NS>(grid, sh, a, t, g, g, v, sl);     // v += g z,  z = A~^{-1} g^+ t
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.out[0] = total;
@@ -2075,7 +2091,8 @@ static int little_gcr_coop(dfl_ctx* d, const T* b, T* v, double tol, int maxit, 
   a.M = Mp<T>(d); a.g = d->a3 ? gp<T>(d) : nullptr; a.Bg = d->a3 ? Bgp<T>(d) : nullptr;
   a.Ainv = d->a3 ? Ainvp<T>(d) : nullptr; a.b = b; a.v = v;
   a.work = lwork<T>(d, 0);
-  a.partial = reinterpret_cast<T*>(d->coop_partial);
+  a.acc = d->coop_partial;                                   // [3][COOP_NV] accumulators
+  DW_CUDA(cudaMemsetAsync(d->coop_partial, 0, 3 * COOP_NV * sizeof(double), s));
   a.out = d->coop_out + (d->defer_slot >= 0 ? 2 * d->defer_slot : 0);
   a.tol = tol;
   void* args[] = {&a};
@@ -2878,6 +2895,8 @@ static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_c
   if (p->boot_steps > 0) {
     if ((rc = bootstrap_steps(c, p, work, ip, &boot_steps_done, &boot_gcr))) return rc;
   }
+  // the relaxation measure (5.2) of the generated fields (FP32 fields only; the network path has it)
+  if (!use_net && ip == DW_F32 && (rc = rho_measure((const float*)work, &rho_out))) return rc;
   // ---- block Gram-Schmidt in FP64
   DW_CUDA(cudaMalloc(&d->basis64, (size_t)Ns * 24 * V * sizeof(double)));
   if (ip == DW_F64) DW_CUDA(cudaMemcpyAsync(d->basis64, work, fb * Ns, cudaMemcpyDeviceToDevice, s));

