@@ -307,6 +307,25 @@ int cgnr_solve(dw_ctx* ctx, double tol, int maxit, const double* eta_dev, double
 int bicgstab_solve(dw_ctx* ctx, double tol, int maxit, const double* eta_dev, double* psi_dev, int* iters,
                    double* relres, void* stream);
 
+/* The nev lowest eigenvalues and eigenvectors of D^+ D by Chebyshev-accelerated subspace iteration,
+ * the method the paper uses for all its eigenmode computations (Section 2.2): a block of nev + nbuf
+ * fields (start: canonical complex128[nev+nbuf][V][4][3], random numbers given by the caller) is
+ * filtered by the Chebyshev polynomial of degree `degree` on [a, b] (a: largest Ritz value of the
+ * block, b: 1.1 x a power-iteration estimate of the largest eigenvalue), re-orthonormalised and
+ * Rayleigh-Ritz projected (FP64) until ||D^+D x_i - theta_i x_i|| <= tol theta_i for the nev lowest
+ * or maxit iterations (DW_ENOTCONV).  prec: precision of the filter (DW_F32 or DW_F64).
+ * modes: canonical complex128[nev][V][4][3] (orthonormal), evals / resid: nev doubles (resid may be
+ * NULL).  nev + nbuf <= 128.  Synchronous; the workspace (3 FP64 and 3 prec blocks of nev + nbuf
+ * fields) is kept by the context. */
+int lowmodes_solve(dw_ctx* ctx, int nev, int nbuf, int degree, double tol, int maxit, int prec,
+                   const double* start_dev, double* modes_dev, double* evals, double* resid, int* iters,
+                   void* stream);
+/* Deficits (3.15) eps_f = ||(1 - P) psi_f||^2 / ||psi_f||^2 of nf fields (canonical
+ * complex128[nf][V][4][3], device) with respect to the block subspace of d (projector (4.1), FP64
+ * arithmetic on the stored basis) -- the local-coherence measurement of Section 5.2.  eps: nf
+ * doubles (host).  Synchronous. */
+int dfl_deficits(dfl_ctx* d, int nf, const double* fields_dev, double* eps, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

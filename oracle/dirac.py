@@ -169,3 +169,12 @@ class WilsonClover:
             E[np.arange(j1 - j0), np.arange(j0, j1)] = 1.0
             M[:, j0:j1] = self.apply(E.reshape(-1, self.V, 4, 3)).reshape(j1 - j0, n).T
         return M
+
+
+def low_modes(D: WilsonClover, k: int):
+    """The k lowest eigenvalues and eigenvectors of D^dag D (Section 2.2 works with this hermitian
+    operator): the dense Hermitian eigendecomposition, the definition.  Small lattices only.
+    Returns (w[k] ascending, v[k, V, 4, 3])."""
+    M = D.dense()
+    w, v = np.linalg.eigh(M.conj().T @ M)
+    return w[:k], v[:, :k].T.reshape(k, D.V, 4, 3)

@@ -353,7 +353,8 @@ struct dw_ctx {
   double* d_red = nullptr;                // reduction scratch
   unsigned* d_count = nullptr;
   double* h_red = nullptr;                // pinned host mirror
-  WsArena ws_solve[3];                    // solver workspaces: [0] GCR, [1] batched GCR, [2] CGNR
+  WsArena ws_solve[4];                    // solver workspaces: [0] GCR, [1] batched GCR, [2] CGNR and
+                                          // BiCGstab, [3] low-mode subspace iteration
 };
 
 // DW_OK when the calling thread's current device is the context's device; otherwise DW_EINVAL

@@ -2247,6 +2247,7 @@ int little_solve_f64(dfl_ctx* d, const double* w, double* v, double tol, int max
   return little_solve_t(d, w, v, tol, maxit, nkv, it, rr, s);
 }
 int dfl_nlittle(const dfl_ctx* d) { return d->N; }
+dw_ctx* dfl_operator(const dfl_ctx* d) { return d->c; }
 // FP64-accurate solution of A v = w (little operator (3.2)/(A.1)) by mixed-precision iterative
 // refinement: FP32 even-odd deflated GCR solves for the corrections, FP64 residuals w - A v with the
 // FP64 operator.  Used for the restart corrections of the mixed-precision solver, so every little

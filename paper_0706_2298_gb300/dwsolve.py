@@ -94,6 +94,9 @@ _SIGNATURES = {
     "gcr_solve": (C.c_int, [_P, _P, C.POINTER(SolParams), C.c_int, _P, _P, C.POINTER(SolInfo), _P]),
     "dw_autotune": (C.c_int, [_P, C.c_int, C.c_char_p, C.c_size_t]),
     "cgnr_solve": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.POINTER(C.c_int), C.POINTER(C.c_double), _P]),
+    "lowmodes_solve": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, _P, _P,
+                                 C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int), _P]),
+    "dfl_deficits": (C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_double), _P]),
     "bicgstab_solve": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.POINTER(C.c_int), C.POINTER(C.c_double), _P]),
     "ptnet_weight_count": (C.c_size_t, [C.c_int]),
     "ptnet_forward": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, _P, _P]),
@@ -335,6 +338,22 @@ def bicgstab_solve(ctx: Ctx, tol, maxit, eta_dev, psi_dev, stream=None):
     rc = _check(lib().bicgstab_solve(ctx.handle, float(tol), int(maxit), _ptr(_as_f64(eta_dev)), _ptr(_as_f64(psi_dev)),
                                      C.byref(it), C.byref(rr), _stream(stream)), ok=(DW_OK, DW_ENOTCONV))
     return rc, it.value, rr.value
+
+
+def lowmodes_solve(ctx: Ctx, nev, nbuf, start_dev, modes_dev, degree=24, tol=1e-8, maxit=100, prec=DW_F64,
+                   stream=None):
+    ev, rs, it = (C.c_double * nev)(), (C.c_double * nev)(), C.c_int()
+    rc = _check(lib().lowmodes_solve(ctx.handle, int(nev), int(nbuf), int(degree), float(tol), int(maxit), int(prec),
+                                     _ptr(_as_f64(start_dev)), _ptr(_as_f64(modes_dev)), ev, rs, C.byref(it),
+                                     _stream(stream)), ok=(DW_OK, DW_ENOTCONV))
+    return rc, list(ev), list(rs), it.value
+
+
+def dfl_deficits(d: Dfl, fields_dev, stream=None):
+    nf = fields_dev.shape[0]
+    eps = (C.c_double * nf)()
+    _check(lib().dfl_deficits(d.handle, int(nf), _ptr(_as_f64(fields_dev)), eps, _stream(stream)))
+    return list(eps)
 
 
 def dw_autotune(ctx: Ctx, nrhs=1) -> dict:

@@ -194,3 +194,30 @@ def test_dense_4x4(D4, dense4):
     assert info.converged
     cond = np.linalg.cond(dense4)
     assert np.linalg.norm(x - x_dense) <= 10 * cond * 1e-12 * np.linalg.norm(x_dense)
+
+
+def test_low_modes_free_field_closed_form():
+    """Lowest eigenvalues of D^dag D for the free field: on the plane wave with momentum p (p0
+    antiperiodic), D = m0 + sum(1 - cos p) + i sum gamma sin p, so D^dag D = (m0 + sum(1 - cos p))^2 +
+    sum sin^2 p on all 12 spin-colour components; the 12 lowest eigenvalues form one multiplet per
+    minimising momentum (here p = (+-pi/4, 0, 0, 0): 24 equal eigenvalues)."""
+    from oracle.dirac import low_modes
+    L = (4, 2, 2, 2)
+    m0 = -0.2
+    D = WilsonClover(L, synth.unit_gauge(L).numpy(), m0, 1.0)
+    w, v = low_modes(D, 30)
+    vals = []
+    for n0 in range(L[0]):
+        for n in np.ndindex(*L[1:]):
+            p = [(2 * n0 + 1) * np.pi / L[0]] + [2 * np.pi * n[k] / L[k + 1] for k in range(3)]
+            vals.append((m0 + sum(1 - np.cos(x) for x in p)) ** 2 + sum(np.sin(x) ** 2 for x in p))
+    vals = np.sort(np.repeat(vals, 12))
+    assert np.allclose(w, vals[:30], rtol=1e-12, atol=1e-12)
+    # eigenvectors: D^dag D v = w v (D^dag = gamma5 D gamma5), orthonormal
+    g5 = np.diag([1, 1, -1, -1]).astype(complex)
+    for i in (0, 23, 29):
+        x = v[i]
+        y = np.einsum("st,vtc->vsc", g5, D.apply(np.einsum("st,vtc->vsc", g5, D.apply(x))))
+        assert np.linalg.norm(y - w[i] * x) <= 1e-11 * np.linalg.norm(y)
+    G = v.reshape(30, -1).conj() @ v.reshape(30, -1).T
+    assert np.allclose(G, np.eye(30), atol=1e-12)
