@@ -36,6 +36,14 @@ WORKLOADS = {
                     n_inv=11, ncy=4, nmr=4, nkv=16, tol=1e-10, gauge_seed=1, source_seed=2, start_seed=3),
     "8^4": dict(L=(8, 8, 8, 8), m0=-0.2, csw=1.0, sap_bs=(4, 4, 4, 4), dfl_bs=(4, 4, 4, 4), Ns=8,
                 n_inv=11, ncy=4, nmr=4, nkv=16, tol=1e-10, gauge_seed=1, source_seed=2, start_seed=3),
+    # 64 x 32^3, 8^4 deflation blocks, Ns = 20, 12 point sources batched
+    "32^3x64": dict(L=(64, 32, 32, 32), m0=0.0, csw=1.0, sap_bs=(4, 4, 4, 4), dfl_bs=(8, 8, 8, 8), Ns=20,
+                    n_inv=11, ncy=4, nmr=4, nkv=16, tol=1e-10, gauge_seed=1, source_seed=2, start_seed=3),
+    # 96 x 48^3, 8^4 deflation blocks, Ns = 32 (BF16 basis 16 GB); the 12 point sources one after the
+    # other (a lockstep batch of 12 would need 12 x 32 Krylov fields at once)
+    "48^3x96": dict(L=(96, 48, 48, 48), m0=0.0, csw=1.0, sap_bs=(4, 4, 4, 4), dfl_bs=(8, 8, 8, 8), Ns=32,
+                    n_inv=11, ncy=4, nmr=4, nkv=16, tol=1e-10, gauge_seed=1, source_seed=2, start_seed=3,
+                    batch=False),
 }
 # Mass of the 24^3x48 workload: the most nearly critical value of a CGNR iteration-count scan
 # (workload_masses.json, written by tune_mass.py; the 2000-iteration rule is out of reach for
@@ -568,7 +576,7 @@ def main():
         eta12 = synth.point_sources(L).cuda()
         psi12 = torch.empty_like(eta12)
         res = {}
-        for mode in ("batched", "sequential"):
+        for mode in (("batched", "sequential") if wl.get("batch", True) else ("sequential",)):
             if mode == "sequential":
                 os.environ["DW_BATCH"] = "0"
             rc, inf12 = dw.gcr_solve(ctx, dfl, p_mixed, 12, eta12, psi12)      # warm-up (captures graphs)
@@ -585,7 +593,8 @@ def main():
                          "gcr_iterations_max": max(i.iterations for i in inf12),
                          "launches": dw.dw_launch_count() - n0b}
         batch = {"workload": f"{args.workload}, 12 point sources (spin-colour unit vectors at the origin)",
-                 **res, "speedup_batched": res["sequential"]["s_total"] / res["batched"]["s_total"],
+                 **res, "speedup_batched": (res["sequential"]["s_total"] / res["batched"]["s_total"]
+                                            if "batched" in res else None),
                  "autotune": tune}
         del eta12, psi12
 

@@ -1923,7 +1923,25 @@ extern "C" int dfl_prolong(dfl_ctx* d, int prec, const void* c, void* psi, void*
 }
 extern "C" int dfl_basis_export(dfl_ctx* d, double* canon, void* stream) {
   if (!d || !canon) { dw_set_error("dfl_basis_export: bad argument"); return DW_EINVAL; }
-  return dw_unpack(d->c, DW_F64, d->Ns, d->basis64, canon, stream);
+  if (d->basis64) return dw_unpack(d->c, DW_F64, d->Ns, d->basis64, canon, stream);
+  // BF16 basis: expand to FP64 in a temporary field block
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t V = d->c->V;
+  double* tmp = nullptr;
+  DW_CUDA(cudaMallocAsync((void**)&tmp, (size_t)d->Ns * 24 * V * sizeof(double), s));
+  dequantize_kernel<<<(unsigned)((V * d->Ns + 255) / 256), 256, 0, s>>>(V, d->Ns, d->basis16, tmp); dw_note_launch();
+  int rc = dw_unpack(d->c, DW_F64, d->Ns, tmp, canon, stream);
+  cudaFreeAsync(tmp, s);
+  return rc;
+}
+
+// A BF16 basis needs its FP64 expansion only while the little operator is assembled: drop it
+// afterwards (the restriction and prolongation kernels read the BF16 basis).  Saves Ns FP64 fields.
+static void drop_basis64(dfl_ctx* d) {
+  if (d->basis16 && d->basis64) {
+    cudaFree(d->basis64);
+    d->basis64 = nullptr;
+  }
 }
 extern "C" int little_apply(dfl_ctx* d, const double* v, double* w, void* stream) {
   if (!d || !v || !w || v == w) { dw_set_error("little_apply: bad argument"); return DW_EINVAL; }
@@ -2948,6 +2966,7 @@ static int build_impl(dw_ctx* c, const dfl_params* p, const double* start, dfl_c
   }
   auto t1 = std::chrono::steady_clock::now();
   if ((rc = little_setup(c, d, nullptr))) return rc;
+  drop_basis64(d);
   auto t2 = std::chrono::steady_clock::now();
   if (info) {
     info->seconds = std::chrono::duration<double>(t2 - t0).count();
@@ -3046,14 +3065,20 @@ extern "C" int dfl_retarget(const dfl_ctx* src, dw_ctx* c, dfl_ctx** out, dfl_in
   auto fail = [&](int r) { dfl_destroy(d); return r; };
   if ((rc = build_tables(c, d))) return fail(rc);
   cudaError_t e = cudaMalloc(&d->basis64, Ns * 24 * V * sizeof(double));
-  if (e == cudaSuccess) e = cudaMemcpy(d->basis64, src->basis64, Ns * 24 * V * sizeof(double), cudaMemcpyDeviceToDevice);
+  if (e == cudaSuccess && src->basis64)
+    e = cudaMemcpy(d->basis64, src->basis64, Ns * 24 * V * sizeof(double), cudaMemcpyDeviceToDevice);
   if (e == cudaSuccess && src->basis16) {
     e = cudaMalloc(&d->basis16, Ns * 3 * V * sizeof(uint4));
     if (e == cudaSuccess) e = cudaMemcpy(d->basis16, src->basis16, Ns * 3 * V * sizeof(uint4), cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess && !src->basis64) {
+      dequantize_kernel<<<(unsigned)((V * Ns + 255) / 256), 256>>>(V, (int)Ns, d->basis16, d->basis64); dw_note_launch();
+      e = cudaGetLastError();
+    }
   }
   if (e != cudaSuccess) return fail(dw_cuda_fail(e, "dfl_retarget"));
   d->graw = src->graw;
   if ((rc = little_setup(c, d, nullptr))) return fail(rc);
+  drop_basis64(d);
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   fill_info(d, info, secs, secs, 0);
   *out = d;
@@ -3168,6 +3193,7 @@ extern "C" int dfl_load(dw_ctx* c, const char* path, dfl_ctx** out, dfl_info* in
   const bool same_op = h.gauge_hash == c->gauge_hash && h.m0 == c->p.m0 && h.csw == c->p.csw &&
                        h.antiperiodic == c->p.antiperiodic;
   if ((rc = little_setup(c, d, same_op ? B.data() : nullptr))) return fail(rc);
+  drop_basis64(d);
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   fill_info(d, info, secs, secs, same_op ? 1 : 0);
   *out = d;
