@@ -387,6 +387,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-batch", action="store_true", help="skip the 12 point-source batched solve")
     ap.add_argument("--no-coherence", action="store_true", help="skip the low-mode / local-coherence measurement")
+    ap.add_argument("--no-ptnet", action="store_true", help="skip the network-layer timing")
     ap.add_argument("--no-table1", action="store_true",
                     help="skip the solver comparison over masses and the subspace generation variants")
     ap.add_argument("--profile-case", choices=["dirac-sap", "little", "batch12"], default=None,
@@ -536,6 +537,7 @@ def main():
 
     # ---- plain FP64 path (same algorithm, FP64 everywhere, FP64 basis)
     plain = None
+    dw.dw_release_workspace(ctx)           # the mixed solver's cached fields are not needed meanwhile
     if not args.no_plain:
         dfl64 = dw.deflation_build(ctx, wl["dfl_bs"], wl["Ns"], wl["n_inv"], wl["ncy"], wl["nmr"], start,
                                    basis_prec=dw.DW_F64, iter_prec=dw.DW_F64)
@@ -553,6 +555,7 @@ def main():
         plain = {"s_per_solve": a.elapsed_time(b) / 1e3 / n_plain, "iterations": inf64[0].iterations,
                  "relres": inf64[0].relres, "converged": rc == dw.DW_OK}
         del dfl64
+        dw.dw_release_workspace(ctx)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
     eta_pin = eta_h.pin_memory()
@@ -597,6 +600,7 @@ def main():
                                             if "batched" in res else None),
                  "autotune": tune}
         del eta12, psi12
+        dw.dw_release_workspace(ctx)
 
     # ---- subspace generation variants (Section 5.3): plain inverse iteration vs bootstrapped steps
     gen = None
@@ -648,9 +652,44 @@ def main():
             if dm:
                 del dm_, cm
 
+    # ---- network layer (learned subspace generation): the 16 -> 16 channel layer on the tensor cores
+    # (tcgen05, BF16 operands, FP32 accumulation) and on the CUDA cores (FP32), one set of 16 fields
+    ptl = None
+    if not args.no_ptnet:
+        import numpy as _np
+        wl1 = (_np.random.default_rng(5).normal(size=(9, 64, 64, 2)) * 0.05).astype(_np.float32)
+        wdev = torch.from_numpy(wl1.reshape(-1)).cuda()
+        hin = torch.randn(16 * V * 24, dtype=torch.float32, device="cuda")
+        hout = torch.empty_like(hin)
+        flops = 9 * 2 * 128 * 128 * 3 * V          # real-form GEMM: 885 kflop per site
+        bf16_peak = 1889.1
+        pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        if os.path.exists(pk):
+            with open(pk) as f:
+                bf16_peak = json.load(f).get("bf16_tflops", bf16_peak)
+        ptl = {"flops_per_layer": flops}
+        for name, tc in (("tensor_cores_bf16", 1), ("cuda_cores_fp32", 0)):
+            for _ in range(2):
+                dw.ptnet_layer16(ctx, wdev, 0, tc, hin, hout)
+            ts = []
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                dw.ptnet_layer16(ctx, wdev, 0, tc, hin, hout)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1) / 1e3)
+            t = statistics.median(ts)
+            ptl[name] = {"ms": t * 1e3, "tflops": flops / t / 1e12}
+        ptl["tensor_cores_bf16"]["frac_of_bf16_peak"] = ptl["tensor_cores_bf16"]["tflops"] / bf16_peak
+        ptl["bf16_peak_tflops"] = bf16_peak
+        ptl["speedup_tensor_cores"] = ptl["cuda_cores_fp32"]["ms"] / ptl["tensor_cores_bf16"]["ms"]
+        del hin, hout, wdev
+
     # ---- local coherence (Section 5.2): low modes of D^+ D by Chebyshev-accelerated subspace
     # iteration, a block subspace (4^4 blocks) from half of them, deficits (3.15) of the others
     coherence = None
+    dw.dw_release_workspace(ctx)
     if not args.no_coherence:
         nev, nbuf = 24, 8
         st = synth.start_fields(L, nev + nbuf, 4242).cuda()
@@ -709,7 +748,7 @@ def main():
                 "speedup_vs_plain_fp64": (plain["s_per_solve"] / value) if plain else None,
                 "dirac": dirac, "roofline": roof, "roofline_sap": roof_sap, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "batch12": batch, "subspace_generation": gen,
-                "table1": table1, "local_coherence": coherence}
+                "table1": table1, "local_coherence": coherence, "ptnet_layer16": ptl}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

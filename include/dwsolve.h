@@ -93,6 +93,10 @@ long long dw_launch_count(void);
 int dw_create(const dw_params* p, const double* links_host, dw_ctx** out);
 void dw_destroy(dw_ctx* ctx);
 
+/* Free the workspaces a context keeps between calls (solver Krylov fields, the double-float copies
+ * of links and clover term); later calls allocate them again.  Synchronises the device. */
+int dw_release_workspace(dw_ctx* ctx);
+
 /* Bytes of one packed field of precision prec (DW_F64 or DW_F32). */
 size_t dw_field_bytes(const dw_ctx* ctx, int prec);
 /* Number of lattice sites V. */
@@ -287,6 +291,15 @@ int ptnet_loss_grad(dw_ctx* ctx, int C, const void* weights, int nf, const void*
 /* One Adam step (beta1 0.9, beta2 0.999) on ncomplex complex weights; m, v: optimiser state. */
 int ptnet_adam(size_t ncomplex, void* weights, const void* grad, void* m, void* v, int step, double lr,
                void* stream);
+/* One 16 -> 16 channel layer of the network: out = sum_d W_d T_d in, or its adjoint
+ * sum_d W_d^+ T_d^+ in (adjoint = 1; the data gradient of back-propagation).  W: the layer's
+ * [9][64][64] complex FP32 weights; in/out: 16 packed FP32 channel fields each (one after the other).
+ * tensor_cores = 1: the 5th-generation tensor cores (tcgen05, BF16 operands, FP32 accumulation;
+ * relative error a few 1e-3), 0: FP32 on the CUDA cores.  Synchronous.  DW_ECUDA if a wait on the
+ * tensor core or a bulk copy timed out. */
+int ptnet_layer16(dw_ctx* ctx, const void* W, int adjoint, int tensor_cores, const void* in, void* out, void* stream);
+/* ptnet_forward with the 16 -> 16 layer on the tensor cores (BF16 operands, FP32 accumulation). */
+int ptnet_forward_tc(dw_ctx* ctx, int C, const void* weights, int nf, const void* x, void* y, void* stream);
 /* The plain subspace generation (5.1) on nf packed FP32 fields in place: nsteps times
  * psi <- M_sap psi, normalised.  Synchronous. */
 int dfl_inverse_iteration(dw_ctx* ctx, int ncy, int nmr, int nsteps, int nf, void* fields, void* stream);

@@ -92,6 +92,18 @@ class PTNet:
             out += np.moveaxis(o.reshape((cout, 4) + o.shape[1:]), 1, -2)
         return out
 
+    def layer_adjoint(self, w, g):
+        """The adjoint of `layer`: sum_d T_d^dag (w[d]^dag g), g[cout, L.., 4, 3] -> [cin, L.., 4, 3]
+        (the data gradient of back-propagation)."""
+        cout = g.shape[0]
+        cin = w.shape[2] // 4
+        out = np.zeros((cin,) + g.shape[1:], dtype=np.complex128)
+        gf = np.moveaxis(g, -2, 1).reshape((cout * 4,) + g.shape[1:-2] + (3,))
+        for d in range(9):
+            b = np.tensordot(w[d].conj().T, gf, axes=(1, 0))                            # [cin*4, L.., 3]
+            out += self.transport_adj(np.moveaxis(b.reshape((cin, 4) + b.shape[1:]), 1, -2), d)
+        return out
+
     def forward(self, W, x, keep=False):
         """x: [V, 4, 3] field -> N(x) [V, 4, 3]; keep=True also returns the layer inputs."""
         h = np.asarray(x, dtype=np.complex128).reshape((1,) + self.L + (4, 3))

@@ -81,6 +81,8 @@ struct dfl_ctx {
   float* ref32 = nullptr;                              //                  2 FP32 little vectors
   double* coop_partial = nullptr;                      // reduction accumulators of the cooperative solver
   double* coop_out = nullptr;                          // iterations, relative residual
+  int* coop_err = nullptr;                             // error flag of the ring variant
+  bool coop_ring = false;                              // FP32 cooperative solver with the shared-memory ring
   dd* ddf = nullptr;                                   // double-float field (restriction/prolongation)
   dd* ddl = nullptr;                                   // double-float little vector
   // work vectors (little GCR)
@@ -773,6 +775,7 @@ struct CoopArgs {
   T* work;            // (2 nkv + 5) vectors of Ne*Ns complex
   double* acc;        // [3][COOP_NV] reduction accumulators, zero at launch
   double* out;        // [0] iterations, [1] relative residual
+  int* err;           // set when a bounded wait of the shared-memory ring gave up
   double tol;
 };
 
@@ -987,18 +990,132 @@ DW_D void coop_hop(int nrow, int Ns, const int* list, const int* lnb, const T* M
   }
 }
 
+// The hops with the operator staged in shared memory: the 8 blocks of a block row (8 Ns^2 complex,
+// contiguous) arrive by one bulk copy into a ring of RING_SLOTS slots (full barrier: bytes landed;
+// empty barrier: the 8 warps are done with the slot).  Thread 0 keeps RING_SLOTS rows in flight and,
+// at the end of a hop, issues the first rows of the next hop (odd and even hops alternate), so the
+// copies overlap the grid barrier and the reductions between hops.  Counters are kept identically
+// by every thread; only thread 0 issues copies.
+constexpr int RING_SLOTS = 6;
+template <int NS>
+struct HopRing {
+  uint64_t* full;
+  uint64_t* empty;
+  unsigned char* slots;
+  uint32_t prod, cons;     // rows issued / consumed since the kernel started
+  int next_issued;         // rows of the coming hop already issued
+  int next_parity;         // 1: odd rows come next, 0: even rows
+  int* err;
+  __host__ __device__ static constexpr uint32_t bytes() { return (uint32_t)(8 * NS * NS * 2 * sizeof(float)); }
+  __host__ __device__ static constexpr uint32_t stride() { return (bytes() + 127u) & ~127u; }
+};
+
+DW_D void coop_row_range(int nrow, int* rb, int* re) {
+  const int R = (nrow + gridDim.x - 1) / gridDim.x;
+  *rb = min(nrow, (int)blockIdx.x * R);
+  *re = min(nrow, *rb + R);
+}
+
+// thread 0: copy block row L into the next slot (after the slot's previous row has been consumed)
+template <int NS>
+DW_D void ring_issue(HopRing<NS>& rg, const float* M, int L) {
+  const uint32_t p = rg.prod, sl = p % RING_SLOTS;
+  if (threadIdx.x == 0) {
+    if (p >= RING_SLOTS) mbar_wait(&rg.empty[sl], ((p / RING_SLOTS) - 1) & 1, rg.err);
+    mbar_expect_tx(&rg.full[sl], HopRing<NS>::bytes());
+    bulk_load(rg.slots + (size_t)sl * HopRing<NS>::stride(), M + (size_t)L * 8 * NS * NS * 2, HopRing<NS>::bytes(),
+              &rg.full[sl]);
+  }
+  ++rg.prod;
+}
+
+// issue the first rows of the hop over `list` (this CTA's rows) that are not yet in flight
+template <int NS>
+DW_D void ring_prefetch(HopRing<NS>& rg, const float* M, int nrow, const int* list) {
+  int rb, re;
+  coop_row_range(nrow, &rb, &re);
+  const int want = min(RING_SLOTS, re - rb);
+  for (int j = rg.next_issued; j < want; ++j) ring_issue<NS>(rg, M, list[rb + j]);
+  rg.next_issued = max(rg.next_issued, want);
+}
+
+// as coop_hop (FP32, Ns = NS), the blocks read from the ring; afterwards the first rows of the
+// hop over (nrow_next, list_next) are issued
+template <int NS>
+DW_D void coop_hop_ring(HopRing<NS>& rg, int nrow, const int* list, const int* lnb, const float* M,
+                        const cplx<float>* src, const cplx<float>* corr, cplx<float> cs, const cplx<float>* base,
+                        cplx<float>* out, float out_sign, cplx<float>* hp, int nrow_next, const int* list_next) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int rb, re;
+  coop_row_range(nrow, &rb, &re);
+  ring_prefetch<NS>(rg, M, nrow, list);            // normally done at the end of the previous hop
+  for (int r0 = rb; r0 < re; r0 += COOP_CH) {
+    const int nr = min(COOP_CH, re - r0);
+    for (int q = 0; q < nr; ++q) {
+      const uint32_t c = rg.cons, sl = c % RING_SLOTS;
+      const int j = __ldg(lnb + (size_t)(r0 + q) * 8 + w);
+      cplx<float> x = lane < NS ? src[(size_t)j * NS + lane] : cplx<float>{0.f, 0.f};
+      if (corr && lane < NS) x -= cs * corr[(size_t)j * NS + lane];
+      if (!mbar_wait(&rg.full[sl], (c / RING_SLOTS) & 1, rg.err)) break;
+      const cplx<float>* Mb = reinterpret_cast<const cplx<float>*>(rg.slots + (size_t)sl * HopRing<NS>::stride()) +
+                              (size_t)w * NS * NS;
+      cplx<float> acc = {0.f, 0.f};
+#pragma unroll
+      for (int col = 0; col < NS; ++col) {
+        const cplx<float> xc = {__shfl_sync(0xffffffffu, x.re, col), __shfl_sync(0xffffffffu, x.im, col)};
+        if (lane < NS) acc += Mb[col * NS + lane] * xc;
+      }
+      hp[(q * 8 + w) * 32 + lane] = acc;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&rg.empty[sl]);
+      ++rg.cons;
+      // keep RING_SLOTS rows in flight: refill with the row RING_SLOTS ahead
+      const int ahead = (r0 + q - rb) + RING_SLOTS;
+      if (ahead < re - rb) ring_issue<NS>(rg, M, __ldg(list + rb + ahead));
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nr * NS; t += COOP_THREADS) {
+      const int q = t / NS, k = t - q * NS;
+      cplx<float> sum = hp[(q * 8) * 32 + k];
+#pragma unroll
+      for (int d = 1; d < 8; ++d) sum += hp[(q * 8 + d) * 32 + k];
+      const size_t o = (size_t)(r0 + q) * NS + k;
+      const cplx<float> bse = base ? base[o] : cplx<float>{0.f, 0.f};
+      out[o] = bse + out_sign * sum;
+    }
+    __syncthreads();
+  }
+  rg.next_issued = 0;
+  ring_prefetch<NS>(rg, M, nrow_next, list_next);
+}
+
 // y = B^ x = x - M_eo (M_oe x); ends with a grid barrier.  The CTA barriers on both sides of
 // the grid barriers are redundant for correctness but halve the solver's run time on GB300
 // (measured: 3.8 ms -> 1.9 ms for 42 iterations at Nb = 2592, Ns = 20).
-template <typename T, int NS>
-DW_D void coop_bhat(cg::grid_group& grid, const CoopArgs<T>& a, const cplx<T>* x, cplx<T>* tmpo, cplx<T>* y,
-                    cplx<T>* hp) {
+// one hop through the register pipeline or the shared-memory ring (FP32, Ns = NS only)
+template <typename T, int NS, bool RING>
+DW_D void hop_any(HopRing<(NS > 0 ? NS : 1)>& rg, const CoopArgs<T>& a, bool odd, const cplx<T>* src,
+                  const cplx<T>* corr, cplx<T> cs, const cplx<T>* base, cplx<T>* out, T sign, cplx<T>* hp) {
+  const int n = odd ? a.No : a.Ne, nn = odd ? a.Ne : a.No;
+  const int* list = odd ? a.list_o : a.list_e;
+  const int* lnb = odd ? a.lnb_o : a.lnb_e;
+  if constexpr (RING && sizeof(T) == 4 && NS > 0) {
+    coop_hop_ring<NS>(rg, n, list, lnb, reinterpret_cast<const float*>(a.M), src, corr, cs, base, out, sign, hp, nn,
+                      odd ? a.list_e : a.list_o);
+  } else {
+    coop_hop<T, NS>(n, a.Ns, list, lnb, a.M, src, corr, cs, base, out, sign, hp);
+  }
+}
+
+template <typename T, int NS, bool RING>
+DW_D void coop_bhat(cg::grid_group& grid, HopRing<(NS > 0 ? NS : 1)>& rg, const CoopArgs<T>& a, const cplx<T>* x,
+                    cplx<T>* tmpo, cplx<T>* y, cplx<T>* hp) {
   const cplx<T> zero = {T(0), T(0)};
-  coop_hop<T, NS>(a.No, a.Ns, a.list_o, a.lnb_o, a.M, x, nullptr, zero, nullptr, tmpo, T(1), hp);   // tmpo = M_oe x
+  hop_any<T, NS, RING>(rg, a, true, x, nullptr, zero, nullptr, tmpo, T(1), hp);     // tmpo = M_oe x
   __syncthreads();
   grid.sync();
   __syncthreads();
-  coop_hop<T, NS>(a.Ne, a.Ns, a.list_e, a.lnb_e, a.M, tmpo, nullptr, zero, x, y, T(-1), hp);      // y = x - M_eo tmpo
+  hop_any<T, NS, RING>(rg, a, false, tmpo, nullptr, zero, x, y, T(-1), hp);         // y = x - M_eo tmpo
   __syncthreads();
   grid.sync();
   __syncthreads();
@@ -1048,13 +1165,36 @@ DW_D void coop_PL(cg::grid_group& grid, CoopShared<T>& sh, const CoopArgs<T>& a,
   }
 }
 
-template <typename T, int NS>
+// dynamic shared memory of the ring variant: hop partial sums, the slots, their barriers
+template <int NS>
+inline size_t coop_ring_smem() {
+  return (size_t)COOP_CH * 8 * 64 * sizeof(float) + (size_t)RING_SLOTS * HopRing<NS>::stride() +
+         2 * RING_SLOTS * sizeof(uint64_t);
+}
+
+template <typename T, int NS, bool RING = false>
 __global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_kernel(CoopArgs<T> a) {
   constexpr int NSM = NS ? NS : 32;
+  constexpr int NSR = NS > 0 ? NS : 1;
   cg::grid_group grid = cg::this_grid();
   __shared__ CoopShared<T> sh;
-  extern __shared__ __align__(16) unsigned char coop_dyn[];
+  extern __shared__ __align__(128) unsigned char coop_dyn[];
   cplx<T>* hp = reinterpret_cast<cplx<T>*>(coop_dyn);                // [COOP_CH][8][32]
+  HopRing<NSR> rg{};
+  if constexpr (RING) {
+    unsigned char* base = coop_dyn + (size_t)COOP_CH * 8 * 64 * sizeof(float);
+    rg.slots = base;
+    rg.full = reinterpret_cast<uint64_t*>(base + (size_t)RING_SLOTS * HopRing<NSR>::stride());
+    rg.empty = rg.full + RING_SLOTS;
+    rg.err = a.err;
+    if (threadIdx.x == 0) {
+      for (int q = 0; q < RING_SLOTS; ++q) {
+        mbar_init(&rg.full[q], 1);
+        mbar_init(&rg.empty[q], COOP_WARPS);
+      }
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
   const int ns = NS ? NS : a.Ns;
   const size_t n = (size_t)a.Ne * ns;
   const CoopSlice sl = coop_rows_slice(a.Ne, ns);
@@ -1114,12 +1254,12 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_kernel(CoopAr
       // this CTA's own rows, so no grid barrier follows it
       slice([&](size_t i) { xk[i] = rk[i]; });
       const cplx<T> acs = k > 0 ? cplx<T>{sh.ac[0], sh.ac[1]} : zero;
-      coop_hop<T, NS>(a.No, ns, a.list_o, a.lnb_o, a.M, k > 0 ? rhob[cur ^ 1] : rk, k > 0 ? chi(k - 1) : nullptr,
-                      acs, nullptr, tmpo, T(1), hp);
+      hop_any<T, NS, RING>(rg, a, true, k > 0 ? rhob[cur ^ 1] : rk, k > 0 ? chi(k - 1) : nullptr, acs, nullptr, tmpo,
+                           T(1), hp);
       __syncthreads();
       grid.sync();
       __syncthreads();
-      coop_hop<T, NS>(a.Ne, ns, a.list_e, a.lnb_e, a.M, tmpo, nullptr, zero, rk, ck, T(-1), hp);
+      hop_any<T, NS, RING>(rg, a, false, tmpo, nullptr, zero, rk, ck, T(-1), hp);
       // one reduction: u = g^+ chi_k (A.3), the raw coefficients (chi'_j, chi_k), j < k, and |rho_k|^2
       if (a.a3) cta_dots<T>(sh, g, n, ns, ck, sl, 0);
       if (k > 0) cta_dots<T>(sh, W, n, k, ck, sl, na);
@@ -1234,7 +1374,7 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_kernel(CoopAr
     grid.sync();
     if (k == 0) break;
     // true residual of the deflated system
-    coop_bhat<T, NS>(grid, a, v, tmpo, t, hp);
+    coop_bhat<T, NS, RING>(grid, rg, a, v, tmpo, t, hp);
     if (a.a3) coop_PL<T, NS>(grid, sh, a, t, g, Bg, nullptr, sl);
     s1[0] = 0;
     cplx<T>* r0 = rhob[cur];
@@ -1251,13 +1391,19 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_kernel(CoopAr
   if (a.a3) {
     // v = chi + g A~^{-1} g^+ (b - B^ chi)
     grid.sync();
-    coop_bhat<T, NS>(grid, a, v, tmpo, t, hp);
+    coop_bhat<T, NS, RING>(grid, rg, a, v, tmpo, t, hp);
     slice([&](size_t i) { t[i] = b[i] - t[i]; });
     coop_PL<T, NS>(grid, sh, a, t, g, g, v, sl);     // v += g z,  z = A~^{-1} g^+ t
+  }
+  if constexpr (RING) {
+    // rows issued ahead for a hop that does not come: wait for their copies before exiting
+    for (uint32_t q = rg.cons; q < rg.prod; ++q) mbar_wait(&rg.full[q % RING_SLOTS], (q / RING_SLOTS) & 1, rg.err);
+    __syncthreads();
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.out[0] = total;
     a.out[1] = bn > 0 ? (double)rn / (double)bn : 0.0;
+    if (RING && *(volatile int*)a.err) a.out[1] = __longlong_as_double(0x7ff8000000000000LL);   // NaN: failed
   }
 }
 
@@ -1792,7 +1938,7 @@ extern "C" void dfl_destroy(dfl_ctx* d) {
   void* ptrs[] = {d->d_sub, d->d_sap2dfl, d->d_bnb, d->d_list[0], d->d_list[1], d->d_lnb[0], d->d_lnb[1],
                   d->basis64, d->basis16, d->B64, d->Binv64, d->Binv32, d->M64, d->M32, d->g64, d->g32,
                   d->Bg64, d->Bg32, d->lw[0], d->lw[1], d->B32, d->fw[0], d->fw[1], d->Ainv64, d->Ainv32,
-                  d->coop_partial, d->coop_out, d->ref64, d->ref32, d->ddf, d->ddl, d->mw, d->mio,
+                  d->coop_partial, d->coop_out, d->coop_err, d->ref64, d->ref32, d->ddf, d->ddl, d->mw, d->mio,
                   d->meo, d->mpart, d->mred, d->mtol, d->mout};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -2110,6 +2256,7 @@ static int little_gcr_coop(dfl_ctx* d, const T* b, T* v, double tol, int maxit, 
   a.Ainv = d->a3 ? Ainvp<T>(d) : nullptr; a.b = b; a.v = v;
   a.work = lwork<T>(d, 0);
   a.acc = d->coop_partial;                                   // [3][COOP_NV] accumulators
+  a.err = d->coop_err;
   DW_CUDA(cudaMemsetAsync(d->coop_partial, 0, 3 * COOP_NV * sizeof(double), s));
   a.out = d->coop_out + (d->defer_slot >= 0 ? 2 * d->defer_slot : 0);
   a.tol = tol;
@@ -2120,8 +2267,17 @@ static int little_gcr_coop(dfl_ctx* d, const T* b, T* v, double tol, int maxit, 
     NS_DISPATCH_FEW(d->Ns, (le = cudaLaunchCooperativeKernel((void*)little_gcr_coop_kernel<T, NSV>, d->coop_grid,
                                                        COOP_THREADS, args, dsm, s)));
   } else {
-    NS_DISPATCH(d->Ns, (le = cudaLaunchCooperativeKernel((void*)little_gcr_coop_kernel<T, NSV>, d->coop_grid,
-                                                       COOP_THREADS, args, dsm, s)));
+    bool done = false;
+    if (d->coop_ring) {
+      NS_DISPATCH_FEW(d->Ns, if constexpr (NSV > 0) {
+        le = cudaLaunchCooperativeKernel((void*)little_gcr_coop_kernel<float, NSV, true>, d->coop_grid, COOP_THREADS,
+                                         args, coop_ring_smem<NSV>(), s);
+        done = true;
+      });
+    }
+    if (!done)
+      NS_DISPATCH(d->Ns, (le = cudaLaunchCooperativeKernel((void*)little_gcr_coop_kernel<T, NSV>, d->coop_grid,
+                                                         COOP_THREADS, args, dsm, s)));
   }
   DW_CUDA(le);
   dw_note_launch();
@@ -2734,6 +2890,20 @@ static int little_setup(dw_ctx* c, dfl_ctx* d, const double* B64_given) {
     if (d->coop_grid) {
       DW_CUDA(cudaMalloc(&d->coop_partial, (size_t)2 * coop_gpad(d->coop_grid) * COOP_NV * sizeof(double)));
       DW_CUDA(cudaMalloc(&d->coop_out, 2 * 64 * sizeof(double)));
+      DW_CUDA(cudaMalloc(&d->coop_err, sizeof(int)));
+      DW_CUDA(cudaMemset(d->coop_err, 0, sizeof(int)));
+      // FP32 solver variant with the operator staged through a shared-memory ring (Ns = 8, 20);
+      // DW_COOP_RING=0 keeps the register-pipelined hops
+      int br = 0;
+      NS_DISPATCH_FEW(Ns, if constexpr (NSV > 0) {
+        if (cudaFuncSetAttribute(little_gcr_coop_kernel<float, NSV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)coop_ring_smem<NSV>()) == cudaSuccess)
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&br, little_gcr_coop_kernel<float, NSV, true>, COOP_THREADS,
+                                                        coop_ring_smem<NSV>());
+      });
+      cudaGetLastError();
+      const char* re = getenv("DW_COOP_RING");
+      d->coop_ring = br > 0 && !(re && re[0] == '0');
       // multi-RHS solver (batches of right-hand sides): Ns with a compiled kernel, all CTAs resident
       int bm = 0;
       const size_t dsmm = coop_m_dyn_bytes(Ns);

@@ -135,7 +135,7 @@ extern "C" int lowmodes_solve(dw_ctx* c, int nev, int nbuf, int degree, double t
   cudaStream_t s = (cudaStream_t)stream;
   const int n = nev + nbuf;
   const size_t V = c->V, fs = V * 24, nc = V * 12;
-  const size_t fb64 = fs * sizeof(double), fbp = fs * real_size(prec);
+  const size_t fb64 = fs * sizeof(double), fbp = fs * sizeof(double);   // filter blocks sized for FP64
   WsArena& ar = c->ws_solve[3];
   ar.rewind();
   double *Yb, *Wb, *Xb, *tmp, *dres;
@@ -173,6 +173,8 @@ extern "C" int lowmodes_solve(dw_ctx* c, int nev, int nbuf, int degree, double t
   std::vector<cd> H((size_t)n * n), Vm;
   double a_cut = 0;
   int it = 0, nconv = 0;
+  int fprec = prec;                 // filter precision: an FP32 filter hands over to FP64 when it stalls
+  double last = INFINITY;
   for (; it <= maxit; ++it) {
     if (it > 0) {
       // Chebyshev filter of the block: y_{k+1} = 2 L(A) y_k - y_{k-1}, y_1 = L(A) y_0
@@ -195,7 +197,7 @@ extern "C" int lowmodes_solve(dw_ctx* c, int nev, int nbuf, int degree, double t
         }
         for (int j = 0; j < n; ++j) field_convert<T, double>(yc + (size_t)j * fs, Y[j], 1.0, V, s);
       };
-      if (prec == DW_F32) filter((float*)f0, (float*)f1, (float*)ft);
+      if (fprec == DW_F32) filter((float*)f0, (float*)f1, (float*)ft);
       else filter((double*)f0, (double*)f1, (double*)ft);
     }
     if ((rc = orthonormalise(c, Y, dres, s))) return rc;
@@ -236,6 +238,11 @@ extern "C" int lowmodes_solve(dw_ctx* c, int nev, int nbuf, int degree, double t
     while (nconv < nev && res[nconv] <= tol * std::max(theta[nconv], 1e-300)) ++nconv;
     a_cut = theta[n - 1];
     if (nconv == nev) break;
+    // the rounding of an FP32 filter limits the residuals to about 1e-7 lambda_max: once the first
+    // unconverged residual no longer halves per iteration, the filter continues in FP64
+    const double cur = res[nconv] / std::max(theta[nconv], 1e-300);
+    if (fprec == DW_F32 && it >= 2 && cur > 0.5 * last) fprec = DW_F64;
+    last = cur;
   }
   if ((rc = dw_unpack(c, DW_F64, nev, Yb, modes, s))) return rc;
   DW_CUDA(cudaStreamSynchronize(s));

@@ -11,6 +11,7 @@
 //
 // Weights: per layer 9 x (4 C_out) x (4 C_in) complex (FP32), layers stored back to back.
 // Channel fields are packed FP32 fields stored one after the other.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -210,6 +211,260 @@ void launch_layer(dw_ctx* c, const float2* W, const float* in, float* out, cudaS
                                                                     out); dw_note_launch();
 }
 
+// ------------------------------------------------------------------ tensor-core 16 -> 16 layer
+// The 16-channel layer is a dense complex contraction per site and colour: out = sum_d W_d (T_d h)
+// with W_d a 64 x 64 complex matrix on (channel, spin).  In real form it is one GEMM per CTA tile:
+//   D[128 x 192] += A_d[128 x 128] B_d[128 x 192],  d = 0..8
+// A_d = [[Re W_d, -Im W_d], [Im W_d, Re W_d]] (rows: output (channel, spin) x (re, im)), B_d the
+// transported input of 64 sites x 3 colours (columns) by (channel, spin) x (re, im) (rows), BF16
+// operands in shared memory, the FP32 accumulator in tensor memory (tcgen05.mma, kind::f16, one
+// elected thread issues).  A_d is staged by a bulk copy from a pre-arranged image; B_d is built by
+// all threads (parallel transport on the CUDA cores, rounded to BF16).  Two stages: the
+// transports of direction d + 1 overlap the MMAs of direction d.  Operands are K-major without
+// swizzle: 8 x 16-byte core matrices, K-adjacent ones 128 bytes apart (leading byte offset),
+// 8-row groups 2048 bytes apart (stride byte offset).
+constexpr int TC_S = 64;                       // sites per tile
+constexpr int TC_M = 128, TC_K = 128, TC_N = 3 * TC_S;
+constexpr int TC_THREADS = 256;
+constexpr uint32_t TC_TMEM_COLS = 256;
+constexpr int TC_A_BYTES = TC_M * TC_K * 2;    // 32 KB
+constexpr int TC_B_BYTES = TC_N * TC_K * 2;    // 48 KB
+constexpr int TC_STAGE_LD = TC_N + 1;          // FP32 staging row stride of the epilogue (bank-conflict free)
+constexpr size_t TC_SMEM = 2 * TC_A_BYTES + 2 * TC_B_BYTES + 1024;
+
+// byte offset of element (row, k) in a K-major no-swizzle operand with K = 128
+DW_HD uint32_t tc_off(int row, int k) {
+  return (uint32_t)((row >> 3) * 2048 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+DW_D uint64_t tc_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)(128 >> 4) << 16;             // leading byte offset: next core matrix along K
+  d |= (uint64_t)(2048 >> 4) << 32;            // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                      // descriptor version of tcgen05; no swizzle
+  return d;
+}
+// instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, N = 192, M = 128
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+                              ((uint32_t)(TC_M >> 4) << 24);
+
+DW_D void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(accum) : "memory");
+}
+DW_D void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+DW_D void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+DW_D void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+DW_D void tc_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// A_d images of one 16 -> 16 layer (ADJ: of W_d^+), BF16 in the core-matrix layout
+template <bool ADJ>
+__global__ void ptnet_tc_pack_kernel(const float2* __restrict__ W, __nv_bfloat16* A) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 9 * TC_M * TC_K) return;
+  const int d = t / (TC_M * TC_K), e = t % (TC_M * TC_K), r = e / TC_K, k = e % TC_K;
+  const int ro = r & 63, ko = k & 63;
+  const float2* Wd = W + (size_t)d * 64 * 64;
+  float2 w = ADJ ? Wd[ko * 64 + ro] : Wd[ro * 64 + ko];
+  if (ADJ) w.y = -w.y;
+  const float val = r < 64 ? (k < 64 ? w.x : -w.y) : (k < 64 ? w.y : w.x);
+  A[(size_t)d * TC_M * TC_K + tc_off(r, k) / 2] = __float2bfloat16_rn(val);
+}
+
+template <bool ADJ>
+__global__ void __launch_bounds__(TC_THREADS, 1) ptnet_tc_layer_kernel(Geom g, const float* __restrict__ links,
+                                                                       const __nv_bfloat16* __restrict__ Apack,
+                                                                       const float* __restrict__ in,
+                                                                       float* __restrict__ out, int* err) {
+  extern __shared__ uint8_t tc_raw[];
+  __shared__ uint64_t bar_tma[2], bar_mma[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int fail;
+  const uint32_t raw = smem_u32(tc_raw);
+  uint8_t* sb = tc_raw + (((raw + 1023u) & ~1023u) - raw);       // 1024-byte aligned operand area
+  uint8_t* abuf[2] = {sb, sb + TC_A_BYTES};
+  uint8_t* bbuf[2] = {sb + 2 * TC_A_BYTES, sb + 2 * TC_A_BYTES + TC_B_BYTES};
+  float* stage = reinterpret_cast<float*>(sb);                   // epilogue: [128][TC_STAGE_LD] FP32
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    mbar_init(&bar_tma[0], 1);
+    mbar_init(&bar_tma[1], 1);
+    mbar_init(&bar_mma[0], 1);
+    mbar_init(&bar_mma[1], 1);
+    fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(TC_TMEM_COLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const size_t V = g.V, fs = V * 24;
+  const long long ntiles = ((long long)V + TC_S - 1) / TC_S;
+  uint32_t use[2] = {0, 0};
+  int gc = 0;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long i0 = tile * TC_S;
+    for (int d = 0; d < 9; ++d) {
+      const int b = gc & 1;
+      // the MMAs that last read stage b must be complete before it is refilled
+      if (use[b] > 0 && !mbar_wait(&bar_mma[b], (use[b] - 1) & 1, err)) fail = 1;
+      __syncthreads();
+      if (fail) break;
+      if (tid == 0) {
+        mbar_expect_tx(&bar_tma[b], TC_A_BYTES);
+        bulk_load(abuf[b], Apack + (size_t)d * TC_M * TC_K, TC_A_BYTES, &bar_tma[b]);
+      }
+      // B_d: item (site q, input channel c) -> rows (4c .. 4c+3) re and (64 + 4c ..) im, columns 3q + colour
+      const int dt = (ADJ && d > 0) ? (((d - 1) ^ 1) + 1) : d;
+      for (int it = tid; it < TC_S * 16; it += TC_THREADS) {
+        const int q = it & (TC_S - 1), c = it / TC_S;
+        const long long i = i0 + q;
+        cplx<float> th[4][3];
+        if (i < (long long)V) {
+          const SiteRef s = decode(g, i);
+          pt_transport(g, links, in + (size_t)c * fs, s, i, dt, th);
+        } else {
+#pragma unroll
+          for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) th[sp][a] = {0.f, 0.f};
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const int n = 3 * q + a;
+          __nv_bfloat162 re01 = __floats2bfloat162_rn(th[0][a].re, th[1][a].re);
+          __nv_bfloat162 re23 = __floats2bfloat162_rn(th[2][a].re, th[3][a].re);
+          __nv_bfloat162 im01 = __floats2bfloat162_rn(th[0][a].im, th[1][a].im);
+          __nv_bfloat162 im23 = __floats2bfloat162_rn(th[2][a].im, th[3][a].im);
+          uint2 vr, vi;
+          vr.x = *reinterpret_cast<uint32_t*>(&re01);
+          vr.y = *reinterpret_cast<uint32_t*>(&re23);
+          vi.x = *reinterpret_cast<uint32_t*>(&im01);
+          vi.y = *reinterpret_cast<uint32_t*>(&im23);
+          *reinterpret_cast<uint2*>(bbuf[b] + tc_off(n, 4 * c)) = vr;
+          *reinterpret_cast<uint2*>(bbuf[b] + tc_off(n, 64 + 4 * c)) = vi;
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");    // generic-proxy writes -> tensor core
+      tc_fence_before();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        if (mbar_wait(&bar_tma[b], use[b] & 1, err)) {
+          const uint32_t a0 = smem_u32(abuf[b]), b0 = smem_u32(bbuf[b]);
+#pragma unroll
+          for (int kk = 0; kk < TC_K / 16; ++kk)
+            tc_mma(tmem, tc_desc(a0 + kk * 256), tc_desc(b0 + kk * 256), (d > 0 || kk > 0) ? 1u : 0u);
+          tc_commit(&bar_mma[b]);
+        } else {
+          fail = 1;
+        }
+      }
+      ++use[b];
+      ++gc;
+    }
+    __syncthreads();
+    if (fail) break;
+    // epilogue: all MMAs of the tile complete -> TMEM rows to shared memory -> output fields
+    const int bl = (gc - 1) & 1;
+    if (!mbar_wait(&bar_mma[bl], (use[bl] - 1) & 1, err)) fail = 1;
+    __syncthreads();
+    if (fail) break;
+    tc_fence_after();
+    {
+      const int row = 32 * (warp & 3) + lane, half = warp >> 2;
+#pragma unroll
+      for (int j = 0; j < TC_N / 2 / 16; ++j) {
+        const int col = half * (TC_N / 2) + 16 * j;
+        float v[16];
+        tc_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)col, v);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) stage[row * TC_STAGE_LD + col + e] = v[e];
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    for (int it = tid; it < TC_S * 16; it += TC_THREADS) {
+      const int q = it & (TC_S - 1), c = it / TC_S;
+      const long long i = i0 + q;
+      if (i >= (long long)V) continue;
+      cplx<float> o[12];
+#pragma unroll
+      for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const int m = 4 * c + sp, n = 3 * q + a;
+          o[3 * sp + a] = {stage[m * TC_STAGE_LD + n], stage[(m + 64) * TC_STAGE_LD + n]};
+        }
+      store_site<float, 12>(out + (size_t)c * fs, V, i, o);
+    }
+    __syncthreads();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+}
+
+// one 16 -> 16 layer (adjoint: W_d^+ and reversed transports) on the tensor cores
+int tc_layer16(dw_ctx* c, const float2* W, int adjoint, const float* in, float* out, cudaStream_t st) {
+  static bool attr_set[2] = {false, false};
+  __nv_bfloat16* A = nullptr;
+  int* err = nullptr;
+  DW_CUDA(cudaMallocAsync((void**)&A, (size_t)9 * TC_A_BYTES, st));
+  DW_CUDA(cudaMallocAsync((void**)&err, sizeof(int), st));
+  DW_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  const int n = 9 * TC_M * TC_K;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long ntiles = (c->V + TC_S - 1) / TC_S;
+  const unsigned grid = (unsigned)std::min<long long>(ntiles, sms);
+  if (adjoint) {
+    if (!attr_set[1]) {
+      DW_CUDA(cudaFuncSetAttribute(ptnet_tc_layer_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+      attr_set[1] = true;
+    }
+    ptnet_tc_pack_kernel<true><<<(n + 255) / 256, 256, 0, st>>>(W, A); dw_note_launch();
+    ptnet_tc_layer_kernel<true><<<grid, TC_THREADS, TC_SMEM, st>>>(c->g, (const float*)c->links[DW_F32], A, in, out, err);
+  } else {
+    if (!attr_set[0]) {
+      DW_CUDA(cudaFuncSetAttribute(ptnet_tc_layer_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+      attr_set[0] = true;
+    }
+    ptnet_tc_pack_kernel<false><<<(n + 255) / 256, 256, 0, st>>>(W, A); dw_note_launch();
+    ptnet_tc_layer_kernel<false><<<grid, TC_THREADS, TC_SMEM, st>>>(c->g, (const float*)c->links[DW_F32], A, in, out, err);
+  }
+  dw_note_launch();
+  DW_CUDA(cudaGetLastError());
+  int herr = 0;
+  DW_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DW_CUDA(cudaStreamSynchronize(st));
+  cudaFreeAsync(A, st);
+  cudaFreeAsync(err, st);
+  if (herr) { dw_set_error("ptnet tensor-core layer: a wait on the tensor core or bulk copy timed out"); return DW_ECUDA; }
+  return DW_OK;
+}
+
 }  // namespace
 
 extern "C" size_t ptnet_weight_count(int C) {
@@ -256,6 +511,48 @@ extern "C" int ptnet_forward(dw_ctx* c, int C, const void* W, int nf, const void
                             (cudaStream_t)stream);
   cudaStreamSynchronize((cudaStream_t)stream);
   cudaFree(acts);
+  return rc;
+}
+
+// One 16 -> 16 layer on a set of 16 channel fields: out = sum_d W_d T_d in (adjoint:
+// sum_d W_d^+ T_d^+ in), on the tensor cores (BF16 operands, FP32 accumulation) or the CUDA cores (FP32).
+extern "C" int ptnet_layer16(dw_ctx* c, const void* W, int adjoint, int tensor_cores, const void* in, void* out,
+                             void* stream) {
+  if (!c || !W || !in || !out || in == out) { dw_set_error("ptnet_layer16: bad argument"); return DW_EINVAL; }
+  if (int rc = dw_check_device(c, "ptnet_layer16")) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (tensor_cores) return tc_layer16(c, (const float2*)W, adjoint, (const float*)in, (float*)out, st);
+  if (adjoint) launch_layer<16, 16, true>(c, (const float2*)W, (const float*)in, (float*)out, st);
+  else launch_layer<16, 16, false>(c, (const float2*)W, (const float*)in, (float*)out, st);
+  DW_CUDA(cudaGetLastError());
+  DW_CUDA(cudaStreamSynchronize(st));
+  return DW_OK;
+}
+
+// The network with its 16 -> 16 layer on the tensor cores (the 1 -> 16 and 16 -> 1 layers, 16x fewer
+// flops, on the CUDA cores).
+extern "C" int ptnet_forward_tc(dw_ctx* c, int C, const void* Wv, int nf, const void* x, void* y, void* stream) {
+  if (!c || !Wv || !x || !y || x == y || nf < 1 || !ptnet_ok(C)) {
+    dw_set_error("ptnet_forward_tc: bad argument (C must be 16)");
+    return DW_EINVAL;
+  }
+  if (int rc = dw_check_device(c, "ptnet_forward_tc")) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const float2* W = (const float2*)Wv;
+  const size_t fs = (size_t)c->V * 24, w1 = 9 * 16 * C, w2 = 9 * 16 * C * C;
+  float* acts = nullptr;
+  DW_CUDA(cudaMalloc(&acts, 2 * C * fs * sizeof(float)));
+  float* h1 = acts;
+  float* h2 = acts + (size_t)C * fs;
+  int rc = DW_OK;
+  for (int f = 0; f < nf && rc == DW_OK; ++f) {
+    launch_layer<1, 16, false>(c, W, (const float*)x + f * fs, h1, st);
+    rc = tc_layer16(c, W + w1, 0, h1, h2, st);
+    if (rc == DW_OK) launch_layer<16, 1, false>(c, W + w1 + w2, h2, (float*)y + f * fs, st);
+  }
+  cudaStreamSynchronize(st);
+  cudaFree(acts);
+  if (rc == DW_OK) DW_CUDA(cudaGetLastError());
   return rc;
 }
 

@@ -281,6 +281,17 @@ static void free_ctx(dw_ctx* c) {
 
 extern "C" void dw_destroy(dw_ctx* c) { free_ctx(c); }
 
+extern "C" int dw_release_workspace(dw_ctx* c) {
+  if (!c) { dw_set_error("dw_release_workspace: null context"); return DW_EINVAL; }
+  if (int rc = dw_check_device(c, "dw_release_workspace")) return rc;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return dw_cuda_fail(e, "dw_release_workspace");
+  for (auto& a : c->ws_solve) a.release();
+  if (c->links_dd) { cudaFree(c->links_dd); c->links_dd = nullptr; }
+  if (c->clov_dd) { cudaFree(c->clov_dd); c->clov_dd = nullptr; }
+  return DW_OK;
+}
+
 extern "C" size_t dw_field_bytes(const dw_ctx* c, int prec) {
   return c ? (size_t)c->V * 24 * real_size(prec) : 0;
 }

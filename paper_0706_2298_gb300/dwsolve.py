@@ -70,6 +70,7 @@ _SIGNATURES = {
     "dw_launch_count": (C.c_longlong, []),
     "dw_create": (C.c_int, [C.POINTER(DwParams), _P, C.POINTER(_P)]),
     "dw_destroy": (None, [_P]),
+    "dw_release_workspace": (C.c_int, [_P]),
     "dw_field_bytes": (C.c_size_t, [_P, C.c_int]),
     "dw_volume": (C.c_longlong, [_P]),
     "dw_pack": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
@@ -101,6 +102,8 @@ _SIGNATURES = {
     "ptnet_weight_count": (C.c_size_t, [C.c_int]),
     "ptnet_forward": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, _P, _P]),
     "ptnet_loss_grad": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, _P, _P, C.POINTER(C.c_double), _P]),
+    "ptnet_layer16": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, _P]),
+    "ptnet_forward_tc": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, _P, _P]),
     "ptnet_adam": (C.c_int, [C.c_size_t, _P, _P, _P, _P, C.c_int, C.c_double, _P]),
     "dfl_inverse_iteration": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P]),
 }
@@ -214,6 +217,10 @@ def dw_create(L, m0, csw, links_host: torch.Tensor, sap_bs=(4, 4, 4, 4), antiper
     h = C.c_void_p()
     _check(lib().dw_create(C.byref(p), _ptr(links), C.byref(h)))
     return Ctx(h, L, p)
+
+
+def dw_release_workspace(ctx: Ctx):
+    _check(lib().dw_release_workspace(ctx.handle))
 
 
 def dw_pack(ctx: Ctx, prec, nrhs, canon_dev, packed_dev, stream=None):
@@ -370,6 +377,15 @@ def ptnet_weight_count(channels=16) -> int:
 def ptnet_forward(ctx: Ctx, weights, nf, x, y, channels=16, stream=None):
     _check(lib().ptnet_forward(ctx.handle, int(channels), _ptr(weights), int(nf), _ptr(x), _ptr(y),
                                _stream(stream)))
+
+
+def ptnet_layer16(ctx: Ctx, W, adjoint, tensor_cores, x, y, stream=None):
+    _check(lib().ptnet_layer16(ctx.handle, _ptr(W), int(adjoint), int(tensor_cores), _ptr(x), _ptr(y), _stream(stream)))
+
+
+def ptnet_forward_tc(ctx: Ctx, weights, nf, x, y, channels=16, stream=None):
+    _check(lib().ptnet_forward_tc(ctx.handle, int(channels), _ptr(weights), int(nf), _ptr(x), _ptr(y),
+                                  _stream(stream)))
 
 
 def ptnet_loss_grad(ctx: Ctx, weights, nf, x, y, grad, channels=16, stream=None) -> float:

@@ -168,6 +168,26 @@ def test_inverse_iteration_fp64(case):
     assert rel(_export(case, d), basis_fields(sub)) <= 1e-11
 
 
+def test_little_solve_ring_matches_register_hops(case, monkeypatch):
+    """The FP32 cooperative solver with the operator staged through the shared-memory ring (the
+    default where it fits) and with register-pipelined hops solve the same system alike."""
+    L, sb, db, Ns, ctx, D, start = case
+    d_ring = _build(case, dw.DW_BF16)
+    monkeypatch.setenv("DW_COOP_RING", "0")
+    d_reg = _build(case, dw.DW_BF16)
+    monkeypatch.delenv("DW_COOP_RING")
+    wv = synth.complex_gaussian((d_ring.Nb * d_ring.Ns,), 24).numpy()
+    res = []
+    for d in (d_ring, d_reg):
+        wt = torch.from_numpy(wv.view(np.float64).copy()).to(torch.float32).cuda()
+        vt = torch.empty_like(wt)
+        rc, it, rr = dw.little_dirac_solve(d, dw.DW_F32, wt, vt, 1e-5, 2000)
+        assert rc == dw.DW_OK and rr <= 1e-5
+        res.append((vt.double().cpu().numpy().view(np.complex128), it))
+    assert rel(res[0][0], res[1][0]) <= 1e-4
+    assert abs(res[0][1] - res[1][1]) <= 2
+
+
 def test_global_mode_deflation_helps(case):
     """A.3 lowers the little GCR count: compare with the same system after A.2 fallback."""
     L, sb, db, Ns, ctx, D, start = case

@@ -25,8 +25,9 @@ def setup():
     return ctx, D, w, v
 
 
-@pytest.mark.parametrize("prec,tol,etol,vtol", [(dw.DW_F64, 1e-10, 1e-9, 1e-8), (dw.DW_F32, 1e-5, 1e-8, 1e-6)])
+@pytest.mark.parametrize("prec,tol,etol,vtol", [(dw.DW_F64, 1e-10, 1e-9, 1e-8), (dw.DW_F32, 1e-9, 1e-9, 1e-7)])
 def test_lowmodes_match_dense_eigendecomposition(setup, prec, tol, etol, vtol):
+    """FP64 filter; FP32 filter, which hands over to FP64 when its rounding stalls the residuals."""
     ctx, D, w, v = setup
     nev, nbuf = 6, 6
     assert np.min(np.diff(w[:nev + 1])) > 1e-6 * w[nev]      # non-degenerate: vectors are unique up to a phase

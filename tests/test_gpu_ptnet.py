@@ -133,3 +133,38 @@ def test_trained_network_gains_over_equal_cost_plain():
     assert res["learned"]["deficit"] < 0.95 * res["plain_k0"]["deficit"]
     assert res["plain_n_inv"]["deficit"] < res["plain_k0"]["deficit"]
     assert all(r["converged"] and r["relres"] <= 1e-10 for r in res.values())
+
+
+@pytest.mark.parametrize("adjoint", [0, 1])
+def test_layer16_tensor_cores(setup, adjoint):
+    """The 16 -> 16 layer (and its adjoint) on the tcgen05 tensor cores with BF16 operands and FP32
+    accumulation against the FP64 oracle (BF16 path: within 2e-2; the rounding of 576-term sums of
+    BF16 products gives a few 1e-3), and the FP32 CUDA-core path within 2e-5."""
+    ctx, P = setup
+    w = init_weights(16, seed=7, scale=0.6)[1]
+    h = synth.complex_gaussian((16, ctx.V, 4, 3), 71).numpy()
+    hg = h.reshape((16,) + L + (4, 3))
+    ref = (P.layer_adjoint(w, hg) if adjoint else P.layer(w, hg)).reshape(16, ctx.V, 4, 3)
+    wd = torch.from_numpy(w.astype(np.complex64).view(np.float32).copy()).cuda()
+    x = to_packed(ctx, dw.DW_F32, h)
+    for tc, tol in ((1, 2e-2), (0, 2e-5)):
+        y = ctx.empty_field(dw.DW_F32, 16)
+        y.fill_(float("nan"))
+        dw.ptnet_layer16(ctx, wd, adjoint, tc, x, y)
+        got = from_packed(ctx, dw.DW_F32, y, 16)
+        assert np.isfinite(got).all()
+        err = rel(got, ref)
+        assert err <= tol, (tc, err)
+        if tc:
+            assert err >= 1e-6          # BF16 operands really were used
+
+
+def test_forward_tensor_cores(setup):
+    """The whole network with its 16 -> 16 layer on the tensor cores against the oracle."""
+    ctx, P = setup
+    W = init_weights(16, seed=1, scale=0.5)
+    x = synth.gaussian_source(L, 3).numpy()
+    xd = to_packed(ctx, dw.DW_F32, x)
+    yd = ctx.empty_field(dw.DW_F32)
+    dw.ptnet_forward_tc(ctx, weights_to_dev(W), 1, xd, yd)
+    assert rel(from_packed(ctx, dw.DW_F32, yd), P.forward(W, x)) <= 2e-2

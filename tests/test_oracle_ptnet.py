@@ -77,3 +77,16 @@ def test_gradient_finite_differences(net):
                 fd = (P.loss_and_grad(Wp, xs, ys)[0] - P.loss_and_grad(Wm, xs, ys)[0]) / (2 * h)
                 an = G[li][idx].real if part == "re" else G[li][idx].imag
                 assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (li, idx, part, fd, an)
+
+
+def test_layer_adjoint_identity():
+    """(layer(w, h), g) = (h, layer_adjoint(w, g)) for a 16 -> 16 layer on random fields."""
+    from oracle.ptnet import PTNet, init_weights
+    L = (4, 2, 2, 2)
+    P = PTNet(WilsonClover(L, synth.random_gauge(L, 61).numpy(), 0.0, 1.0))
+    w = init_weights(16, seed=5, scale=0.7)[1]
+    h = synth.complex_gaussian((16,) + L + (4, 3), 62).numpy()
+    g = synth.complex_gaussian((16,) + L + (4, 3), 63).numpy()
+    lhs = np.vdot(P.layer(w, h), g)
+    rhs = np.vdot(h, P.layer_adjoint(w, g))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
