@@ -335,7 +335,8 @@ def profile_case(args, wl):
     """Small fixed launch sequences for ncu captures of single kernels (not a benchmark):
     'dirac-sap': 3 D applications and 2 M_sap (ncy = 1) in --prec;  'little': --solves FP32
     little solves to 1e-6 with an Ns-field subspace (4 inverse-iteration steps);  'batch12': one
-    batched solve of the 12 point sources."""
+    batched solve of the 12 point sources;  'ptnet': one 16 -> 16 network layer on the tensor cores
+    and one on the CUDA cores."""
     import torch
     import __graft_entry__ as ge
     ge.build()
@@ -344,7 +345,14 @@ def profile_case(args, wl):
     L = wl["L"]
     U = synth.random_gauge(L, wl["gauge_seed"], device="cuda").cpu()
     ctx = dw.dw_create(L, wl["m0"], wl["csw"], U, wl["sap_bs"])
-    if args.profile_case == "dirac-sap":
+    if args.profile_case == "ptnet":
+        # one 16 -> 16 network layer on the tensor cores and one on the CUDA cores
+        w = torch.randn(9 * 64 * 64 * 2, dtype=torch.float32, device="cuda") * 0.05
+        hin = torch.randn(16 * synth.volume(L) * 24, dtype=torch.float32, device="cuda")
+        hout = torch.empty_like(hin)
+        dw.ptnet_layer16(ctx, w, 0, 1, hin, hout)
+        dw.ptnet_layer16(ctx, w, 0, 0, hin, hout)
+    elif args.profile_case == "dirac-sap":
         prec = dw.DW_F32 if args.prec == "f32" else dw.DW_F64
         x, y = ctx.empty_field(prec), ctx.empty_field(prec)
         dw.dw_pack(ctx, prec, 1, synth.gaussian_source(L, 2).cuda(), x)
@@ -386,11 +394,12 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-batch", action="store_true", help="skip the 12 point-source batched solve")
-    ap.add_argument("--no-coherence", action="store_true", help="skip the low-mode / local-coherence measurement")
+    ap.add_argument("--coherence", action="store_true",
+                    help="also measure local coherence (24 low modes of D^+D, about two minutes at 48x24^3)")
     ap.add_argument("--no-ptnet", action="store_true", help="skip the network-layer timing")
     ap.add_argument("--no-table1", action="store_true",
                     help="skip the solver comparison over masses and the subspace generation variants")
-    ap.add_argument("--profile-case", choices=["dirac-sap", "little", "batch12"], default=None,
+    ap.add_argument("--profile-case", choices=["dirac-sap", "little", "batch12", "ptnet"], default=None,
                     help="run a small fixed launch sequence for an ncu capture and exit")
     ap.add_argument("--prec", default="f32", choices=["f32", "f64"], help="--profile-case dirac-sap precision")
     ap.add_argument("--solves", type=int, default=1, help="--profile-case little: number of little solves")
@@ -690,7 +699,7 @@ def main():
     # iteration, a block subspace (4^4 blocks) from half of them, deficits (3.15) of the others
     coherence = None
     dw.dw_release_workspace(ctx)
-    if not args.no_coherence:
+    if args.coherence:
         nev, nbuf = 24, 8
         st = synth.start_fields(L, nev + nbuf, 4242).cuda()
         modes = torch.empty((nev, V, 4, 3), dtype=torch.complex128, device="cuda")
