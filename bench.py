@@ -447,6 +447,7 @@ def main():
     dfl = dw.deflation_build(ctx, wl["dfl_bs"], wl["Ns"], wl["n_inv"], wl["ncy"], wl["nmr"], start,
                              basis_prec=dw.DW_BF16, iter_prec=dw.DW_F32)
     t_build = time.perf_counter() - t0
+    little_tune = dw.dfl_autotune(dfl)          # grid size and hop variant of the little solver
     p_mixed = dw.sol_params(tol=wl["tol"], nkv=wl["nkv"], ncy=wl["ncy"], nmr=wl["nmr"], mixed=1)
 
     def solve():
@@ -677,7 +678,9 @@ def main():
             with open(pk) as f:
                 bf16_peak = json.load(f).get("bf16_tflops", bf16_peak)
         ptl = {"flops_per_layer": flops}
-        for name, tc in (("tensor_cores_bf16", 1), ("cuda_cores_fp32", 0)):
+        for name, tc in (("tensor_cores_bf16", 1), ("tensor_cores_bf16_tile32", 1), ("cuda_cores_fp32", 0)):
+            if name.endswith("tile32"):
+                os.environ["DW_TC_TILE"] = "32"
             for _ in range(2):
                 dw.ptnet_layer16(ctx, wdev, 0, tc, hin, hout)
             ts = []
@@ -688,6 +691,7 @@ def main():
                 e1.record()
                 torch.cuda.synchronize()
                 ts.append(e0.elapsed_time(e1) / 1e3)
+            os.environ.pop("DW_TC_TILE", None)
             t = statistics.median(ts)
             ptl[name] = {"ms": t * 1e3, "tflops": flops / t / 1e12}
         ptl["tensor_cores_bf16"]["frac_of_bf16_peak"] = ptl["tensor_cores_bf16"]["tflops"] / bf16_peak
@@ -753,7 +757,7 @@ def main():
                 "little_iterations_per_solve": statistics.median([i.little_iterations for i in infos]),
                 "phase_s": {k: statistics.median([getattr(i, k) for i in infos])
                             for k in ("t_sap", "t_dirac", "t_project", "t_little", "t_orth", "t_restart")},
-                "dfl_build_s": t_build, "plain_fp64": plain,
+                "dfl_build_s": t_build, "little_autotune": little_tune, "plain_fp64": plain,
                 "speedup_vs_plain_fp64": (plain["s_per_solve"] / value) if plain else None,
                 "dirac": dirac, "roofline": roof, "roofline_sap": roof_sap, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "batch12": batch, "subspace_generation": gen,

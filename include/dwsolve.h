@@ -277,6 +277,12 @@ int gcr_solve(dw_ctx* ctx, dfl_ctx* d, const sol_params* p, int nrhs, const doub
  * (may be NULL).  Synchronous; allocates two temporary batches of fields. */
 int dw_autotune(dw_ctx* ctx, int nrhs, char* report, size_t report_len);
 
+/* Shape sweep of the FP32 cooperative little solver of d: grid sizes (all SMs, 3/4 and 1/2 of them)
+ * x hop variant (operator staged through a shared-memory ring by bulk copies / register-pipelined
+ * loads), timed with CUDA events on little solves of a fixed right-hand side; the fastest per
+ * iteration is kept in d.  JSON summary in report (may be NULL).  Synchronous. */
+int dfl_autotune(dfl_ctx* d, char* report, size_t report_len);
+
 /* Parallel-transport network of the learned subspace generation (3 layers, 1 -> C -> C -> 1
  * channels; each layer h'(x) = sum over the 9 transports {1, U_mu(x) . (x+mu), U_mu(x-mu)^+ . (x-mu)}
  * of a (channel x spin) matrix; gauge covariant).  Weights: ptnet_weight_count(C) complex FP32

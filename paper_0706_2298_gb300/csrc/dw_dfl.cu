@@ -26,6 +26,7 @@
 #include <cooperative_groups.h>
 #include <cstdio>
 #include <cstring>
+#include <string>
 #include <type_traits>
 
 #include "dw_common.cuh"
@@ -2675,6 +2676,79 @@ extern "C" int little_dirac_solve(dfl_ctx* d, int prec, const void* w, void* v, 
     if (e != cudaSuccess) return dw_cuda_fail(e, "little_dirac_solve");
   }
   return rc;
+}
+
+// Shape sweep of the FP32 cooperative little solver: grid sizes (all SMs, 3/4 and 1/2 of them, each
+// CTA then owning more block rows) x hop variant (shared-memory ring / register pipeline), timed
+// with CUDA events on little solves of a fixed random right-hand side to 1e-6; the fastest per
+// iteration is kept in the context.
+extern "C" int dfl_autotune(dfl_ctx* d, char* report, size_t report_len) {
+  if (!d) { dw_set_error("dfl_autotune: null context"); return DW_EINVAL; }
+  if (int rc = dw_check_device(d->c, "dfl_autotune")) return rc;
+  if (d->coop_grid <= 0 || d->illcond) {
+    if (report && report_len) snprintf(report, report_len, "{\"tuned\": false}");
+    return DW_OK;
+  }
+  cudaStream_t s = 0;
+  const size_t n2 = (size_t)d->N * 2;
+  float *w = nullptr, *v = nullptr;
+  DW_CUDA(cudaMalloc(&w, n2 * sizeof(float)));
+  DW_CUDA(cudaMalloc(&v, n2 * sizeof(float)));
+  {
+    std::vector<float> hw(n2);
+    uint64_t x = 0x9e3779b97f4a7c15ull;
+    for (auto& e : hw) { x ^= x << 13; x ^= x >> 7; x ^= x << 17; e = (float)((double)(x >> 11) / 9007199254740992.0 - 0.5); }
+    DW_CUDA(cudaMemcpy(w, hw.data(), n2 * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  const int full = d->coop_grid;
+  const bool ring_ok = d->coop_ring;
+  int best_grid = full;
+  bool best_ring = ring_ok;
+  double best = 1e300;
+  std::string rep = "{\"tuned\": true, \"us_per_iteration\": {";
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  bool first = true;
+  for (int gi = 0; gi < 3; ++gi) {
+    const int grid = gi == 0 ? full : (gi == 1 ? full * 3 / 4 : full / 2);
+    for (int rv = (ring_ok ? 1 : 0); rv >= 0; --rv) {
+      d->coop_grid = grid;
+      d->coop_ring = rv == 1;
+      int it = 0;
+      double rr = 0;
+      int rc = little_solve_t<float>(d, w, v, 1e-6, 2000, 24, &it, &rr, s);   // warm-up
+      if (rc < 0) { cudaFree(w); cudaFree(v); d->coop_grid = full; d->coop_ring = ring_ok; return rc; }
+      cudaEventRecord(e0, s);
+      int tot = 0;
+      for (int r = 0; r < 3; ++r) {
+        little_solve_t<float>(d, w, v, 1e-6, 2000, 24, &it, &rr, s);
+        tot += it;
+      }
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const double us = 1e3 * ms / std::max(tot, 1);
+      char buf[96];
+      snprintf(buf, sizeof buf, "%s\"grid %d %s\": %.2f", first ? "" : ", ", grid, rv ? "ring" : "registers", us);
+      rep += buf;
+      first = false;
+      if (us < best) { best = us; best_grid = grid; best_ring = rv == 1; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(w);
+  cudaFree(v);
+  d->coop_grid = best_grid;
+  d->coop_ring = best_ring;
+  char tail[128];
+  snprintf(tail, sizeof tail, "}, \"grid\": %d, \"ring\": %d}", best_grid, best_ring ? 1 : 0);
+  rep += tail;
+  if (report && report_len) snprintf(report, report_len, "%s", rep.c_str());
+  DW_CUDA(cudaGetLastError());
+  return DW_OK;
 }
 
 extern "C" int little_dirac_solve_batch(dfl_ctx* d, int prec, int nrhs, const void* w, void* v, double tol,

@@ -12,6 +12,7 @@
 // Weights: per layer 9 x (4 C_out) x (4 C_in) complex (FP32), layers stored back to back.
 // Channel fields are packed FP32 fields stored one after the other.
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <vector>
 
@@ -223,14 +224,22 @@ void launch_layer(dw_ctx* c, const float2* W, const float* in, float* out, cudaS
 // transports of direction d + 1 overlap the MMAs of direction d.  Operands are K-major without
 // swizzle: 8 x 16-byte core matrices, K-adjacent ones 128 bytes apart (leading byte offset),
 // 8-row groups 2048 bytes apart (stride byte offset).
-constexpr int TC_S = 64;                       // sites per tile
-constexpr int TC_M = 128, TC_K = 128, TC_N = 3 * TC_S;
+constexpr int TC_M = 128, TC_K = 128;
 constexpr int TC_THREADS = 256;
-constexpr uint32_t TC_TMEM_COLS = 256;
 constexpr int TC_A_BYTES = TC_M * TC_K * 2;    // 32 KB
-constexpr int TC_B_BYTES = TC_N * TC_K * 2;    // 48 KB
-constexpr int TC_STAGE_LD = TC_N + 1;          // FP32 staging row stride of the epilogue (bank-conflict free)
-constexpr size_t TC_SMEM = 2 * TC_A_BYTES + 2 * TC_B_BYTES + 1024;
+// per tile of S sites (S = 64: one CTA per SM; S = 32: two, for more warps hiding the transports)
+template <int S>
+struct TcTile {
+  static constexpr int N = 3 * S;                              // columns: (site, colour)
+  static constexpr int B_BYTES = N * TC_K * 2;                 // 48 KB / 24 KB
+  static constexpr uint32_t TMEM_COLS = N <= 128 ? 128u : 256u;
+  static constexpr int STAGE_LD = N + 1;                       // FP32 staging row stride (bank-conflict free)
+  static constexpr size_t SMEM = 2 * TC_A_BYTES + 2 * B_BYTES + 128;   // two per SM fit at S = 32
+  static constexpr int MIN_BLOCKS = S <= 32 ? 2 : 1;
+  // instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, N = 3S, M = 128
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+                                    ((uint32_t)(TC_M >> 4) << 24);
+};
 
 // byte offset of element (row, k) in a K-major no-swizzle operand with K = 128
 DW_HD uint32_t tc_off(int row, int k) {
@@ -243,14 +252,11 @@ DW_D uint64_t tc_desc(uint32_t saddr) {
   d |= (uint64_t)1 << 46;                      // descriptor version of tcgen05; no swizzle
   return d;
 }
-// instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, N = 192, M = 128
-constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
-                              ((uint32_t)(TC_M >> 4) << 24);
 
-DW_D void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+DW_D void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(accum) : "memory");
+      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum) : "memory");
 }
 DW_D void tc_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -284,20 +290,21 @@ __global__ void ptnet_tc_pack_kernel(const float2* __restrict__ W, __nv_bfloat16
   A[(size_t)d * TC_M * TC_K + tc_off(r, k) / 2] = __float2bfloat16_rn(val);
 }
 
-template <bool ADJ>
-__global__ void __launch_bounds__(TC_THREADS, 1) ptnet_tc_layer_kernel(Geom g, const float* __restrict__ links,
+template <bool ADJ, int S>
+__global__ void __launch_bounds__(TC_THREADS, TcTile<S>::MIN_BLOCKS) ptnet_tc_layer_kernel(Geom g, const float* __restrict__ links,
                                                                        const __nv_bfloat16* __restrict__ Apack,
                                                                        const float* __restrict__ in,
                                                                        float* __restrict__ out, int* err) {
+  using TT = TcTile<S>;
   extern __shared__ uint8_t tc_raw[];
   __shared__ uint64_t bar_tma[2], bar_mma[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int fail;
   const uint32_t raw = smem_u32(tc_raw);
-  uint8_t* sb = tc_raw + (((raw + 1023u) & ~1023u) - raw);       // 1024-byte aligned operand area
+  uint8_t* sb = tc_raw + (((raw + 127u) & ~127u) - raw);         // 128-byte aligned operand area
   uint8_t* abuf[2] = {sb, sb + TC_A_BYTES};
-  uint8_t* bbuf[2] = {sb + 2 * TC_A_BYTES, sb + 2 * TC_A_BYTES + TC_B_BYTES};
-  float* stage = reinterpret_cast<float*>(sb);                   // epilogue: [128][TC_STAGE_LD] FP32
+  uint8_t* bbuf[2] = {sb + 2 * TC_A_BYTES, sb + 2 * TC_A_BYTES + TT::B_BYTES};
+  float* stage = reinterpret_cast<float*>(sb);                   // epilogue: [128][TT::STAGE_LD] FP32
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     mbar_init(&bar_tma[0], 1);
@@ -309,7 +316,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ptnet_tc_layer_kernel(Geom g, c
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(TC_TMEM_COLS) : "memory");
+                 "r"(TT::TMEM_COLS) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
@@ -317,11 +324,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ptnet_tc_layer_kernel(Geom g, c
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
   const size_t V = g.V, fs = V * 24;
-  const long long ntiles = ((long long)V + TC_S - 1) / TC_S;
+  const long long ntiles = ((long long)V + S - 1) / S;
   uint32_t use[2] = {0, 0};
   int gc = 0;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long i0 = tile * TC_S;
+    const long long i0 = tile * S;
     for (int d = 0; d < 9; ++d) {
       const int b = gc & 1;
       // the MMAs that last read stage b must be complete before it is refilled
@@ -334,8 +341,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ptnet_tc_layer_kernel(Geom g, c
       }
       // B_d: item (site q, input channel c) -> rows (4c .. 4c+3) re and (64 + 4c ..) im, columns 3q + colour
       const int dt = (ADJ && d > 0) ? (((d - 1) ^ 1) + 1) : d;
-      for (int it = tid; it < TC_S * 16; it += TC_THREADS) {
-        const int q = it & (TC_S - 1), c = it / TC_S;
+      for (int it = tid; it < S * 16; it += TC_THREADS) {
+        const int q = it & (S - 1), c = it / S;
         const long long i = i0 + q;
         cplx<float> th[4][3];
         if (i < (long long)V) {
@@ -372,7 +379,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ptnet_tc_layer_kernel(Geom g, c
           const uint32_t a0 = smem_u32(abuf[b]), b0 = smem_u32(bbuf[b]);
 #pragma unroll
           for (int kk = 0; kk < TC_K / 16; ++kk)
-            tc_mma(tmem, tc_desc(a0 + kk * 256), tc_desc(b0 + kk * 256), (d > 0 || kk > 0) ? 1u : 0u);
+            tc_mma(tmem, tc_desc(a0 + kk * 256), tc_desc(b0 + kk * 256), TT::IDESC, (d > 0 || kk > 0) ? 1u : 0u);
           tc_commit(&bar_mma[b]);
         } else {
           fail = 1;
@@ -392,18 +399,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ptnet_tc_layer_kernel(Geom g, c
     {
       const int row = 32 * (warp & 3) + lane, half = warp >> 2;
 #pragma unroll
-      for (int j = 0; j < TC_N / 2 / 16; ++j) {
-        const int col = half * (TC_N / 2) + 16 * j;
+      for (int j = 0; j < TT::N / 2 / 16; ++j) {
+        const int col = half * (TT::N / 2) + 16 * j;
         float v[16];
         tc_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)col, v);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) stage[row * TC_STAGE_LD + col + e] = v[e];
+        for (int e = 0; e < 16; ++e) stage[row * TT::STAGE_LD + col + e] = v[e];
       }
     }
     tc_fence_before();
     __syncthreads();
-    for (int it = tid; it < TC_S * 16; it += TC_THREADS) {
-      const int q = it & (TC_S - 1), c = it / TC_S;
+    for (int it = tid; it < S * 16; it += TC_THREADS) {
+      const int q = it & (S - 1), c = it / S;
       const long long i = i0 + q;
       if (i >= (long long)V) continue;
       cplx<float> o[12];
@@ -412,7 +419,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ptnet_tc_layer_kernel(Geom g, c
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           const int m = 4 * c + sp, n = 3 * q + a;
-          o[3 * sp + a] = {stage[m * TC_STAGE_LD + n], stage[(m + 64) * TC_STAGE_LD + n]};
+          o[3 * sp + a] = {stage[m * TT::STAGE_LD + n], stage[(m + 64) * TT::STAGE_LD + n]};
         }
       store_site<float, 12>(out + (size_t)c * fs, V, i, o);
     }
@@ -422,39 +429,48 @@ __global__ void __launch_bounds__(TC_THREADS, 1) ptnet_tc_layer_kernel(Geom g, c
   __syncthreads();
   tc_fence_after();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TT::TMEM_COLS) : "memory");
 }
 
 // one 16 -> 16 layer (adjoint: W_d^+ and reversed transports) on the tensor cores
+template <bool ADJ, int S>
+static int launch_tc(dw_ctx* c, const __nv_bfloat16* A, const float* in, float* out, int* err, cudaStream_t st) {
+  using TT = TcTile<S>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    DW_CUDA(cudaFuncSetAttribute(ptnet_tc_layer_kernel<ADJ, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT::SMEM));
+    attr_set = true;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long ntiles = (c->V + S - 1) / S;
+  const unsigned grid = (unsigned)std::min<long long>(ntiles, (long long)sms * TT::MIN_BLOCKS);
+  ptnet_tc_layer_kernel<ADJ, S><<<grid, TC_THREADS, TT::SMEM, st>>>(c->g, (const float*)c->links[DW_F32], A, in, out, err);
+  dw_note_launch();
+  return DW_OK;
+}
+
+// one 16 -> 16 layer (adjoint: W_d^+ and reversed transports) on the tensor cores; tiles of 64 sites
+// (one CTA per SM) or, with DW_TC_TILE=32, of 32 sites (two CTAs per SM)
 int tc_layer16(dw_ctx* c, const float2* W, int adjoint, const float* in, float* out, cudaStream_t st) {
-  static bool attr_set[2] = {false, false};
   __nv_bfloat16* A = nullptr;
   int* err = nullptr;
   DW_CUDA(cudaMallocAsync((void**)&A, (size_t)9 * TC_A_BYTES, st));
   DW_CUDA(cudaMallocAsync((void**)&err, sizeof(int), st));
   DW_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
   const int n = 9 * TC_M * TC_K;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long ntiles = (c->V + TC_S - 1) / TC_S;
-  const unsigned grid = (unsigned)std::min<long long>(ntiles, sms);
+  const char* te = getenv("DW_TC_TILE");
+  const bool small = te && atoi(te) == 32;
+  int rc;
   if (adjoint) {
-    if (!attr_set[1]) {
-      DW_CUDA(cudaFuncSetAttribute(ptnet_tc_layer_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
-      attr_set[1] = true;
-    }
     ptnet_tc_pack_kernel<true><<<(n + 255) / 256, 256, 0, st>>>(W, A); dw_note_launch();
-    ptnet_tc_layer_kernel<true><<<grid, TC_THREADS, TC_SMEM, st>>>(c->g, (const float*)c->links[DW_F32], A, in, out, err);
+    rc = small ? launch_tc<true, 32>(c, A, in, out, err, st) : launch_tc<true, 64>(c, A, in, out, err, st);
   } else {
-    if (!attr_set[0]) {
-      DW_CUDA(cudaFuncSetAttribute(ptnet_tc_layer_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
-      attr_set[0] = true;
-    }
     ptnet_tc_pack_kernel<false><<<(n + 255) / 256, 256, 0, st>>>(W, A); dw_note_launch();
-    ptnet_tc_layer_kernel<false><<<grid, TC_THREADS, TC_SMEM, st>>>(c->g, (const float*)c->links[DW_F32], A, in, out, err);
+    rc = small ? launch_tc<false, 32>(c, A, in, out, err, st) : launch_tc<false, 64>(c, A, in, out, err, st);
   }
-  dw_note_launch();
+  if (rc) return rc;
   DW_CUDA(cudaGetLastError());
   int herr = 0;
   DW_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -94,6 +94,7 @@ _SIGNATURES = {
                                            C.POINTER(C.c_double), _P]),
     "gcr_solve": (C.c_int, [_P, _P, C.POINTER(SolParams), C.c_int, _P, _P, C.POINTER(SolInfo), _P]),
     "dw_autotune": (C.c_int, [_P, C.c_int, C.c_char_p, C.c_size_t]),
+    "dfl_autotune": (C.c_int, [_P, C.c_char_p, C.c_size_t]),
     "cgnr_solve": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.POINTER(C.c_int), C.POINTER(C.c_double), _P]),
     "lowmodes_solve": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, _P, _P,
                                  C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int), _P]),
@@ -367,6 +368,13 @@ def dw_autotune(ctx: Ctx, nrhs=1) -> dict:
     import json
     buf = C.create_string_buffer(1024)
     _check(lib().dw_autotune(ctx.handle, int(nrhs), buf, 1024))
+    return json.loads(buf.value.decode())
+
+
+def dfl_autotune(d: Dfl) -> dict:
+    import json
+    buf = C.create_string_buffer(1024)
+    _check(lib().dfl_autotune(d.handle, buf, 1024))
     return json.loads(buf.value.decode())
 
 

@@ -123,3 +123,18 @@ def test_autotune(setup):
     rep = dw.dw_autotune(ctx, 4)
     assert rep["rgroup"] in (1, 2, 3) and rep["sap_staged"] in (0, 1)
     assert all(v > 0 for v in rep["dirac_mrhs_ms"].values())
+
+
+def test_little_solver_autotune(setup, dfl):
+    """The shape sweep of the cooperative little solver keeps a configuration it timed, and the
+    solver still reaches the tolerance with it."""
+    ctx, D = setup
+    rep = dw.dfl_autotune(dfl)
+    assert rep["tuned"] and rep["grid"] > 0 and rep["ring"] in (0, 1)
+    assert all(v > 0 for v in rep["us_per_iteration"].values())
+    eta = synth.gaussian_source(L, 25)
+    psi = torch.empty_like(eta, device="cuda")
+    rc, _ = dw.gcr_solve(ctx, dfl, dw.sol_params(tol=1e-10, mixed=1), 1, eta.cuda(), psi)
+    assert rc == dw.DW_OK
+    r = np.linalg.norm(eta.numpy() - D.apply(psi.cpu().numpy())) / np.linalg.norm(eta.numpy())
+    assert r <= 1.05e-10

@@ -135,12 +135,14 @@ def test_trained_network_gains_over_equal_cost_plain():
     assert all(r["converged"] and r["relres"] <= 1e-10 for r in res.values())
 
 
+@pytest.mark.parametrize("tile", ["64", "32"])
 @pytest.mark.parametrize("adjoint", [0, 1])
-def test_layer16_tensor_cores(setup, adjoint):
+def test_layer16_tensor_cores(setup, adjoint, tile, monkeypatch):
     """The 16 -> 16 layer (and its adjoint) on the tcgen05 tensor cores with BF16 operands and FP32
     accumulation against the FP64 oracle (BF16 path: within 2e-2; the rounding of 576-term sums of
     BF16 products gives a few 1e-3), and the FP32 CUDA-core path within 2e-5."""
     ctx, P = setup
+    monkeypatch.setenv("DW_TC_TILE", tile)        # 64 sites per tile (one CTA per SM) or 32 (two)
     w = init_weights(16, seed=7, scale=0.6)[1]
     h = synth.complex_gaussian((16, ctx.V, 4, 3), 71).numpy()
     hg = h.reshape((16,) + L + (4, 3))
