@@ -62,9 +62,9 @@ PLAIN_COUNTS = os.path.join(ROOT, "paper_0706_2298_gb300", "plain_gcr_counts.jso
 
 # DRAM bytes per little-GCR iteration of the cooperative kernel, from one ncu capture of the
 # current kernel (dram__bytes_read.sum + dram__bytes_write.sum of one launch / its iterations):
-# 48x24^3, Ns = 20: (84.87 + 4.76) MB over 42 iterations (cold cache: the first iteration reads
+# 48x24^3, Ns = 20: (76.61 + 3.65) MB over 41 iterations (cold cache: the first iteration reads
 # the little operator from HBM, the rest hit L2).  Remove an entry when the kernel changes.
-LITTLE_TRAFFIC = {("24^3x48", 20): 89.63e6 / 42}
+LITTLE_TRAFFIC = {("24^3x48", 20): 80.26e6 / 41}
 
 
 def aggregate_ranks(t_ms, steps, world, device="cpu"):
