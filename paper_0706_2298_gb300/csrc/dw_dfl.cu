@@ -1052,21 +1052,32 @@ DW_D void coop_hop_ring(HopRing<NS>& rg, int nrow, const int* list, const int* l
   ring_prefetch<NS>(rg, M, nrow, list);            // normally done at the end of the previous hop
   for (int r0 = rb; r0 < re; r0 += COOP_CH) {
     const int nr = min(COOP_CH, re - r0);
+    // the source entries of every row of the chunk (direction w) into the warp's slots of hp: all
+    // the gathers are in flight together instead of one L2 round trip per row
+    if (lane < NS)
+      for (int q = 0; q < nr; ++q) {
+        const int j = __ldg(lnb + (size_t)(r0 + q) * 8 + w);
+        cplx<float> x = src[(size_t)j * NS + lane];
+        if (corr) x -= cs * corr[(size_t)j * NS + lane];
+        hp[(q * 8 + w) * 32 + lane] = x;
+      }
+    __syncwarp();
     for (int q = 0; q < nr; ++q) {
       const uint32_t c = rg.cons, sl = c % RING_SLOTS;
-      const int j = __ldg(lnb + (size_t)(r0 + q) * 8 + w);
-      cplx<float> x = lane < NS ? src[(size_t)j * NS + lane] : cplx<float>{0.f, 0.f};
-      if (corr && lane < NS) x -= cs * corr[(size_t)j * NS + lane];
       if (!mbar_wait(&rg.full[sl], (c / RING_SLOTS) & 1, rg.err)) break;
       const cplx<float>* Mb = reinterpret_cast<const cplx<float>*>(rg.slots + (size_t)sl * HopRing<NS>::stride()) +
                               (size_t)w * NS * NS;
-      cplx<float> acc = {0.f, 0.f};
+      const cplx<float>* xq = hp + (q * 8 + w) * 32;           // broadcast reads
+      cplx<float> a0 = {0.f, 0.f}, a1 = {0.f, 0.f};            // two chains of FMAs
+      if (lane < NS) {
 #pragma unroll
-      for (int col = 0; col < NS; ++col) {
-        const cplx<float> xc = {__shfl_sync(0xffffffffu, x.re, col), __shfl_sync(0xffffffffu, x.im, col)};
-        if (lane < NS) acc += Mb[col * NS + lane] * xc;
+        for (int col = 0; col < NS; col += 2) {
+          a0 += Mb[col * NS + lane] * xq[col];
+          if (col + 1 < NS) a1 += Mb[(col + 1) * NS + lane] * xq[col + 1];
+        }
       }
-      hp[(q * 8 + w) * 32 + lane] = acc;
+      __syncwarp();
+      hp[(q * 8 + w) * 32 + lane] = a0 + a1;
       __syncwarp();
       if (lane == 0) mbar_arrive(&rg.empty[sl]);
       ++rg.cons;
@@ -1292,18 +1303,23 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_kernel(CoopAr
       // chi'_k = P~_L chi_k - sum_j b_jk chi'_j / c_j ; then (chi'_k, rho_k), |chi'_k|^2, (B^ g_l, chi'_k)
       T s3[3] = {0, 0, 0};
       slice([&](size_t i) {
-        cplx<T> y = ck[i];
+        cplx<T> y = ck[i], y2 = {T(0), T(0)};         // two chains of FMAs
         if (a.a3) {
 #pragma unroll
           for (int l = 0; l < NSM; ++l)
-            if (l < ns) y -= cplx<T>{sh.z[2 * l], sh.z[2 * l + 1]} * Bg[(size_t)l * n + i];
+            if (l < ns) {
+              const cplx<T> t = cplx<T>{sh.z[2 * l], sh.z[2 * l + 1]} * Bg[(size_t)l * n + i];
+              if (l & 1) y2 -= t; else y -= t;
+            }
         }
 #pragma unroll
         for (int j = 0; j < COOP_NKV; ++j)
           if (j < k) {
             const T ic = T(1) / sh.c[j];
-            y -= cplx<T>{sh.bb[j][2 * k] * ic, sh.bb[j][2 * k + 1] * ic} * chi(j)[i];
+            const cplx<T> t = cplx<T>{sh.bb[j][2 * k] * ic, sh.bb[j][2 * k + 1] * ic} * chi(j)[i];
+            if (j & 1) y2 -= t; else y -= t;
           }
+        y += y2;
         ck[i] = y;
         const cplx<T> r = rk[i];
         s3[0] += y.re * r.re + y.im * r.im;

@@ -51,45 +51,6 @@ DW_D void pt_transport(const Geom& g, const float* __restrict__ links, const flo
   }
 }
 
-// pt_transport split into its loads and its arithmetic, so that a thread can have the loads of
-// two transports in flight before it multiplies
-struct PtLoad {
-  cplx<float> p[12];
-  SU3<float> U;
-  float sg;
-  int kind;          // 0: identity, 1: U h(x+mu), 2: U^+ h(x-mu)
-};
-DW_D void pt_fetch(const Geom& g, const float* __restrict__ links, const float* __restrict__ f, const SiteRef& s,
-                   long long i, int d, PtLoad& o) {
-  const size_t V = g.V;
-  if (d == 0) {
-    load_site<float, 12>(f, V, i, o.p);
-    o.kind = 0;
-    return;
-  }
-  const int nd = d - 1, mu = nd >> 1;
-  bool cr;
-  const long long j = neighbour(g, s, nd, &cr);
-  o.sg = time_wrap(g, s, nd) ? -1.f : 1.f;
-  load_link(links, V, mu, (nd & 1) ? j : i, o.U);
-  load_site<float, 12>(f, V, j, o.p);
-  o.kind = (nd & 1) ? 2 : 1;
-}
-DW_D void pt_finish(const PtLoad& in, cplx<float> (*o)[3]) {
-#pragma unroll
-  for (int sp = 0; sp < 4; ++sp) {
-    if (in.kind == 0) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) o[sp][a] = in.p[3 * sp + a];
-    } else {
-      cplx<float> w[3];
-      if (in.kind == 2) su3_dag_mul(in.U, in.p + 3 * sp, w); else su3_mul(in.U, in.p + 3 * sp, w);
-#pragma unroll
-      for (int a = 0; a < 3; ++a) o[sp][a] = in.sg * w[a];
-    }
-  }
-}
-
 // one layer (ADJ = false) or its adjoint (ADJ = true); thread = (site, output channel)
 template <int CIN, int COUT, bool ADJ>
 __global__ void __launch_bounds__(PT_THREADS) ptnet_layer_kernel(Geom g, const float* __restrict__ links,
@@ -380,25 +341,13 @@ __global__ void __launch_bounds__(TC_THREADS, TcTile<S>::MIN_BLOCKS) ptnet_tc_la
       }
       // B_d: item (site q, input channel c) -> rows (4c .. 4c+3) re and (64 + 4c ..) im, columns 3q + colour
       const int dt = (ADJ && d > 0) ? (((d - 1) ^ 1) + 1) : d;
-      for (int it0 = tid; it0 < S * 16; it0 += 2 * TC_THREADS) {
-        // two transports per thread: both loads issued before either is multiplied
-        PtLoad ld[2];
-        bool ok[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int it = it0 + u * TC_THREADS;
-          const long long i = i0 + (it & (S - 1));
-          ok[u] = it < S * 16 && i < (long long)V;
-          if (ok[u]) pt_fetch(g, links, in + (size_t)(it / S) * fs, decode(g, i), i, dt, ld[u]);
-        }
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-        const int it = it0 + u * TC_THREADS;
-        if (it >= S * 16) break;
+      for (int it = tid; it < S * 16; it += TC_THREADS) {
         const int q = it & (S - 1), c = it / S;
+        const long long i = i0 + q;
         cplx<float> th[4][3];
-        if (ok[u]) {
-          pt_finish(ld[u], th);
+        if (i < (long long)V) {
+          const SiteRef s = decode(g, i);
+          pt_transport(g, links, in + (size_t)c * fs, s, i, dt, th);
         } else {
 #pragma unroll
           for (int sp = 0; sp < 4; ++sp)
@@ -419,7 +368,6 @@ __global__ void __launch_bounds__(TC_THREADS, TcTile<S>::MIN_BLOCKS) ptnet_tc_la
           vi.y = *reinterpret_cast<uint32_t*>(&im23);
           *reinterpret_cast<uint2*>(bbuf[b] + tc_off(n, 4 * c)) = vr;
           *reinterpret_cast<uint2*>(bbuf[b] + tc_off(n, 64 + 4 * c)) = vi;
-        }
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");    // generic-proxy writes -> tensor core
