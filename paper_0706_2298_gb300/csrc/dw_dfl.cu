@@ -777,6 +777,8 @@ struct CoopArgs {
   double* acc;        // [3][COOP_NV] reduction accumulators, zero at launch
   double* out;        // [0] iterations, [1] relative residual
   int* err;           // set when a bounded wait of the shared-memory ring gave up
+  int vec_rows;       // > 0: this CTA's slices of g, B^ g and chi'_j (vec_rows block rows each) are kept
+                      // in dynamic shared memory after the hop partial sums (register-pipelined hops)
   double tol;
 };
 
@@ -794,6 +796,7 @@ struct CoopShared {
   T z[2 * 32];
   T ainv[2 * 32 * 32];       // A~^{-1}, row-major
   T ac[2];                   // a_{k-1} / c_{k-1}: rho_k = rho_{k-1} - ac chi'_{k-1}
+  T bbn[2 * COOP_NKV];       // b_jk / c_j of the current step (coefficients on the unnormalised chi'_j)
   T rr;                      // this CTA's share of |rho_k|^2 (folded into the next reduction)
   int phase;
 };
@@ -1177,6 +1180,15 @@ DW_D void coop_PL(cg::grid_group& grid, CoopShared<T>& sh, const CoopArgs<T>& a,
   }
 }
 
+// shared memory of the vector slices (g, B^ g: Ns vectors each; chi'_j: nkv vectors) of a CTA that
+// owns `rows` block rows; the register-pipelined kernels are given up to coop_vec_smem_max() bytes
+template <typename T>
+inline size_t coop_vec_smem(int rows, int Ns, int nkv) {
+  return (size_t)(2 * Ns + nkv) * rows * Ns * 2 * sizeof(T);
+}
+template <typename T>
+inline size_t coop_vec_smem_max() { return (sizeof(T) == 4 ? 200 : 180) * 1024; }   // + static CoopShared <= 227 KB
+
 // dynamic shared memory of the ring variant: hop partial sums, the slots, their barriers
 template <int NS>
 inline size_t coop_ring_smem() {
@@ -1224,6 +1236,26 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_kernel(CoopAr
   __syncthreads();
   cplx<T>* W = reinterpret_cast<cplx<T>*>(a.work);
   cplx<T>* rhob[2] = {W + (size_t)2 * nkv * n, W + (size_t)(2 * nkv + 1) * n};
+  // shared-memory copies of this CTA's slices (index i - s0): g, B^ g (constant) and chi'_j
+  const bool vs = !RING && a.vec_rows > 0;
+  const size_t vstr = (size_t)a.vec_rows * ns;
+  cplx<T>* gS = reinterpret_cast<cplx<T>*>(coop_dyn + (size_t)COOP_CH * 8 * 64 * sizeof(T));
+  cplx<T>* bgS = gS + (size_t)ns * vstr;
+  cplx<T>* chiS = bgS + (size_t)ns * vstr;
+  if (vs && a.a3) {
+    for (size_t e = threadIdx.x; e < (size_t)ns * (sl.s1 - sl.s0); e += COOP_THREADS) {
+      const size_t l = e / (sl.s1 - sl.s0), i = sl.s0 + e % (sl.s1 - sl.s0);
+      gS[l * vstr + (i - sl.s0)] = reinterpret_cast<const cplx<T>*>(a.g)[l * n + i];
+      bgS[l * vstr + (i - sl.s0)] = reinterpret_cast<const cplx<T>*>(a.Bg)[l * n + i];
+    }
+    __syncthreads();
+  }
+  // the vectors as seen by the inner products and updates of a step (shifted so that entry i of
+  // vector j sits at [j * stride + i] for this CTA's i)
+  const cplx<T>* gV = vs ? gS - sl.s0 : reinterpret_cast<const cplx<T>*>(a.g);
+  const cplx<T>* bgV = vs ? bgS - sl.s0 : reinterpret_cast<const cplx<T>*>(a.Bg);
+  const cplx<T>* chiV = vs ? chiS - sl.s0 : W;
+  const size_t vn = vs ? vstr : n;
   cplx<T>* tmpo = W + (size_t)(2 * nkv + 2) * n;
   cplx<T>* t = W + (size_t)(2 * nkv + 3) * n;
   cplx<T>* rhsd = W + (size_t)(2 * nkv + 4) * n;
@@ -1273,8 +1305,8 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_kernel(CoopAr
       __syncthreads();
       hop_any<T, NS, RING>(rg, a, false, tmpo, nullptr, zero, rk, ck, T(-1), hp);
       // one reduction: u = g^+ chi_k (A.3), the raw coefficients (chi'_j, chi_k), j < k, and |rho_k|^2
-      if (a.a3) cta_dots<T>(sh, g, n, ns, ck, sl, 0);
-      if (k > 0) cta_dots<T>(sh, W, n, k, ck, sl, na);
+      if (a.a3) cta_dots<T>(sh, gV, vn, ns, ck, sl, 0);
+      if (k > 0) cta_dots<T>(sh, chiV, vn, k, ck, sl, na);
       __syncthreads();
       if (threadIdx.x == 0) sh.cta[na + 2 * k] = sh.rr;
       coop_reduce(grid, sh, na + 2 * k + 1, a.acc);
@@ -1298,6 +1330,8 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_kernel(CoopAr
         }
         sh.bb[j][2 * k] = br;
         sh.bb[j][2 * k + 1] = bi;
+        sh.bbn[2 * j] = br * ic;
+        sh.bbn[2 * j + 1] = bi * ic;
       }
       __syncthreads();
       // chi'_k = P~_L chi_k - sum_j b_jk chi'_j / c_j ; then (chi'_k, rho_k), |chi'_k|^2, (B^ g_l, chi'_k)
@@ -1308,26 +1342,26 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_kernel(CoopAr
 #pragma unroll
           for (int l = 0; l < NSM; ++l)
             if (l < ns) {
-              const cplx<T> t = cplx<T>{sh.z[2 * l], sh.z[2 * l + 1]} * Bg[(size_t)l * n + i];
+              const cplx<T> t = cplx<T>{sh.z[2 * l], sh.z[2 * l + 1]} * bgV[(size_t)l * vn + i];
               if (l & 1) y2 -= t; else y -= t;
             }
         }
 #pragma unroll
         for (int j = 0; j < COOP_NKV; ++j)
           if (j < k) {
-            const T ic = T(1) / sh.c[j];
-            const cplx<T> t = cplx<T>{sh.bb[j][2 * k] * ic, sh.bb[j][2 * k + 1] * ic} * chi(j)[i];
+            const cplx<T> t = cplx<T>{sh.bbn[2 * j], sh.bbn[2 * j + 1]} * chiV[(size_t)j * vn + i];
             if (j & 1) y2 -= t; else y -= t;
           }
         y += y2;
         ck[i] = y;
+        if (vs) chiS[(size_t)k * vstr + (i - sl.s0)] = y;
         const cplx<T> r = rk[i];
         s3[0] += y.re * r.re + y.im * r.im;
         s3[1] += y.re * r.im - y.im * r.re;
         s3[2] += y.re * y.re + y.im * y.im;
       });
       cta_sum<T, 3>(sh, s3);
-      if (a.a3) cta_dots<T>(sh, Bg, n, ns, ck, sl, 3);
+      if (a.a3) cta_dots<T>(sh, bgV, vn, ns, ck, sl, 3);
       coop_reduce(grid, sh, 3 + na, a.acc);
       const T cn = sqrt(sh.res[2]);
       if (!(cn > 0)) break;
@@ -2274,12 +2308,22 @@ static int little_gcr_coop(dfl_ctx* d, const T* b, T* v, double tol, int maxit, 
   a.work = lwork<T>(d, 0);
   a.acc = d->coop_partial;                                   // [3][COOP_NV] accumulators
   a.err = d->coop_err;
+  a.vec_rows = 0;
   DW_CUDA(cudaMemsetAsync(d->coop_partial, 0, 3 * COOP_NV * sizeof(double), s));
   a.out = d->coop_out + (d->defer_slot >= 0 ? 2 * d->defer_slot : 0);
   a.tol = tol;
   void* args[] = {&a};
   cudaError_t le = cudaSuccess;
-  const size_t dsm = coop_dyn_smem<T>(d->coop_grid);
+  size_t dsm = coop_dyn_smem<T>(d->coop_grid);
+  if (!d->coop_ring || sizeof(T) == 8) {
+    // register-pipelined hops leave shared memory free for the CTA's vector slices
+    const int rows = (d->Ne + d->coop_grid - 1) / d->coop_grid;
+    const size_t extra = coop_vec_smem<T>(rows, d->Ns, nkv);
+    if (dsm + extra <= coop_vec_smem_max<T>()) {
+      a.vec_rows = rows;
+      dsm += extra;
+    }
+  }
   if constexpr (sizeof(T) == 8) {
     NS_DISPATCH_FEW(d->Ns, (le = cudaLaunchCooperativeKernel((void*)little_gcr_coop_kernel<T, NSV>, d->coop_grid,
                                                        COOP_THREADS, args, dsm, s)));
@@ -2969,9 +3013,11 @@ static int little_setup(dw_ctx* c, dfl_ctx* d, const double* B64_given) {
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     const size_t dsm32 = coop_dyn_smem<float>(sms), dsm64 = coop_dyn_smem<double>(sms);
     NS_DISPATCH(Ns, (cudaFuncSetAttribute(little_gcr_coop_kernel<float, NSV>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm32)));
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)coop_vec_smem_max<float>())));
     NS_DISPATCH_FEW(Ns, (cudaFuncSetAttribute(little_gcr_coop_kernel<double, NSV>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm64)));
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)coop_vec_smem_max<double>())));
     NS_DISPATCH(Ns, (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, little_gcr_coop_kernel<float, NSV>,
                                                                    COOP_THREADS, dsm32)));
     NS_DISPATCH_FEW(Ns, (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, little_gcr_coop_kernel<double, NSV>,
