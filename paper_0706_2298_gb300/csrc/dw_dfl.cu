@@ -70,11 +70,11 @@ struct dfl_ctx {
   double* Ainv64 = nullptr; float* Ainv32 = nullptr;   // device copies of A~^{-1}
   int coop_grid = 0;                                   // CTAs of the cooperative little solver (0: not possible)
   bool coop_m = false;                                 // multi-RHS cooperative little solver available
-  float* mw = nullptr;                                 // its work: (2 COOP_NKV + 4) x COOP_MAXR vectors
+  float* mw = nullptr;                                 // its work: 2 COOP_NKV + 6 vectors of COOP_MRP systems
   float* mio = nullptr;                                // right-hand sides and solutions [2][COOP_MAXR][Ne Ns]
   float* meo = nullptr;                                // odd-part work [2][COOP_MAXR][No Ns]
-  float* mpart = nullptr;                              // reduction partials [COOP_MNV][Gp]
-  float* mred = nullptr;                               // reduction results [COOP_MNV]
+  double* macc = nullptr;                              // reduction accumulators [3][COOP_MNV]
+  float* mscr = nullptr;                               // per-CTA coefficient tables of the multi-RHS solver
   float* mtol = nullptr;                               // tolerances [COOP_MAXR]
   double* mout = nullptr;                              // iterations, relative residuals [COOP_MAXR][2]
   int defer_slot = -1;                                 // >= 0: write results to coop_out[2*slot], no host sync
@@ -1459,485 +1459,693 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_kernel(CoopAr
 }
 
 // ------------------------------------------------------------------ multi-RHS cooperative little GCR
-// Up to COOP_MAXR little systems (the same operator, several right-hand sides) solved in lockstep
-// by one persistent kernel (FP32): every GCR step of every right-hand side shares the grid
-// barriers and reductions, and each block row of the operator is read once per step for all of
-// them.  Each right-hand side keeps its own GCR scalars, tolerance and convergence flag; a
-// converged (or stalled) right-hand side is frozen while the others continue.  Vectors are stored
-// [kind][rhs][n].  Reductions with many values use two phases: CTA c adds the partials of the
-// values v = c, c + G, ... (fixed order), a second barrier publishes the sums.
+// Up to COOP_MAXR little systems with the same operator, solved in lockstep by one persistent kernel
+// (FP32).  The GCR steps of all systems share the hops (each operator block is read once per step
+// for all of them), the grid barriers and the reductions; every system keeps its own scalars,
+// tolerance and convergence flag and is frozen once it has converged.  A step is the one of the
+// one-system kernel: odd hop on rho_{k-1} - (a/c) chi'_{k-1}, even hop, one reduction for g^+ chi_k,
+// (chi'_j, chi_k) and |rho_k|^2, the projected and orthogonalised chi'_k with its inner products, a
+// second reduction, the local update of rho.  The vectors hold the systems innermost, padded to RP
+// (a power of two, >= 2): entry i of system r at [i RP + r], padding entries zero.  In the passes
+// over a CTA's entries a lane always serves the same pair of systems (one float4) and every entry
+// is always handled by the same thread, so the per-system sums meet by warp shuffles and the passes
+// need no CTA barrier between them; the sums over CTAs are FP64 atomics, one grid barrier each.
 constexpr int COOP_MAXR = 12;
-constexpr int COOP_MNV = COOP_MAXR * (2 * 32 + 2 * COOP_NKV);   // values of the largest reduction
+constexpr int COOP_MRP = 16;                              // RP of COOP_MAXR systems
+constexpr int COOP_MST = 2 * 32 + 2 * COOP_NKV + 4;       // reduced values per system, at most
+constexpr int COOP_MNV = COOP_MAXR * COOP_MST;
+constexpr int COOP_MVG = 8;                               // vectors per pass of the slice inner products
+
+DW_HD int coop_mrp(int R) {
+  int p = 2;
+  while (p < R) p <<= 1;
+  return p;
+}
 
 struct CoopMArgs {
-  int Ne, No, nkv, maxit, a3, R;
+  int Ne, No, nkv, maxit, a3, R, RP;
   const int *list_e, *list_o, *lnb_e, *lnb_o;
-  const float *M, *g, *Bg, *Ainv, *b;
+  const float *M, *g, *Bg, *Ainv;
+  const float* b;     // [R][Ne Ns] complex right-hand sides
   const float* tol;   // [R] relative tolerances
-  float* v;           // [R][Ne Ns] complex
-  float* work;        // (2 nkv + 4) x R vectors of Ne Ns complex
-  float* partial;     // [COOP_MNV][Gp]
-  float* red;         // [COOP_MNV]
+  float* v;           // [R][Ne Ns] complex solutions
+  float* work;        // 2 nkv + 6 vectors of max(Ne, No) Ns RP complex
+  float* scratch;     // per-CTA coefficient tables, coop_m_cta_scratch(Ns) floats each
+  double* acc;        // [3][COOP_MNV] reduction accumulators, zero at launch
   double* out;        // [R][2]: iterations, relative residual
 };
 
-struct CoopMShared {
-  float cta[COOP_MNV];
-  float res[COOP_MNV];
-  float ws[COOP_WARPS][3 * COOP_MAXR];
-  float z[COOP_MAXR][2 * 32];
-  float ainv[2 * 32 * 32];
-  float a[COOP_MAXR][2 * COOP_NKV], c[COOP_MAXR][COOP_NKV], beta[COOP_MAXR][2 * COOP_NKV];
-  float bn[COOP_MAXR], rn[COOP_MAXR];
+struct __align__(16) CoopMShared {
+  float cta[COOP_MNV];                                   // this CTA's share of a reduction
+  float res[COOP_MNV];                                   // the reduced values
+  float part[COOP_WARPS][COOP_MVG][COOP_MRP / 2][4];     // warp sums of the slice inner products
+  float ainv[2 * 32 * 32];                               // A~^{-1}, row-major
+  float z[32][COOP_MRP][2];                              // A~^{-1} u per system (zero for idle ones)
+  float bbn[COOP_NKV][COOP_MRP][2];                      // coefficients on chi'_j of a slice update
+  float cf[COOP_MRP][2];                                 // a_k / c_k of the current step
+  float ac[COOP_MRP][2];                                 // a_{k-1} / c_{k-1}: rho_k = rho_{k-1} - ac chi'_{k-1}
+  float rr[COOP_MRP];                                    // this CTA's share of |rho_k|^2 (next reduction)
+  float c[COOP_MAXR][COOP_NKV], a[COOP_MAXR][2 * COOP_NKV], beta[COOP_MAXR][2 * COOP_NKV];
+  float bn[COOP_MAXR], rn[COOP_MAXR], rn2[COOP_MAXR];
   int live[COOP_MAXR], kr[COOP_MAXR], its[COOP_MAXR];
-  int any;
+  int phase, any;
 };
 
-// dynamic shared memory: bb [R][nkv][2 nkv], tg [R][nkv][2 NS], staged neighbour vectors
-// xs [2][8][R][NS] complex, direction partial sums hp [2][R][8][NS] complex
-constexpr int COOP_YS_CAP = 2048;     // complex numbers of the shared-memory mirror of chi_k (all RHS)
-__host__ __device__ inline size_t coop_m_dyn_bytes(int ns) {
-  return ((size_t)COOP_MAXR * COOP_NKV * 2 * COOP_NKV + (size_t)COOP_MAXR * COOP_NKV * 2 * ns +
-          (size_t)2 * 8 * COOP_MAXR * ns * 2 + (size_t)2 * COOP_MAXR * 8 * ns * 2 + (size_t)COOP_YS_CAP * 2) *
-         sizeof(float);
+// dynamic shared memory: the operator blocks of a row Ms [2][8 NS NS] and the staged neighbour
+// blocks xs, cs [2][8 NS RP] (double-buffered), direction sums hp [8][NS RP], complex
+__host__ __device__ inline size_t coop_m_dyn_bytes(int ns, int rp) {
+  return ((size_t)2 * 8 * ns * ns + (size_t)2 * 2 * 8 * ns * rp + (size_t)8 * ns * rp) * 2 * sizeof(float);
+}
+// per-CTA global scratch of the multi-RHS solver: tg [COOP_MAXR][COOP_NKV][NS] = (chi_j, B^ g_l) and
+// the GCR coefficients bb [COOP_MAXR][COOP_NKV][COOP_NKV], complex
+__host__ __device__ inline size_t coop_m_cta_scratch(int ns) {
+  return (size_t)COOP_MAXR * COOP_NKV * (ns + COOP_NKV) * 2;          // floats
 }
 
-// sums of sh.cta[0..nv) over all CTAs into sh.res (all CTAs); two grid barriers
-DW_D void coop_mreduce(cg::grid_group& grid, CoopMShared& sh, int nv, float* partial, float* red) {
-  const int G = gridDim.x, Gp = coop_gpad(G);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+DW_D void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+DW_D void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+DW_D void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// sums of sh.cta[0..nv) over all CTAs into sh.res: FP64 atomics into accumulator set (phase mod 3),
+// one grid barrier; CTA 0 clears the set used two reductions ahead (as coop_reduce)
+DW_D void coop_mreduce(cg::grid_group& grid, CoopMShared& sh, int nv, double* acc_base) {
   __syncthreads();
-  for (int v = threadIdx.x; v < nv; v += COOP_THREADS) partial[(size_t)v * Gp + blockIdx.x] = sh.cta[v];
+  double* acc = acc_base + (size_t)(sh.phase % 3) * COOP_MNV;
+  for (int v = threadIdx.x; v < nv; v += COOP_THREADS) atomicAdd(acc + v, (double)sh.cta[v]);
+  __syncthreads();
   grid.sync();
-  for (int v = blockIdx.x + w * G; v < nv; v += COOP_WARPS * G) {
-    float y0 = 0.f, y1 = 0.f;
-    int q = lane;
-    for (; q + 32 < G; q += 64) { y0 += __ldcg(partial + (size_t)v * Gp + q); y1 += __ldcg(partial + (size_t)v * Gp + q + 32); }
-    if (q < G) y0 += __ldcg(partial + (size_t)v * Gp + q);
-    const float y = warp_allsum(y0 + y1);
-    if (lane == 0) red[v] = y;
+  for (int v = threadIdx.x; v < nv; v += COOP_THREADS) sh.res[v] = (float)__ldcg(acc + v);
+  if (blockIdx.x == 0) {
+    double* old = acc_base + (size_t)((sh.phase + 2) % 3) * COOP_MNV;
+    for (int v = threadIdx.x; v < COOP_MNV; v += COOP_THREADS) old[v] = 0.0;
   }
-  grid.sync();
-  for (int v = threadIdx.x; v < nv; v += COOP_THREADS) sh.res[v] = __ldcg(red + v);
+  __syncthreads();
+  if (threadIdx.x == 0) sh.phase += 1;
   __syncthreads();
 }
 
-// per-thread values x[j][r] (j < NVAL, r < R) -> CTA sums in sh.cta[r * stride + j]
-template <int NVAL>
-DW_D void cta_msum(CoopMShared& sh, const float (&x)[NVAL][COOP_MAXR], int R, int stride) {
+// lane mapping of the passes over this CTA's even entries s0 + e, e < S: the thread handles the
+// system pair rq (float4 rq of an entry, RP / 2 per entry) of the entries e0, e0 + estep, ...
+template <int RP>
+struct MLane {
+  static constexpr int RQ = RP / 2, EPW = 32 / RQ, ESTEP = COOP_WARPS * EPW;
+  int rq, e0, S;
+  size_t s0;
+  DW_D MLane(int nrow, int ns) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    rq = lane % RQ;
+    e0 = w * EPW + lane / RQ;
+    int rb, re;
+    coop_row_range(nrow, &rb, &re);
+    s0 = (size_t)rb * ns;
+    S = (re - rb) * ns;
+  }
+};
+
+// per-thread values s[h NV + f] (value f of system 2 rq + h) -> their CTA sums dst[r ST + off + f]
+template <int RP, int NV>
+DW_D void mslice_sum(CoopMShared& sh, const MLane<RP>& ml, float (&s)[2 * NV], int R, float* dst, int ST, int off) {
+  constexpr int RQ = RP / 2;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-  for (int r = 0; r < COOP_MAXR; ++r) {
+  for (int o = RQ; o < 32; o <<= 1)
+#pragma unroll
+    for (int m = 0; m < 2 * NV; ++m) s[m] += __shfl_xor_sync(0xffffffffu, s[m], o);
+  if (lane < RQ)
+#pragma unroll
+    for (int m = 0; m < 2 * NV; ++m) (&sh.part[w][0][0][0])[ml.rq * 2 * NV + m] = s[m];
+  __syncthreads();
+  for (int t = threadIdx.x; t < RQ * 2 * NV; t += COOP_THREADS) {
+    const int q = t / (2 * NV), m = t - q * 2 * NV, h = m / NV, f = m - h * NV, r = 2 * q + h;
     if (r < R) {
+      float x = 0.f;
 #pragma unroll
-      for (int j = 0; j < NVAL; ++j) {
-        const float y = warp_allsum(x[j][r]);
-        if (lane == 0) sh.ws[w][j * COOP_MAXR + r] = y;
-      }
+      for (int ww = 0; ww < COOP_WARPS; ++ww) x += (&sh.part[ww][0][0][0])[t];
+      dst[r * ST + off + f] = x;
     }
   }
   __syncthreads();
-  for (int tt = threadIdx.x; tt < NVAL * R; tt += COOP_THREADS) {
-    const int j = tt / R, r = tt - j * R;
-    float y = 0.f;
-#pragma unroll
-    for (int q = 0; q < COOP_WARPS; ++q) y += sh.ws[q][j * COOP_MAXR + r];
-    sh.cta[r * stride + j] = y;
-  }
 }
 
-// (X_j, y) for j < nvec over the CTA's slice into sh.cta[off + 2j], four vectors per warp pass
-DW_D void cta_mdots(CoopMShared& sh, const cplx<float>* X, size_t xstride, int nvec, const cplx<float>* y,
-                    const CoopSlice& sl, int off) {
-  __syncthreads();
+// sh.cta[r ST + off + 2v (+1)] = this CTA's share of (X_v, Y_r), v < nvec, r < R.  SHX: X_v is one
+// vector for all systems (entry i at X_v[i], vectors xs complex apart); otherwise X_v holds all
+// systems like Y (vectors xs complex apart).
+template <int RP, bool SHX>
+DW_D void mslice_dots(CoopMShared& sh, const MLane<RP>& ml, const float* X, size_t xs, int nvec, const float* Y, int R,
+                      int ST, int off) {
+  constexpr int RQ = RP / 2;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int j0 = w; j0 < nvec; j0 += 4 * COOP_WARPS) {
-    const cplx<float>* xs[4];
+  const float4* Y4 = reinterpret_cast<const float4*>(Y);
+  for (int v0 = 0; v0 < nvec; v0 += COOP_MVG) {
+    float acc[COOP_MVG][4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int jj = j0 + u * COOP_WARPS;
-      xs[u] = X + (size_t)(jj < nvec ? jj : j0) * xstride;
-    }
-    float acc[8];
+    for (int u = 0; u < COOP_MVG; ++u) acc[u][0] = acc[u][1] = acc[u][2] = acc[u][3] = 0.f;
+    // two entries per pass: the loads of both are in flight together
+    constexpr int ES = MLane<RP>::ESTEP;
+    for (int e = ml.e0; e < ml.S; e += 2 * ES) {
+      const bool two = e + ES < ml.S;
+      const size_t i0 = ml.s0 + e, i1 = two ? i0 + ES : i0;
+      const float4 ya = __ldcg(Y4 + i0 * RQ + ml.rq);
+      float4 yb = __ldcg(Y4 + i1 * RQ + ml.rq);
+      if (!two) yb = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int m = 0; m < 8; ++m) acc[m] = 0.f;
-#pragma unroll 4
-    for (size_t i = sl.s0 + lane; i < sl.s1; i += 32) {
-      const cplx<float> q = y[i];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const cplx<float> p = xs[u][i];
-        acc[2 * u] += p.re * q.re + p.im * q.im;
-        acc[2 * u + 1] += p.re * q.im - p.im * q.re;
+      for (int u = 0; u < COOP_MVG; ++u) {
+        if (v0 + u < nvec) {
+          if constexpr (SHX) {
+            const float2* Xv = reinterpret_cast<const float2*>(X) + (size_t)(v0 + u) * xs;
+            const float2 p = __ldg(Xv + i0), pb = __ldg(Xv + i1);
+            acc[u][0] = fmaf(pb.y, yb.y, fmaf(pb.x, yb.x, fmaf(p.y, ya.y, fmaf(p.x, ya.x, acc[u][0]))));
+            acc[u][1] = fmaf(-pb.y, yb.x, fmaf(pb.x, yb.y, fmaf(-p.y, ya.x, fmaf(p.x, ya.y, acc[u][1]))));
+            acc[u][2] = fmaf(pb.y, yb.w, fmaf(pb.x, yb.z, fmaf(p.y, ya.w, fmaf(p.x, ya.z, acc[u][2]))));
+            acc[u][3] = fmaf(-pb.y, yb.z, fmaf(pb.x, yb.w, fmaf(-p.y, ya.z, fmaf(p.x, ya.w, acc[u][3]))));
+          } else {
+            const float4* Xv = reinterpret_cast<const float4*>(X + 2 * (size_t)(v0 + u) * xs) + ml.rq;
+            const float4 p = __ldcg(Xv + i0 * RQ), pb = __ldcg(Xv + i1 * RQ);
+            acc[u][0] = fmaf(pb.y, yb.y, fmaf(pb.x, yb.x, fmaf(p.y, ya.y, fmaf(p.x, ya.x, acc[u][0]))));
+            acc[u][1] = fmaf(-pb.y, yb.x, fmaf(pb.x, yb.y, fmaf(-p.y, ya.x, fmaf(p.x, ya.y, acc[u][1]))));
+            acc[u][2] = fmaf(pb.w, yb.w, fmaf(pb.z, yb.z, fmaf(p.w, ya.w, fmaf(p.z, ya.z, acc[u][2]))));
+            acc[u][3] = fmaf(-pb.w, yb.z, fmaf(pb.z, yb.w, fmaf(-p.w, ya.z, fmaf(p.z, ya.w, acc[u][3]))));
+          }
+        }
       }
     }
-    int base = 0;
-    WarpHalve<float, 8, 16>::run(acc, lane, base);
-    const int u = base >> 1, jj = j0 + u * COOP_WARPS;
-    if ((lane & 3) == 0 && jj < nvec) sh.cta[off + 2 * jj + (base & 1)] = acc[0];
+#pragma unroll
+    for (int o = RQ; o < 32; o <<= 1)
+#pragma unroll
+      for (int u = 0; u < COOP_MVG; ++u)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) acc[u][m] += __shfl_xor_sync(0xffffffffu, acc[u][m], o);
+    if (lane < RQ)
+#pragma unroll
+      for (int u = 0; u < COOP_MVG; ++u)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) sh.part[w][u][ml.rq][m] = acc[u][m];
+    __syncthreads();
+    for (int t = threadIdx.x; t < COOP_MVG * RQ * 4; t += COOP_THREADS) {
+      const int u = t / (RQ * 4), q = (t >> 2) % RQ, m = t & 3, r = 2 * q + (m >> 1);
+      if (v0 + u < nvec && r < R) {
+        float x = 0.f;
+#pragma unroll
+        for (int ww = 0; ww < COOP_WARPS; ++ww) x += sh.part[ww][u][q][m];
+        sh.cta[r * ST + off + 2 * (v0 + u) + (m & 1)] = x;
+      }
+    }
+    __syncthreads();
   }
 }
 
-// out[r] = base[r] + sign * sum_d M[list[row]][d] src[r][lnb[row][d]] for all R right-hand sides on
-// this CTA's block rows: the 8 x R neighbour vectors of a row are staged in shared memory (the next
-// row's by cp.async while the current one is multiplied), warp d multiplies block d (its columns
-// held in registers) into all R vectors, the direction sums meet in shared memory.
-template <int NS>
-DW_D void coop_mhop(int nrow, int R, size_t n, const int* list, const int* lnb, const float* M, const cplx<float>* src,
-                    const cplx<float>* base, cplx<float>* out, float sign, cplx<float>* xs, cplx<float>* hp,
-                    cplx<float>* ymir = nullptr) {
+// out = base + sign * sum_d M[list[row]][d] src[lnb[row][d]] on this CTA's rows, all systems (vectors
+// with RP systems innermost); with corr the source is src - ac_r corr (ac from sh).  The operator
+// blocks of a row and its 8 neighbour blocks are copied into shared memory by cp.async one row
+// ahead (double buffers); warp d multiplies block d, lane k holding the column entries M(k, c) in
+// registers, into all systems (four independent FMA chains per system pair); the direction sums
+// meet in shared memory.
+template <int NS, int RP>
+DW_D void coop_mhop(int nrow, int R, const int* list, const int* lnb, const float* M, const float* src,
+                    const float* corr, const CoopMShared& sh, const float* base, float* out, float sign,
+                    float4* Ms, float4* xs, float4* cs, float4* hp) {
+  constexpr int RQ = RP / 2, BLK4 = NS * RQ, NST = 8 * BLK4;          // float4 of a row's neighbour data
+  constexpr int MB4 = 8 * NS * NS / 2;                                  // float4 of a row's operator blocks
+  constexpr int QG = 32 / NS;                                           // lane groups (system pairs split)
+  static_assert(NS % 2 == 0 && NS <= 32, "even Ns <= 32");
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const cplx<float>* Mc = reinterpret_cast<const cplx<float>*>(M);
-  const int Rw = (nrow + gridDim.x - 1) / gridDim.x;
-  const int rb = min(nrow, (int)blockIdx.x * Rw), re = min(nrow, rb + Rw);
-  const int nx = 8 * R * NS;                       // complex numbers staged per row
-  auto stage = [&](int row, cplx<float>* dst) {
-    for (int t = threadIdx.x; t < nx; t += COOP_THREADS) {
-      const int d = t / (R * NS), rem = t - d * R * NS, r = rem / NS, c = rem - r * NS;
-      const cplx<float>* sp = src + (size_t)r * n + (size_t)__ldg(lnb + row * 8 + d) * NS + c;
-      const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + t);
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(sp) : "memory");
+  const int kk = lane % NS, q = lane / NS;
+  const float4* S4 = reinterpret_cast<const float4*>(src);
+  const float4* C4 = reinterpret_cast<const float4*>(corr);
+  int rb, re;
+  coop_row_range(nrow, &rb, &re);
+  auto issue = [&](int row, int buf) {
+    const float4* Mg = reinterpret_cast<const float4*>(M) + (size_t)__ldg(list + row) * MB4;
+    for (int t = threadIdx.x; t < MB4; t += COOP_THREADS) cp_async16(Ms + buf * MB4 + t, Mg + t);
+    for (int t = threadIdx.x; t < NST; t += COOP_THREADS) {
+      const int d = t / BLK4, o = t - d * BLK4;
+      const size_t g4 = (size_t)__ldg(lnb + row * 8 + d) * BLK4 + o;
+      cp_async16(xs + buf * NST + t, S4 + g4);
+      if (corr) cp_async16(cs + buf * NST + t, C4 + g4);
     }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    cp_async_commit();
   };
-  // the block's column entries for this warp's direction (lane = output row), one row ahead
-  auto loadM = [&](int row, cplx<float> (&m)[NS]) {
-    const cplx<float>* Mb = Mc + ((size_t)__ldg(list + row) * 8 + w) * NS * NS;
-#pragma unroll
-    for (int c = 0; c < NS; ++c) m[c] = lane < NS ? Mb[c * NS + lane] : cplx<float>{0.f, 0.f};
-  };
-  auto compute = [&](int row, const cplx<float> (&m)[NS]) {
-    const int q = row - rb;
-    cplx<float>* xcur = xs + (size_t)(q & 1) * nx;
-    cplx<float>* hcur = hp + (size_t)(q & 1) * R * 8 * NS;
+  if (rb < re) issue(rb, 0);
+  int buf = 0;
+  for (int row = rb; row < re; ++row, buf ^= 1) {
     if (row + 1 < re) {
-      stage(row + 1, xs + (size_t)((q + 1) & 1) * nx);
-      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+      issue(row + 1, buf ^ 1);
+      cp_async_wait<1>();
     } else {
-      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      cp_async_wait<0>();
     }
+    if (corr)     // the elements this thread copied: x = src - ac corr
+      for (int t = threadIdx.x; t < NST; t += COOP_THREADS) {
+        const int r0 = 2 * (t % RQ);
+        float4 x = xs[buf * NST + t];
+        const float4 y = cs[buf * NST + t];
+        const float c0r = sh.ac[r0][0], c0i = sh.ac[r0][1], c1r = sh.ac[r0 + 1][0], c1i = sh.ac[r0 + 1][1];
+        x.x -= c0r * y.x - c0i * y.y;
+        x.y -= c0r * y.y + c0i * y.x;
+        x.z -= c1r * y.z - c1i * y.w;
+        x.w -= c1r * y.w + c1i * y.z;
+        xs[buf * NST + t] = x;
+      }
     __syncthreads();
-    if (lane < NS) {
-      for (int r = 0; r < R; ++r) {
-        const cplx<float>* x = xcur + (size_t)(w * R + r) * NS;
-        cplx<float> acc = {0.f, 0.f};
+    if (q < QG) {
+      const float2* Mw = reinterpret_cast<const float2*>(Ms + buf * MB4) + w * NS * NS + kk;
+      float2 m[NS];
 #pragma unroll
-        for (int c = 0; c < NS; ++c) acc += m[c] * x[c];
-        hcur[(r * 8 + w) * NS + lane] = acc;
+      for (int c = 0; c < NS; ++c) m[c] = Mw[c * NS];
+      const float4* xd = xs + buf * NST + w * BLK4;
+      float2* hd = reinterpret_cast<float2*>(hp) + (w * NS + kk) * RP;
+#pragma unroll
+      for (int u2 = q; u2 < RQ; u2 += QG) {
+        if (2 * u2 < R) {
+          float ar0 = 0.f, ai0 = 0.f, ar1 = 0.f, ai1 = 0.f;
+#pragma unroll
+          for (int c = 0; c < NS; ++c) {
+            const float4 x = xd[c * RQ + u2];
+            ar0 = fmaf(-m[c].y, x.y, fmaf(m[c].x, x.x, ar0));
+            ai0 = fmaf(m[c].y, x.x, fmaf(m[c].x, x.y, ai0));
+            ar1 = fmaf(-m[c].y, x.w, fmaf(m[c].x, x.z, ar1));
+            ai1 = fmaf(m[c].y, x.z, fmaf(m[c].x, x.w, ai1));
+          }
+          hd[2 * u2] = make_float2(ar0, ai0);
+          hd[2 * u2 + 1] = make_float2(ar1, ai1);
+        }
       }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < R * NS; t += COOP_THREADS) {
-      const int r = t / NS, k = t - r * NS;
-      cplx<float> sum = hcur[(r * 8) * NS + k];
+    for (int tt = threadIdx.x; tt < BLK4; tt += COOP_THREADS) {
+      const int r0 = 2 * (tt % RQ);
+      float4 s = hp[tt];
 #pragma unroll
-      for (int d = 1; d < 8; ++d) sum += hcur[(r * 8 + d) * NS + k];
-      const size_t o = (size_t)r * n + (size_t)row * NS + k;
-      const cplx<float> bse = base ? base[o] : cplx<float>{0.f, 0.f};
-      const cplx<float> val = bse + sign * sum;
-      out[o] = val;
-      if (ymir) ymir[(size_t)r * (re - rb) * NS + (size_t)(row - rb) * NS + k] = val;
-    }
-  };
-  if (rb < re) {
-    stage(rb, xs);
-    cplx<float> mA[NS], mB[NS];
-    loadM(rb, mA);
-    for (int row = rb; row < re; row += 2) {
-      if (row + 1 < re) loadM(row + 1, mB);
-      compute(row, mA);
-      if (row + 1 < re) {
-        if (row + 2 < re) loadM(row + 2, mA);
-        compute(row + 1, mB);
+      for (int d = 1; d < 8; ++d) {
+        const float4 h = hp[d * BLK4 + tt];
+        s.x += h.x; s.y += h.y; s.z += h.z; s.w += h.w;
       }
+      const size_t o = (size_t)row * BLK4 + tt;
+      float4 val = base ? __ldcg(reinterpret_cast<const float4*>(base) + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+      val.x = fmaf(sign, s.x, val.x); val.y = fmaf(sign, s.y, val.y);
+      val.z = fmaf(sign, s.z, val.z); val.w = fmaf(sign, s.w, val.w);
+      if (r0 >= R) val.x = val.y = 0.f;                   // padding systems stay zero
+      if (r0 + 1 >= R) val.z = val.w = 0.f;
+      reinterpret_cast<float4*>(out)[o] = val;
     }
   }
   __syncthreads();
 }
 
-template <int NS>
+template <int NS, int RP>
 __global__ void __launch_bounds__(COOP_THREADS, 1) little_gcr_coop_mrhs_kernel(CoopMArgs a) {
   cg::grid_group grid = cg::this_grid();
   __shared__ CoopMShared sh;
   extern __shared__ __align__(16) unsigned char coop_mdyn[];
+  constexpr int RQ = RP / 2;
   const int R = a.R, nkv = a.nkv;
-  float* bbm = reinterpret_cast<float*>(coop_mdyn);                           // [R][nkv][2 nkv]
-  float* tgm = bbm + (size_t)COOP_MAXR * COOP_NKV * 2 * COOP_NKV;               // [R][nkv][2 NS]
-  cplx<float>* xs = reinterpret_cast<cplx<float>*>(tgm + (size_t)COOP_MAXR * COOP_NKV * 2 * NS);
-  cplx<float>* hp = xs + (size_t)2 * 8 * COOP_MAXR * NS;
-  cplx<float>* ysm = hp + (size_t)2 * COOP_MAXR * 8 * NS;                     // [R][S] mirror of chi_k
-  auto BB = [&](int r, int j, int k) -> float* { return bbm + ((size_t)(r * COOP_NKV + j) * COOP_NKV + k) * 2; };
-  auto TG = [&](int r, int j, int l) -> float* { return tgm + ((size_t)(r * COOP_NKV + j) * NS + l) * 2; };
-  const size_t n = (size_t)a.Ne * NS;
-  const CoopSlice sl = coop_rows_slice(a.Ne, NS);
-  const size_t S = sl.s1 - sl.s0;
-  cplx<float>* ys = (size_t)a.R * S <= COOP_YS_CAP ? ysm : nullptr;             // mirror if it fits
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float4* Ms = reinterpret_cast<float4*>(coop_mdyn);                  // [2][8 NS NS / 2]
+  float4* xs = Ms + 2 * 8 * NS * NS / 2;                              // [2][8 NS RQ]
+  float4* cs = xs + 2 * 8 * NS * RQ;                                  // [2][8 NS RQ]
+  float4* hp = cs + 2 * 8 * NS * RQ;                                  // [8][NS RQ]
+  cplx<float>* tg = reinterpret_cast<cplx<float>*>(a.scratch + blockIdx.x * coop_m_cta_scratch(NS));
+  cplx<float>* bbm = tg + (size_t)COOP_MAXR * COOP_NKV * NS;         // [R][nkv][nkv]
+  auto TG = [&](int r, int j, int l) -> cplx<float>& { return tg[((size_t)r * COOP_NKV + j) * NS + l]; };
+  auto BB = [&](int r, int j, int k) -> cplx<float>& { return bbm[((size_t)r * COOP_NKV + j) * COOP_NKV + k]; };
+  const size_t n = (size_t)a.Ne * NS;                                // entries of an even vector
+  const size_t vlen = (size_t)max(a.Ne, a.No) * NS * RP;             // complex numbers per work vector
+  const MLane<RP> ml(a.Ne, NS);
   const int na = a.a3 ? 2 * NS : 0;
-  if (a.a3)
-    for (int t = threadIdx.x; t < NS * NS; t += COOP_THREADS) {
-      sh.ainv[2 * t] = a.Ainv[2 * t];
-      sh.ainv[2 * t + 1] = a.Ainv[2 * t + 1];
-    }
-  if (threadIdx.x < R) { sh.its[threadIdx.x] = 0; sh.kr[threadIdx.x] = 0; }
-  __syncthreads();
-  cplx<float>* W = reinterpret_cast<cplx<float>*>(a.work);
-  const size_t vs = (size_t)R * n;                                   // one vector kind for all RHS
-  cplx<float>* rho = W + (size_t)2 * nkv * vs;
-  cplx<float>* tmpo = rho + vs;
-  cplx<float>* t = tmpo + vs;
-  cplx<float>* rhsd = t + vs;
-  const cplx<float>* b = reinterpret_cast<const cplx<float>*>(a.b);
-  const cplx<float>* g = reinterpret_cast<const cplx<float>*>(a.g);
-  const cplx<float>* Bg = reinterpret_cast<const cplx<float>*>(a.Bg);
-  cplx<float>* v = reinterpret_cast<cplx<float>*>(a.v);
-  auto chi = [&](int k) { return W + (size_t)k * vs; };
-  auto xi = [&](int k) { return W + (size_t)(nkv + k) * vs; };
-  auto slice = [&](auto&& f) {
-#pragma unroll
-    for (int r = 0; r < COOP_MAXR; ++r)
-      if (r < R)
-        for (size_t i = sl.s0 + threadIdx.x; i < sl.s1; i += COOP_THREADS) f(r, (size_t)r * n + i);
+  auto V = [&](int qv) { return a.work + 2 * (size_t)qv * vlen; };
+  auto V4 = [&](float* p) { return reinterpret_cast<float4*>(p); };
+  // work vectors: chi'_j (j < nkv, unnormalised, norms c_j), xi_j, rho (two buffers), tmpo, t, rhsd, v
+  float* rhob[2] = {V(2 * nkv), V(2 * nkv + 1)};
+  float* tmpo = V(2 * nkv + 2);
+  float* t = V(2 * nkv + 3);
+  float* rhsd = V(2 * nkv + 4);
+  float* vv = V(2 * nkv + 5);
+  const float2* g2 = reinterpret_cast<const float2*>(a.g);
+  const float2* Bg2 = reinterpret_cast<const float2*>(a.Bg);
+  const float2* b2 = reinterpret_cast<const float2*>(a.b);
+  auto slice4 = [&](auto&& f) {
+    for (int e = ml.e0; e < ml.S; e += MLane<RP>::ESTEP) f(((size_t)ml.s0 + e) * RQ + ml.rq, (size_t)ml.s0 + e);
   };
-  // z_r = A~^{-1} u_r with u_r at sh.res[off_r(r)..] (threads r * NS + l)
-  auto zsolve = [&](int stride, int off) {
-    for (int tt = threadIdx.x; tt < R * NS; tt += COOP_THREADS) {
+  auto update_any = [&]() {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int x = 0;
+      for (int r = 0; r < R; ++r) x |= sh.live[r];
+      sh.any = x;
+    }
+    __syncthreads();
+    return sh.any != 0;
+  };
+  // z_r = A~^{-1} u_r, u_r at sh.res[r ST + off ..]; only_live: zero for frozen systems
+  auto mzsolve = [&](int ST, int off, bool only_live) {
+    for (int tt = threadIdx.x; tt < COOP_MRP * NS; tt += COOP_THREADS) {
       const int r = tt / NS, l = tt - r * NS;
       float zr = 0.f, zi = 0.f;
-      for (int qq = 0; qq < NS; ++qq) {
-        const float mr = sh.ainv[2 * (l * NS + qq)], mi = sh.ainv[2 * (l * NS + qq) + 1];
-        const float yr = sh.res[r * stride + off + 2 * qq], yi = sh.res[r * stride + off + 2 * qq + 1];
-        zr += mr * yr - mi * yi;
-        zi += mr * yi + mi * yr;
+      if (r < R && (!only_live || sh.live[r])) {
+        for (int qq = 0; qq < NS; ++qq) {
+          const float mr = sh.ainv[2 * (l * NS + qq)], mi = sh.ainv[2 * (l * NS + qq) + 1];
+          const float yr = sh.res[r * ST + off + 2 * qq], yi = sh.res[r * ST + off + 2 * qq + 1];
+          zr += mr * yr - mi * yi;
+          zi += mr * yi + mi * yr;
+        }
       }
-      sh.z[r][2 * l] = zr;
-      sh.z[r][2 * l + 1] = zi;
+      sh.z[l][r][0] = zr;
+      sh.z[l][r][1] = zi;
     }
+    __syncthreads();
   };
-  // u <- u - sg * sum_l z_l vecs_l on the slice, for all r (vecs shared by the RHS)
-  auto zupdate = [&](cplx<float>* u, const cplx<float>* vecs, float sg) {
-    slice([&](int r, size_t i) {
-      const size_t il = i - (size_t)r * n;
-      cplx<float> x = u[i];
+  // upd -= sg sum_l z_l vecs_l with z = A~^{-1} g^+ dot, for every system (A.3)
+  auto mproject = [&](const float* dot, float* upd, const float2* vecs, float sg) {
+    mslice_dots<RP, true>(sh, ml, a.g, n, NS, dot, R, 2 * NS, 0);
+    coop_mreduce(grid, sh, R * 2 * NS, a.acc);
+    mzsolve(2 * NS, 0, false);
+    slice4([&](size_t q4, size_t i) {
+      float4 x = __ldcg(V4(upd) + q4);
 #pragma unroll
-      for (int l = 0; l < NS; ++l) x -= sg * (cplx<float>{sh.z[r][2 * l], sh.z[r][2 * l + 1]} * vecs[(size_t)l * n + il]);
-      u[i] = x;
+      for (int l = 0; l < NS; ++l) {
+        const float2 gv = __ldg(vecs + (size_t)l * n + i);
+        const float4 zz = *reinterpret_cast<const float4*>(&sh.z[l][2 * ml.rq][0]);
+        x.x -= sg * (zz.x * gv.x - zz.y * gv.y);
+        x.y -= sg * (zz.x * gv.y + zz.y * gv.x);
+        x.z -= sg * (zz.z * gv.x - zz.w * gv.y);
+        x.w -= sg * (zz.z * gv.y + zz.w * gv.x);
+      }
+      V4(upd)[q4] = x;
     });
   };
-  // P~_L on all RHS of u (in place)
-  auto PL = [&](cplx<float>* u) {
-    for (int r = 0; r < R; ++r) cta_mdots(sh, g, n, NS, u + (size_t)r * n, sl, r * 2 * NS);
-    coop_mreduce(grid, sh, R * 2 * NS, a.partial, a.red);
-    zsolve(2 * NS, 0);
-    __syncthreads();
-    zupdate(u, Bg, 1.f);
+  // the sums of s2 (|.|^2 of the two systems of a thread) into sh.cta[r] and sh.rr[r]
+  auto norm_share = [&](float (&s2)[2]) {
+    mslice_sum<RP, 1>(sh, ml, s2, R, sh.cta, 1, 0);
+    if (threadIdx.x < R) sh.rr[threadIdx.x] = sh.cta[threadIdx.x];
   };
-  float acc[3][COOP_MAXR];
-  auto zero = [&]() {
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-#pragma unroll
-      for (int r = 0; r < COOP_MAXR; ++r) acc[j][r] = 0.f;
-  };
-  float (&acc1)[1][COOP_MAXR] = reinterpret_cast<float (&)[1][COOP_MAXR]>(acc);
 
-  // rhsd = P~_L b, rho = rhsd, v = 0, bn
-  slice([&](int r, size_t i) { rhsd[i] = b[i]; });
-  if (a.a3) PL(rhsd);
-  zero();
-  slice([&](int r, size_t i) {
-    const cplx<float> x = rhsd[i];
-    rho[i] = x;
-    v[i] = {0.f, 0.f};
-    acc[0][r] += x.re * x.re + x.im * x.im;
+  if (a.a3)
+    for (int tt = threadIdx.x; tt < NS * NS; tt += COOP_THREADS) {
+      sh.ainv[2 * tt] = a.Ainv[2 * tt];
+      sh.ainv[2 * tt + 1] = a.Ainv[2 * tt + 1];
+    }
+  for (int tt = threadIdx.x; tt < 32 * COOP_MRP * 2; tt += COOP_THREADS) (&sh.z[0][0][0])[tt] = 0.f;
+  for (int tt = threadIdx.x; tt < COOP_NKV * COOP_MRP * 2; tt += COOP_THREADS) (&sh.bbn[0][0][0])[tt] = 0.f;
+  if (threadIdx.x < COOP_MRP) {
+    sh.ac[threadIdx.x][0] = sh.ac[threadIdx.x][1] = 0.f;
+    sh.cf[threadIdx.x][0] = sh.cf[threadIdx.x][1] = 0.f;
+    sh.rr[threadIdx.x] = 0.f;
+  }
+  if (threadIdx.x < COOP_MAXR) {
+    sh.its[threadIdx.x] = 0;
+    sh.kr[threadIdx.x] = 0;
+    sh.live[threadIdx.x] = 0;
+  }
+  if (threadIdx.x == 0) sh.phase = 0;
+  __syncthreads();
+
+  // rhsd = P~_L b (systems innermost, padding zero), rho_0 = rhsd, v = 0
+  slice4([&](size_t q4, size_t i) {
+    const int r0 = 2 * ml.rq;
+    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r0 < R) { const float2 y = b2[(size_t)r0 * n + i]; x.x = y.x; x.y = y.y; }
+    if (r0 + 1 < R) { const float2 y = b2[(size_t)(r0 + 1) * n + i]; x.z = y.x; x.w = y.y; }
+    V4(rhsd)[q4] = x;
+    V4(vv)[q4] = make_float4(0.f, 0.f, 0.f, 0.f);
   });
-  cta_msum<1>(sh, acc1, R, 1);
-  coop_mreduce(grid, sh, R, a.partial, a.red);
+  if (a.a3) mproject(rhsd, rhsd, Bg2, 1.f);
+  {
+    float s2[2] = {0.f, 0.f};
+    slice4([&](size_t q4, size_t) {
+      const float4 x = __ldcg(V4(rhsd) + q4);
+      V4(rhob[0])[q4] = x;
+      s2[0] += x.x * x.x + x.y * x.y;
+      s2[1] += x.z * x.z + x.w * x.w;
+    });
+    norm_share(s2);
+  }
+  coop_mreduce(grid, sh, R, a.acc);
   if (threadIdx.x < R) {
     const int r = threadIdx.x;
     sh.bn[r] = sqrtf(sh.res[r]);
     sh.rn[r] = sh.bn[r];
     sh.live[r] = sh.bn[r] > 0.f && a.maxit > 0;
   }
-  __syncthreads();
-  auto any_live = [&]() {
-    int x = 0;
-    for (int r = 0; r < R; ++r) x |= sh.live[r];
-    return x;
-  };
-  while (any_live()) {
+  int cur = 0;                                            // rhob[cur] holds rho_k on this CTA's rows
+  while (update_any()) {
     if (threadIdx.x < R) sh.kr[threadIdx.x] = 0;
     __syncthreads();
-    for (int k = 0; k < nkv && any_live(); ++k) {
-      cplx<float>* ck = chi(k);
-      cplx<float>* xk = xi(k);
-      slice([&](int r, size_t i) { xk[i] = rho[i]; });
-      coop_mhop<NS>(a.No, R, n, a.list_o, a.lnb_o, a.M, rho, nullptr, tmpo, 1.f, xs, hp);
+    for (int k = 0; k < nkv; ++k) {
+      float* ck = V(k);
+      float* rk = rhob[cur];
+      // xi_k = rho_k; chi_k = B^ rho_k (the odd hop reads rho_k of other CTAs as rho_{k-1} - ac chi'_{k-1})
+      slice4([&](size_t q4, size_t) { V4(V(nkv + k))[q4] = __ldcg(V4(rk) + q4); });
+      coop_mhop<NS, RP>(a.No, R, a.list_o, a.lnb_o, a.M, k > 0 ? rhob[cur ^ 1] : rk, k > 0 ? V(k - 1) : nullptr, sh,
+                    nullptr, tmpo, 1.f, Ms, xs, cs, hp);
       grid.sync();
-      coop_mhop<NS>(a.Ne, R, n, a.list_e, a.lnb_e, a.M, tmpo, rho, ck, -1.f, xs, hp, ys);
-      // one reduction per step for u = g^+ chi_k and (chi_j, chi_k), j < k (per RHS block of na + 2k)
-      const int st = na + 2 * k;
-      for (int r = 0; r < R; ++r) {
-        if (a.a3) cta_mdots(sh, g, n, NS, ck + (size_t)r * n, sl, r * st);
-        if (k > 0) cta_mdots(sh, W + (size_t)r * n, vs, k, ck + (size_t)r * n, sl, r * st + na);
-      }
-      if (st > 0) coop_mreduce(grid, sh, R * st, a.partial, a.red);
-      if (a.a3) zsolve(st, 0);
       __syncthreads();
-      for (int tt = threadIdx.x; tt < R * k; tt += COOP_THREADS) {
-        const int r = tt / k, j = tt - r * k;
-        float br = sh.res[r * st + na + 2 * j], bi = sh.res[r * st + na + 2 * j + 1];
-        if (a.a3)
-          for (int l = 0; l < NS; ++l) {
-            const float zr = sh.z[r][2 * l], zi = sh.z[r][2 * l + 1], tr = TG(r, j, l)[0], ti = TG(r, j, l)[1];
-            br -= zr * tr - zi * ti;
-            bi -= zr * ti + zi * tr;
-          }
-        BB(r, j, k)[0] = br;
-        BB(r, j, k)[1] = bi;
-      }
-      __syncthreads();
-      zero();
-      // chi_k <- P~_L chi_k - sum_j b_jk chi_j per RHS; the B^g entries of a site are loaded once
-      for (size_t i = sl.s0 + threadIdx.x; i < sl.s1; i += COOP_THREADS) {
-        const size_t ii = i - sl.s0;
-        cplx<float> bgv[NS];
-        if (a.a3) {
-#pragma unroll
-          for (int l = 0; l < NS; ++l) bgv[l] = Bg[(size_t)l * n + i];
-        }
-#pragma unroll
-        for (int r = 0; r < COOP_MAXR; ++r) {
-          if (r < R) {
-            const size_t ir = (size_t)r * n + i;
-            cplx<float> y = ys ? ys[(size_t)r * S + ii] : ck[ir];
-            if (a.a3) {
-#pragma unroll
-              for (int l = 0; l < NS; ++l) y -= cplx<float>{sh.z[r][2 * l], sh.z[r][2 * l + 1]} * bgv[l];
-            }
-#pragma unroll
-            for (int j = 0; j < COOP_NKV; ++j)
-              if (j < k) y -= cplx<float>{BB(r, j, k)[0], BB(r, j, k)[1]} * chi(j)[ir];
-            ck[ir] = y;
-            if (ys) ys[(size_t)r * S + ii] = y;
-            const cplx<float> q = rho[ir];
-            acc[0][r] += y.re * q.re + y.im * q.im;
-            acc[1][r] += y.re * q.im - y.im * q.re;
-            acc[2][r] += y.re * y.re + y.im * y.im;
-          }
-        }
-      }
-      // reduction: per RHS (chi_k, rho), |chi_k|^2 and (B^ g_l, chi_k)
-      const int sb = 3 + na;
-      cta_msum<3>(sh, acc, R, sb);
-      if (a.a3)
-        for (int r = 0; r < R; ++r) cta_mdots(sh, Bg, n, NS, ck + (size_t)r * n, sl, r * sb + 3);
-      coop_mreduce(grid, sh, R * sb, a.partial, a.red);
-      // per RHS: normalise chi_k, update rho (live RHS only)
-      for (int r = 0; r < R; ++r) {
-        const float cn = sqrtf(sh.res[r * sb + 2]);
-        const bool ok = sh.live[r] && cn > 0.f;
-        const float inv = ok ? 1.f / cn : 0.f;
-        if (threadIdx.x == 0) {
-          sh.c[r][k] = ok ? cn : 1.f;
-          sh.a[r][2 * k] = ok ? sh.res[r * sb] * inv : 0.f;
-          sh.a[r][2 * k + 1] = ok ? sh.res[r * sb + 1] * inv : 0.f;
-        }
-        if (a.a3 && threadIdx.x < NS) {
-          TG(r, k, threadIdx.x)[0] = sh.res[r * sb + 3 + 2 * threadIdx.x] * inv;
-          TG(r, k, threadIdx.x)[1] = -sh.res[r * sb + 3 + 2 * threadIdx.x + 1] * inv;
-        }
-      }
-      __syncthreads();
-      zero();
-      slice([&](int r, size_t i) {
-        if (sh.live[r]) {
-          const float inv = 1.f / sh.c[r][k];
-          const cplx<float> x = inv * ck[i];
-          ck[i] = x;
-          const cplx<float> y = rho[i] - cplx<float>{sh.a[r][2 * k], sh.a[r][2 * k + 1]} * x;
-          rho[i] = y;
-          acc[0][r] += y.re * y.re + y.im * y.im;
-        }
-      });
-      cta_msum<1>(sh, acc1, R, 1);
-      coop_mreduce(grid, sh, R, a.partial, a.red);
+      coop_mhop<NS, RP>(a.Ne, R, a.list_e, a.lnb_e, a.M, tmpo, nullptr, sh, rk, ck, -1.f, Ms, xs, cs, hp);
+      // one reduction: u = g^+ chi_k (A.3), (chi'_j, chi_k) for j < k, |rho_k|^2
+      const int ST1 = na + 2 * k + 1;
+      if (a.a3) mslice_dots<RP, true>(sh, ml, a.g, n, NS, ck, R, ST1, 0);
+      if (k > 0) mslice_dots<RP, false>(sh, ml, a.work, vlen, k, ck, R, ST1, na);
+      if (threadIdx.x < R) sh.cta[threadIdx.x * ST1 + na + 2 * k] = sh.rr[threadIdx.x];
+      coop_mreduce(grid, sh, R * ST1, a.acc);
       if (threadIdx.x < R) {
         const int r = threadIdx.x;
-        if (sh.live[r]) {
-          sh.rn[r] = sqrtf(sh.res[r]);
-          sh.its[r] += 1;
-          sh.kr[r] = k + 1;
-          if (!(sh.c[r][k] > 0.f) || sh.a[r][2 * k] != sh.a[r][2 * k] ||
-              (double)sh.rn[r] <= (double)a.tol[r] * (double)sh.bn[r] || sh.its[r] >= a.maxit)
-            sh.live[r] = 0;
+        sh.rn2[r] = sh.res[r * ST1 + na + 2 * k];
+        sh.rn[r] = sqrtf(sh.rn2[r]);
+        if (sh.live[r] && (double)sh.rn[r] <= (double)a.tol[r] * (double)sh.bn[r]) sh.live[r] = 0;
+      }
+      if (!update_any()) break;                           // every rho_k converged: chi_k unused
+      if (a.a3) mzsolve(ST1, 0, true);
+      // coefficients of P~_L chi_k on the normalised chi_j: (chi'_j, chi_k) / c_j - sum_l z_l (chi_j, B^ g_l)
+      for (int tt = threadIdx.x; tt < COOP_MRP * k; tt += COOP_THREADS) {
+        const int r = tt / k, j = tt - r * k;
+        float br = 0.f, bi = 0.f, ic = 0.f;
+        if (r < R && sh.live[r]) {
+          ic = 1.f / sh.c[r][j];
+          br = sh.res[r * ST1 + na + 2 * j] * ic;
+          bi = sh.res[r * ST1 + na + 2 * j + 1] * ic;
+          if (a.a3)
+            for (int l = 0; l < NS; ++l) {
+              const float zr = sh.z[l][r][0], zi = sh.z[l][r][1];
+              const cplx<float> tv = TG(r, j, l);
+              br -= zr * tv.re - zi * tv.im;
+              bi -= zr * tv.im + zi * tv.re;
+            }
+          BB(r, j, k) = cplx<float>{br, bi};
         }
+        sh.bbn[j][r][0] = br * ic;
+        sh.bbn[j][r][1] = bi * ic;
       }
       __syncthreads();
+      // chi'_k = P~_L chi_k - sum_j b_jk chi'_j / c_j in place; (chi'_k, rho_k), |chi'_k|^2
+      {
+        float s6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        slice4([&](size_t q4, size_t i) {
+          float4 y = __ldcg(V4(ck) + q4), y2 = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (a.a3) {
+#pragma unroll
+            for (int l = 0; l < NS; ++l) {
+              const float2 bg = __ldg(Bg2 + (size_t)l * n + i);
+              const float4 zz = *reinterpret_cast<const float4*>(&sh.z[l][2 * ml.rq][0]);
+              float4& u = (l & 1) ? y2 : y;
+              u.x -= zz.x * bg.x - zz.y * bg.y;
+              u.y -= zz.x * bg.y + zz.y * bg.x;
+              u.z -= zz.z * bg.x - zz.w * bg.y;
+              u.w -= zz.z * bg.y + zz.w * bg.x;
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < COOP_NKV; ++j) {
+            if (j < k) {
+              const float4 x = __ldcg(V4(V(j)) + q4);
+              const float4 bb = *reinterpret_cast<const float4*>(&sh.bbn[j][2 * ml.rq][0]);
+              float4& u = (j & 1) ? y2 : y;
+              u.x -= bb.x * x.x - bb.y * x.y;
+              u.y -= bb.x * x.y + bb.y * x.x;
+              u.z -= bb.z * x.z - bb.w * x.w;
+              u.w -= bb.z * x.w + bb.w * x.z;
+            }
+          }
+          y.x += y2.x; y.y += y2.y; y.z += y2.z; y.w += y2.w;
+          V4(ck)[q4] = y;
+          const float4 r = __ldcg(V4(rk) + q4);
+          s6[0] += y.x * r.x + y.y * r.y;
+          s6[1] += y.x * r.y - y.y * r.x;
+          s6[2] += y.x * y.x + y.y * y.y;
+          s6[3] += y.z * r.z + y.w * r.w;
+          s6[4] += y.z * r.w - y.w * r.z;
+          s6[5] += y.z * y.z + y.w * y.w;
+        });
+        const int ST2 = 3 + na;
+        mslice_sum<RP, 3>(sh, ml, s6, R, sh.cta, ST2, 0);
+        if (a.a3) mslice_dots<RP, true>(sh, ml, a.Bg, n, NS, ck, R, ST2, 3);
+        coop_mreduce(grid, sh, R * ST2, a.acc);
+        // per system: c_k = |chi'_k|, a_k = (chi_k, rho_k), the rho update coefficient a_k / c_k
+        if (threadIdx.x < COOP_MRP) {
+          const int r = threadIdx.x;
+          float ar = 0.f, ai = 0.f, inv = 0.f;
+          if (r < R && sh.live[r]) {
+            const float cn = sqrtf(sh.res[r * ST2 + 2]);
+            inv = cn > 0.f ? 1.f / cn : 0.f;
+            ar = sh.res[r * ST2] * inv;
+            ai = sh.res[r * ST2 + 1] * inv;
+            if (cn > 0.f && ar == ar && ai == ai) {
+              sh.c[r][k] = cn;
+              sh.a[r][2 * k] = ar;
+              sh.a[r][2 * k + 1] = ai;
+            } else {                                      // breakdown: the cycle of r ends with k steps
+              sh.live[r] = 0;
+              ar = ai = inv = 0.f;
+            }
+          }
+          sh.cf[r][0] = ar * inv;
+          sh.cf[r][1] = ai * inv;
+        }
+        __syncthreads();
+        if (a.a3)       // (chi_k, B^ g_l) = conj((B^ g_l, chi'_k)) / c_k
+          for (int tt = threadIdx.x; tt < R * NS; tt += COOP_THREADS) {
+            const int r = tt / NS, l = tt - r * NS;
+            if (sh.live[r]) {
+              const float inv = 1.f / sh.c[r][k];
+              TG(r, k, l) = cplx<float>{sh.res[r * ST2 + 3 + 2 * l] * inv, -sh.res[r * ST2 + 3 + 2 * l + 1] * inv};
+            }
+          }
+      }
+      // rho_{k+1} = rho_k - (a_k / c_k) chi'_k on this CTA's rows, into the other buffer
+      {
+        float s2[2] = {0.f, 0.f};
+        float* rn1 = rhob[cur ^ 1];
+        slice4([&](size_t q4, size_t) {
+          const float4 cf = *reinterpret_cast<const float4*>(&sh.cf[2 * ml.rq][0]);
+          const float4 x = __ldcg(V4(ck) + q4), r = __ldcg(V4(rk) + q4);
+          float4 y;
+          y.x = r.x - (cf.x * x.x - cf.y * x.y);
+          y.y = r.y - (cf.x * x.y + cf.y * x.x);
+          y.z = r.z - (cf.z * x.z - cf.w * x.w);
+          y.w = r.w - (cf.z * x.w + cf.w * x.z);
+          V4(rn1)[q4] = y;
+          s2[0] += y.x * y.x + y.y * y.y;
+          s2[1] += y.z * y.z + y.w * y.w;
+        });
+        mslice_sum<RP, 1>(sh, ml, s2, R, sh.rr, 1, 0);
+      }
+      if (threadIdx.x < COOP_MRP) {
+        const int r = threadIdx.x;
+        sh.ac[r][0] = sh.cf[r][0];
+        sh.ac[r][1] = sh.cf[r][1];
+        if (r < R && sh.live[r]) {
+          sh.its[r] += 1;
+          sh.kr[r] = k + 1;
+          // |rho_{k+1}|^2 = |rho_k|^2 - |a_k|^2: stop stepping this system once it is below the tolerance
+          const float ar = sh.a[r][2 * k], ai = sh.a[r][2 * k + 1];
+          const float est = sh.rn2[r] - (ar * ar + ai * ai);
+          const float rne = est > 0.f ? sqrtf(est) : 0.f;
+          if ((double)rne <= (double)a.tol[r] * (double)sh.bn[r] || sh.its[r] >= a.maxit) sh.live[r] = 0;
+        }
+      }
+      cur ^= 1;
+      if (!update_any()) break;
     }
-    // back substitution per RHS (warp r), v_r += sum_j beta_j xi_j
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // back substitution per system (warp r), then v += sum_j beta_j xi_j
+    __syncthreads();
     for (int r = w; r < R; r += COOP_WARPS) {
       const int kk = sh.kr[r];
       float br = lane < kk ? sh.a[r][2 * lane] : 0.f, bi = lane < kk ? sh.a[r][2 * lane + 1] : 0.f;
       for (int j = kk - 1; j >= 0; --j) {
         const float cj = sh.c[r][j];
         const float yr = __shfl_sync(0xffffffffu, br, j) / cj, yi = __shfl_sync(0xffffffffu, bi, j) / cj;
-        if (lane == j) { sh.beta[r][2 * j] = yr; sh.beta[r][2 * j + 1] = yi; }
+        if (lane == j) {
+          sh.beta[r][2 * j] = yr;
+          sh.beta[r][2 * j + 1] = yi;
+        }
         if (lane < j) {
-          const float mr = BB(r, lane, j)[0], mi = BB(r, lane, j)[1];
-          br -= mr * yr - mi * yi;
-          bi -= mr * yi + mi * yr;
+          const cplx<float> mv = BB(r, lane, j);
+          br -= mv.re * yr - mv.im * yi;
+          bi -= mv.re * yi + mv.im * yr;
         }
       }
     }
     __syncthreads();
-    slice([&](int r, size_t i) {
-      cplx<float> x = v[i];
-      const int kk = sh.kr[r];
+    int kmax = 0;
+    for (int r = 0; r < R; ++r) kmax = max(kmax, sh.kr[r]);
+    for (int tt = threadIdx.x; tt < COOP_NKV * COOP_MRP; tt += COOP_THREADS) {
+      const int j = tt / COOP_MRP, r = tt - j * COOP_MRP;
+      const bool u = r < R && j < sh.kr[r];
+      sh.bbn[j][r][0] = u ? sh.beta[r][2 * j] : 0.f;
+      sh.bbn[j][r][1] = u ? sh.beta[r][2 * j + 1] : 0.f;
+    }
+    __syncthreads();
+    slice4([&](size_t q4, size_t) {
+      float4 x = __ldcg(V4(vv) + q4);
 #pragma unroll
-      for (int j = 0; j < COOP_NKV; ++j)
-        if (j < kk) x += cplx<float>{sh.beta[r][2 * j], sh.beta[r][2 * j + 1]} * xi(j)[i];
-      v[i] = x;
+      for (int j = 0; j < COOP_NKV; ++j) {
+        if (j < kmax) {
+          const float4 xx = __ldcg(V4(V(nkv + j)) + q4);
+          const float4 bb = *reinterpret_cast<const float4*>(&sh.bbn[j][2 * ml.rq][0]);
+          x.x += bb.x * xx.x - bb.y * xx.y;
+          x.y += bb.x * xx.y + bb.y * xx.x;
+          x.z += bb.z * xx.z - bb.w * xx.w;
+          x.w += bb.z * xx.w + bb.w * xx.z;
+        }
+      }
+      V4(vv)[q4] = x;
     });
+    __syncthreads();
     grid.sync();
-    // true residuals of the deflated systems; RHS still live after their last step continue
-    int again = 0;
-    for (int r = 0; r < R; ++r) again |= sh.live[r];
-    if (!again) break;
-    coop_mhop<NS>(a.No, R, n, a.list_o, a.lnb_o, a.M, v, nullptr, tmpo, 1.f, xs, hp);
+    if (kmax == 0) break;                                 // nothing changed since the last true residual
+    // true residuals of the deflated systems: rho = P~_L (rhsd - B^ v)
+    coop_mhop<NS, RP>(a.No, R, a.list_o, a.lnb_o, a.M, vv, nullptr, sh, nullptr, tmpo, 1.f, Ms, xs, cs, hp);
     grid.sync();
-    coop_mhop<NS>(a.Ne, R, n, a.list_e, a.lnb_e, a.M, tmpo, v, t, -1.f, xs, hp);
-    grid.sync();
-    if (a.a3) PL(t);
-    zero();
-    slice([&](int r, size_t i) {
-      const cplx<float> y = rhsd[i] - t[i];
-      rho[i] = y;
-      acc[0][r] += y.re * y.re + y.im * y.im;
-    });
-    cta_msum<1>(sh, acc1, R, 1);
-    coop_mreduce(grid, sh, R, a.partial, a.red);
+    __syncthreads();
+    coop_mhop<NS, RP>(a.Ne, R, a.list_e, a.lnb_e, a.M, tmpo, nullptr, sh, vv, t, -1.f, Ms, xs, cs, hp);
+    if (a.a3) mproject(t, t, Bg2, 1.f);
+    {
+      float s2[2] = {0.f, 0.f};
+      float* r0p = rhob[cur];
+      slice4([&](size_t q4, size_t) {
+        const float4 x = __ldcg(V4(rhsd) + q4), tt4 = __ldcg(V4(t) + q4);
+        const float4 y = make_float4(x.x - tt4.x, x.y - tt4.y, x.z - tt4.z, x.w - tt4.w);
+        V4(r0p)[q4] = y;
+        s2[0] += y.x * y.x + y.y * y.y;
+        s2[1] += y.z * y.z + y.w * y.w;
+      });
+      norm_share(s2);
+    }
+    coop_mreduce(grid, sh, R, a.acc);
     if (threadIdx.x < R) {
       const int r = threadIdx.x;
       sh.rn[r] = sqrtf(sh.res[r]);
-      if (sh.live[r] && (double)sh.rn[r] <= (double)a.tol[r] * (double)sh.bn[r]) sh.live[r] = 0;
+      sh.live[r] = sh.bn[r] > 0.f && (double)sh.rn[r] > (double)a.tol[r] * (double)sh.bn[r] && sh.its[r] < a.maxit;
     }
-    __syncthreads();
+    if (threadIdx.x < COOP_MRP) sh.ac[threadIdx.x][0] = sh.ac[threadIdx.x][1] = 0.f;
   }
   if (a.a3) {
-    // v = chi + g A~^{-1} g^+ (b - B^ chi) for every RHS
+    // v = chi + g A~^{-1} g^+ (b - B^ chi) for every system
     grid.sync();
-    coop_mhop<NS>(a.No, R, n, a.list_o, a.lnb_o, a.M, v, nullptr, tmpo, 1.f, xs, hp);
-    grid.sync();
-    coop_mhop<NS>(a.Ne, R, n, a.list_e, a.lnb_e, a.M, tmpo, v, t, -1.f, xs, hp);
-    grid.sync();
-    slice([&](int r, size_t i) { t[i] = b[i] - t[i]; });
-    for (int r = 0; r < R; ++r) cta_mdots(sh, g, n, NS, t + (size_t)r * n, sl, r * 2 * NS);
-    coop_mreduce(grid, sh, R * 2 * NS, a.partial, a.red);
-    zsolve(2 * NS, 0);
     __syncthreads();
-    zupdate(v, g, -1.f);
+    coop_mhop<NS, RP>(a.No, R, a.list_o, a.lnb_o, a.M, vv, nullptr, sh, nullptr, tmpo, 1.f, Ms, xs, cs, hp);
+    grid.sync();
+    __syncthreads();
+    coop_mhop<NS, RP>(a.Ne, R, a.list_e, a.lnb_e, a.M, tmpo, nullptr, sh, vv, t, -1.f, Ms, xs, cs, hp);
+    slice4([&](size_t q4, size_t i) {
+      const int r0 = 2 * ml.rq;
+      float4 x = __ldcg(V4(t) + q4);
+      float4 bx = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r0 < R) { const float2 y = b2[(size_t)r0 * n + i]; bx.x = y.x; bx.y = y.y; }
+      if (r0 + 1 < R) { const float2 y = b2[(size_t)(r0 + 1) * n + i]; bx.z = y.x; bx.w = y.y; }
+      V4(t)[q4] = make_float4(bx.x - x.x, bx.y - x.y, bx.z - x.z, bx.w - x.w);
+    });
+    mproject(t, vv, g2, -1.f);
   }
+  // the solutions in the [R][Ne Ns] layout
+  slice4([&](size_t q4, size_t i) {
+    const int r0 = 2 * ml.rq;
+    const float4 x = __ldcg(V4(vv) + q4);
+    float2* vo = reinterpret_cast<float2*>(a.v);
+    if (r0 < R) vo[(size_t)r0 * n + i] = make_float2(x.x, x.y);
+    if (r0 + 1 < R) vo[(size_t)(r0 + 1) * n + i] = make_float2(x.z, x.w);
+  });
   if (blockIdx.x == 0 && threadIdx.x < R) {
     const int r = threadIdx.x;
     a.out[2 * r] = sh.its[r];
@@ -1990,7 +2198,7 @@ extern "C" void dfl_destroy(dfl_ctx* d) {
                   d->basis64, d->basis16, d->B64, d->Binv64, d->Binv32, d->M64, d->M32, d->g64, d->g32,
                   d->Bg64, d->Bg32, d->lw[0], d->lw[1], d->B32, d->fw[0], d->fw[1], d->Ainv64, d->Ainv32,
                   d->coop_partial, d->coop_out, d->coop_err, d->ref64, d->ref32, d->ddf, d->ddl, d->mw, d->mio,
-                  d->meo, d->mpart, d->mred, d->mtol, d->mout};
+                  d->meo, d->macc, d->mscr, d->mtol, d->mout};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete d;
@@ -2538,9 +2746,30 @@ static bool launch_little_mrhs(dfl_ctx* d, CoopMArgs& a, cudaStream_t s, cudaErr
     return false;
   } else {
     void* args[] = {&a};
-    *err = cudaLaunchCooperativeKernel((void*)little_gcr_coop_mrhs_kernel<NS>, d->coop_grid, COOP_THREADS, args,
-                                       coop_m_dyn_bytes(NS), s);
+    void* fn = a.RP == 2   ? (void*)little_gcr_coop_mrhs_kernel<NS, 2>
+               : a.RP == 4 ? (void*)little_gcr_coop_mrhs_kernel<NS, 4>
+               : a.RP == 8 ? (void*)little_gcr_coop_mrhs_kernel<NS, 8>
+                           : (void*)little_gcr_coop_mrhs_kernel<NS, 16>;
+    *err = cudaLaunchCooperativeKernel(fn, d->coop_grid, COOP_THREADS, args, coop_m_dyn_bytes(NS, a.RP), s);
     return true;
+  }
+}
+
+// shared-memory limits of the multi-RHS kernels (RP = 2, 4, 8, 16); CTAs per SM of the largest
+template <int NS>
+static int mrhs_prepare(size_t dsm_max) {
+  if constexpr (NS == 0) {
+    return 0;
+  } else {
+    const void* fns[4] = {(const void*)little_gcr_coop_mrhs_kernel<NS, 2>, (const void*)little_gcr_coop_mrhs_kernel<NS, 4>,
+                          (const void*)little_gcr_coop_mrhs_kernel<NS, 8>, (const void*)little_gcr_coop_mrhs_kernel<NS, 16>};
+    for (int q = 0; q < 4; ++q)
+      if (cudaFuncSetAttribute(fns[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)coop_m_dyn_bytes(NS, 2 << q)) !=
+          cudaSuccess)
+        return 0;
+    int bm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bm, fns[3], COOP_THREADS, dsm_max) != cudaSuccess) return 0;
+    return bm;
   }
 }
 
@@ -2575,10 +2804,11 @@ static int little_solve_mrhs(dfl_ctx* d, const float* w, float* v, const double*
   for (int q = 0; q < R; ++q) htol[q] = (float)tol[idx[q]];
   DW_CUDA(cudaMemcpyAsync(d->mtol, htol, R * sizeof(float), cudaMemcpyHostToDevice, s));
   CoopMArgs a;
-  a.Ne = d->Ne; a.No = d->No; a.nkv = nkv; a.maxit = maxit; a.a3 = d->a3 ? 1 : 0; a.R = R;
+  a.Ne = d->Ne; a.No = d->No; a.nkv = nkv; a.maxit = maxit; a.a3 = d->a3 ? 1 : 0; a.R = R; a.RP = coop_mrp(R);
   a.list_e = d->d_list[0]; a.list_o = d->d_list[1]; a.lnb_e = d->d_lnb[0]; a.lnb_o = d->d_lnb[1];
   a.M = d->M32; a.g = d->a3 ? d->g32 : nullptr; a.Bg = d->a3 ? d->Bg32 : nullptr; a.Ainv = d->a3 ? d->Ainv32 : nullptr;
-  a.b = bE; a.tol = d->mtol; a.v = vE; a.work = d->mw; a.partial = d->mpart; a.red = d->mred; a.out = d->mout;
+  a.b = bE; a.tol = d->mtol; a.v = vE; a.work = d->mw; a.scratch = d->mscr; a.acc = d->macc; a.out = d->mout;
+  DW_CUDA(cudaMemsetAsync(d->macc, 0, 3 * COOP_MNV * sizeof(double), s));
   cudaError_t le = cudaSuccess;
   bool launched = false;
   NS_DISPATCH_FEW(Ns, (launched = launch_little_mrhs<NSV>(d, a, s, &le)));
@@ -3042,20 +3272,16 @@ static int little_setup(dw_ctx* c, dfl_ctx* d, const double* B64_given) {
       d->coop_ring = br > 0 && !(re && re[0] == '0');
       // multi-RHS solver (batches of right-hand sides): Ns with a compiled kernel, all CTAs resident
       int bm = 0;
-      const size_t dsmm = coop_m_dyn_bytes(Ns);
-      NS_DISPATCH_FEW(Ns, if constexpr (NSV > 0) {
-        if (cudaFuncSetAttribute(little_gcr_coop_mrhs_kernel<NSV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)dsmm) == cudaSuccess)
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bm, little_gcr_coop_mrhs_kernel<NSV>, COOP_THREADS, dsmm);
-      });
+      const size_t dsmm = coop_m_dyn_bytes(Ns, COOP_MRP);
+      NS_DISPATCH_FEW(Ns, (bm = mrhs_prepare<NSV>(dsmm)));
       cudaGetLastError();
       if (bm > 0) {
         const size_t ne = (size_t)d->Ne * Ns, no = (size_t)d->No * Ns;
-        DW_CUDA(cudaMalloc(&d->mw, ((size_t)2 * COOP_NKV + 4) * COOP_MAXR * ne * 2 * sizeof(float)));
+        DW_CUDA(cudaMalloc(&d->mw, ((size_t)2 * COOP_NKV + 6) * COOP_MRP * std::max(ne, no) * 2 * sizeof(float)));
         DW_CUDA(cudaMalloc(&d->mio, (size_t)2 * COOP_MAXR * ne * 2 * sizeof(float)));
         DW_CUDA(cudaMalloc(&d->meo, (size_t)2 * COOP_MAXR * no * 2 * sizeof(float)));
-        DW_CUDA(cudaMalloc(&d->mpart, (size_t)COOP_MNV * coop_gpad(d->coop_grid) * sizeof(float)));
-        DW_CUDA(cudaMalloc(&d->mred, (size_t)COOP_MNV * sizeof(float)));
+        DW_CUDA(cudaMalloc(&d->macc, (size_t)3 * COOP_MNV * sizeof(double)));
+        DW_CUDA(cudaMalloc(&d->mscr, (size_t)sms * coop_m_cta_scratch(Ns) * sizeof(float)));
         DW_CUDA(cudaMalloc(&d->mtol, COOP_MAXR * sizeof(float)));
         DW_CUDA(cudaMalloc(&d->mout, 2 * COOP_MAXR * sizeof(double)));
         d->coop_m = true;

@@ -228,6 +228,24 @@ def test_little_solve_batch(case, prec, tol, cmp):
         assert rel(v1.double().cpu().numpy().view(np.complex128), v[0]) <= cmp
 
 
+@pytest.mark.parametrize("R", [1, 3, 5])
+def test_little_solve_batch_padded(case, R):
+    """System counts that are not a power of two (the lockstep solver pads the systems to 2, 4, 8):
+    every solution against the dense solve of the oracle's little operator."""
+    L, sb, db, Ns, ctx, D, start = case
+    d = _build(case, dw.DW_BF16)
+    sub = oracle_sub(case, True)
+    wv = synth.complex_gaussian((R, d.Nb * d.Ns), 19).numpy()
+    wt = torch.from_numpy(wv.view(np.float64).copy()).to(torch.float32).cuda()
+    vt = torch.empty_like(wt)
+    rc, its, rrs = dw.little_dirac_solve_batch(d, dw.DW_F32, R, wt, vt, 1e-5, 2000)
+    assert rc == dw.DW_OK and max(rrs) <= 1e-5 and min(its) > 0
+    v = vt.double().cpu().numpy().view(np.complex128).reshape(R, -1)
+    ref = np.linalg.solve(sub.A, wv.T).T
+    for r in range(R):
+        assert rel(v[r], ref[r]) <= 1e-4, r
+
+
 # ----------------------------------------------------------------------------- full solver
 @pytest.fixture(scope="module")
 def solve_case():
