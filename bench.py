@@ -378,7 +378,12 @@ def profile_case(args, wl):
         else:
             eta = synth.point_sources(L).cuda()
             psi = torch.empty_like(eta)
+            dw.dw_autotune(ctx, 12)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_push("batched_solve")
             rc, _ = dw.gcr_solve(ctx, d, dw.sol_params(tol=wl["tol"], nkv=wl["nkv"], mixed=1), 12, eta, psi)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
             print("batched solve rc", rc, flush=True)
     torch.cuda.synchronize()
     print("ok", flush=True)

@@ -2235,13 +2235,93 @@ static int prolong_t(dfl_ctx* d, const T* c, T* psi, int mode, cudaStream_t s, i
                                             (size_t)d->N * 2); dw_note_launch();
   return DW_OK;
 }
+// s + e += f x for an FP32 number f and a double-float x: the product split exactly into
+// h + l (h = fl(f x.hi), its rounding error by one FMA, plus f x.lo), h added to s by TwoSum, the
+// addition error and l added to the compensation e (compensated dot product, Ogita, Rump and
+// Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005)
+DW_D void dot2_acc(float& s, float& e, float f, dd x) {
+  const float h = __fmul_rn(f, x.hi);
+  const float l = __fmaf_rn(f, x.lo, __fmaf_rn(f, x.hi, -h));
+  const float t = __fadd_rn(s, h);
+  const float b = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, b)), __fsub_rn(h, b));
+  s = t;
+  e = __fadd_rn(e, __fadd_rn(err, l));
+}
+
+// c[L][k] = (phi^L_k, psi) for a double-float psi and the BF16 basis (its entries are exact FP32
+// numbers): per thread a compensated dot product (dot2_acc: about 11 FP32 operations per real
+// product, against about 30 for full double-float arithmetic), then the threads' s + e combined
+// in double-float arithmetic.  The result carries about twice the FP32 precision.
+template <int NS>
+__global__ void __launch_bounds__(128, 2) restrict_dd_bf16_kernel(Geom g, const int* __restrict__ sub, int nsub,
+                                                                   const uint4* __restrict__ b16,
+                                                                   const dd* __restrict__ psi0, dd* __restrict__ c0,
+                                                                   int nrhs, size_t fstride, size_t cstride) {
+  using WH = WarpHalve<dd, 2 * NS, 16>;
+  constexpr int MF = WH::final_m();
+  __shared__ dd sh[4][2 * NS];
+  const int L = blockIdx.x;
+  const size_t V = g.V;
+  const int nsite = nsub * g.svol;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int rhs = 0; rhs < nrhs; ++rhs) {
+    const dd* psi = psi0 + (size_t)rhs * fstride;
+    dd* c = c0 + (size_t)rhs * cstride;
+    float sa[2 * NS], ea[2 * NS];
+#pragma unroll
+    for (int m = 0; m < 2 * NS; ++m) sa[m] = ea[m] = 0.f;
+    for (int t = threadIdx.x; t < nsite; t += blockDim.x) {
+      const long long i = dfl_site(g, sub, nsub, L, t);
+      cplx<dd> p[12];
+      load_site<dd, 12>(psi, V, i, p);
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        cplx<float> f[12];
+        load_basis<float>(nullptr, b16, V, k, i, f);
+#pragma unroll
+        for (int j = 0; j < 12; ++j) {   // (f, p) = sum conj(f) p
+          dot2_acc(sa[2 * k], ea[2 * k], f[j].re, p[j].re);
+          dot2_acc(sa[2 * k], ea[2 * k], f[j].im, p[j].im);
+          dot2_acc(sa[2 * k + 1], ea[2 * k + 1], f[j].re, p[j].im);
+          dot2_acc(sa[2 * k + 1], ea[2 * k + 1], -f[j].im, p[j].re);
+        }
+      }
+    }
+    dd acc[2 * NS];
+#pragma unroll
+    for (int m = 0; m < 2 * NS; ++m) acc[m] = dd_two_sum(sa[m], ea[m]);
+    int base = 0;
+    WH::run(acc, lane, base);
+#pragma unroll
+    for (int m = 0; m < MF; ++m) sh[w][base + m] = acc[m];
+    __syncthreads();
+    if (threadIdx.x < 2 * NS) {
+      dd y = sh[0][threadIdx.x];
+#pragma unroll
+      for (int q = 1; q < 4; ++q) y += sh[q][threadIdx.x];
+      c[(size_t)L * 2 * NS + threadIdx.x] = y;
+    }
+    __syncthreads();
+  }
+}
+
+// DW_DD_DOT2=0: full double-float arithmetic in the restriction (the compensated kernel's reference)
+static bool dd_dot2_disabled() {
+  const char* e = getenv("DW_DD_DOT2");
+  return e && e[0] == '0';
+}
 template <int NS>
 static bool launch_restrict_dd(dfl_ctx* d, const dd* psi, dd* c, cudaStream_t s) {
   if constexpr (NS == 0) {
     return false;
   } else {
-    restrict_ns_kernel<dd, NS><<<d->Nb, 128, 0, s>>>(d->c->g, d->d_sub, d->nsub, d->basis16 ? nullptr : d->basis64,
-                                                     d->basis16, psi, c, 1, (size_t)d->c->V * 24, (size_t)d->N * 2);
+    if (d->basis16 && !dd_dot2_disabled())
+      restrict_dd_bf16_kernel<NS><<<d->Nb, 128, 0, s>>>(d->c->g, d->d_sub, d->nsub, d->basis16, psi, c, 1,
+                                                        (size_t)d->c->V * 24, (size_t)d->N * 2);
+    else
+      restrict_ns_kernel<dd, NS><<<d->Nb, 128, 0, s>>>(d->c->g, d->d_sub, d->nsub, d->basis16 ? nullptr : d->basis64,
+                                                       d->basis16, psi, c, 1, (size_t)d->c->V * 24, (size_t)d->N * 2);
     return true;
   }
 }
