@@ -64,7 +64,7 @@ PLAIN_COUNTS = os.path.join(ROOT, "paper_0706_2298_gb300", "plain_gcr_counts.jso
 # current kernel (dram__bytes_read.sum + dram__bytes_write.sum of one launch / its iterations):
 # 48x24^3, Ns = 20: (76.61 + 3.65) MB over 41 iterations (cold cache: the first iteration reads
 # the little operator from HBM, the rest hit L2).  Remove an entry when the kernel changes.
-LITTLE_TRAFFIC = {("24^3x48", 20): 80.26e6 / 41}
+LITTLE_TRAFFIC = {("24^3x48", 20): 80.84e6 / 41}
 
 
 def aggregate_ranks(t_ms, steps, world, device="cpu"):
@@ -334,7 +334,8 @@ def run_reference(args, wl, rank):
 def profile_case(args, wl):
     """Small fixed launch sequences for ncu captures of single kernels (not a benchmark):
     'dirac-sap': 3 D applications and 2 M_sap (ncy = 1) in --prec;  'little': --solves FP32
-    little solves to 1e-6 with an Ns-field subspace (4 inverse-iteration steps);  'batch12': one
+    little solves to 1e-6 with an Ns-field subspace (4 inverse-iteration steps);  'little12': the
+    same with 12 systems in one multi-RHS solve;  'batch12': one
     batched solve of the 12 point sources;  'ptnet': one 16 -> 16 network layer on the tensor cores
     and one on the CUDA cores."""
     import torch
@@ -361,10 +362,22 @@ def profile_case(args, wl):
         for _ in range(2):
             dw.sap_precondition(ctx, prec, 1, wl["nmr"], 1, x, y)
     else:
-        n_inv = 4 if args.profile_case == "little" else wl["n_inv"]
+        n_inv = 4 if args.profile_case in ("little", "little12") else wl["n_inv"]
         d = dw.deflation_build(ctx, wl["dfl_bs"], wl["Ns"], n_inv, wl["ncy"], wl["nmr"],
                                synth.start_fields(L, wl["Ns"], wl["start_seed"]).cuda())
-        if args.profile_case == "little":
+        if args.profile_case == "little12":
+            # the 12 systems of a point-source batch in one multi-RHS little solve (FP32, 1e-6)
+            w = torch.randn(12 * d.Nb * d.Ns * 2, dtype=torch.float32, device="cuda")
+            v = torch.empty_like(w)
+            for _ in range(args.solves):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rc, its, rr = dw.little_dirac_solve_batch(d, dw.DW_F32, 12, w, v, 1e-6, 2000)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                print(f"12-system little solve rc {rc} iterations {max(its)} {dt * 1e6 / max(max(its), 1):.1f} "
+                      "us/iteration", flush=True)
+        elif args.profile_case == "little":
             w = torch.randn(d.Nb * d.Ns * 2, dtype=torch.float32, device="cuda")
             v = torch.empty_like(w)
             for _ in range(args.solves):
@@ -404,7 +417,7 @@ def main():
     ap.add_argument("--no-ptnet", action="store_true", help="skip the network-layer timing")
     ap.add_argument("--no-table1", action="store_true",
                     help="skip the solver comparison over masses and the subspace generation variants")
-    ap.add_argument("--profile-case", choices=["dirac-sap", "little", "batch12", "ptnet"], default=None,
+    ap.add_argument("--profile-case", choices=["dirac-sap", "little", "little12", "batch12", "ptnet"], default=None,
                     help="run a small fixed launch sequence for an ncu capture and exit")
     ap.add_argument("--prec", default="f32", choices=["f32", "f64"], help="--profile-case dirac-sap precision")
     ap.add_argument("--solves", type=int, default=1, help="--profile-case little: number of little solves")

@@ -629,7 +629,12 @@ DW_D cplx<T> warp_mv(const cplx<T>* __restrict__ m, const cplx<T>* __restrict__ 
 template <typename T, int NS>
 __global__ void __launch_bounds__(256) little_hop_kernel(int n, int Ns, const int* __restrict__ list,
                                                          const int* __restrict__ lnb, const T* __restrict__ M,
-                                                         const T* __restrict__ src, const T* base, T* out) {
+                                                         const T* __restrict__ src, const T* base, T* out,
+                                                         size_t sys_stride_in = 0, size_t sys_stride_out = 0) {
+  // blockIdx.y: system of a batch (vectors sys_stride_* reals apart; base strided like src)
+  src += blockIdx.y * sys_stride_in;
+  if (base) base += blockIdx.y * sys_stride_out;
+  out += blockIdx.y * sys_stride_out;
   __shared__ double hop64[8][2 * 32];
   const int r = blockIdx.x;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -657,7 +662,9 @@ __global__ void __launch_bounds__(256) little_hop_kernel(int n, int Ns, const in
 // out[i] = Binv[blk_i] * src[i]  (compact parity list vectors)
 template <typename T, int NS>
 __global__ void little_bdiag_kernel(int n, int Ns, const int* __restrict__ list, const T* __restrict__ Binv,
-                                    const T* __restrict__ src, T* out) {
+                                    const T* __restrict__ src, T* out, size_t sys_stride = 0) {
+  src += blockIdx.y * sys_stride;       // blockIdx.y: system of a batch
+  out += blockIdx.y * sys_stride;
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (wid >= n) return;
@@ -694,7 +701,9 @@ __global__ void little_bdiag_kernel(int n, int Ns, const int* __restrict__ list,
 // gather a parity part of a full little vector ([Nb][Ns]) into compact order / scatter back
 template <typename Tin, typename Tout>
 __global__ void little_gather_kernel(int n, int Ns, const int* __restrict__ list, const Tin* __restrict__ full,
-                                     Tout* part) {
+                                     Tout* part, size_t sys_stride_full = 0, size_t sys_stride_part = 0) {
+  full += blockIdx.y * sys_stride_full;   // blockIdx.y: system of a batch
+  part += blockIdx.y * sys_stride_part;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * Ns) return;
   int i = t / Ns, k = t % Ns;
@@ -704,7 +713,9 @@ __global__ void little_gather_kernel(int n, int Ns, const int* __restrict__ list
 }
 template <typename Tin, typename Tout>
 __global__ void little_scatter_kernel(int n, int Ns, const int* __restrict__ list, const Tin* __restrict__ part,
-                                      Tout* full) {
+                                      Tout* full, size_t sys_stride_part = 0, size_t sys_stride_full = 0) {
+  part += blockIdx.y * sys_stride_part;   // blockIdx.y: system of a batch
+  full += blockIdx.y * sys_stride_full;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * Ns) return;
   int i = t / Ns, k = t % Ns;
@@ -2864,7 +2875,24 @@ static int little_solve_mrhs(dfl_ctx* d, const float* w, float* v, const double*
   float* wO = d->meo;                                   // [R][n_o] complex
   float* yO = d->meo + (size_t)COOP_MAXR * n_o * 2;
   unsigned ge = (unsigned)((n_e + 255) / 256), go = (unsigned)((n_o + 255) / 256);
-  for (int q = 0; q < R; ++q) {
+  // systems idx[0], idx[0] + 1, ...: every step below is one launch for all of them (grid.y)
+  bool contiguous = true;
+  for (int q = 1; q < R; ++q) contiguous &= idx[q] == idx[0] + q;
+  if (contiguous) {
+    const float* wr = w + (size_t)idx[0] * N2;
+    const size_t se = 2 * (size_t)n_e, so = 2 * (size_t)n_o;
+    float* wt = vE;                                     // scratch until the solve overwrites it
+    little_gather_kernel<float, float><<<dim3(ge, R), 256, 0, s>>>(d->Ne, Ns, d->d_list[0], wr, bE, N2, se);
+    little_gather_kernel<float, float><<<dim3(go, R), 256, 0, s>>>(d->No, Ns, d->d_list[1], wr, wO, N2, so);
+    NS_DISPATCH(Ns, (little_bdiag_kernel<float, NSV><<<dim3(warps_grid(d->No), R), 128, 0, s>>>(
+                         d->No, Ns, d->d_list[1], d->Binv32, wO, yO, so)));
+    NS_DISPATCH(Ns, (little_bdiag_kernel<float, NSV><<<dim3(warps_grid(d->Ne), R), 128, 0, s>>>(
+                         d->Ne, Ns, d->d_list[0], d->Binv32, bE, wt, se)));
+    NS_DISPATCH(Ns, (little_hop_kernel<float, NSV><<<dim3(d->Ne, R), 256, 0, s>>>(
+                         d->Ne, Ns, d->d_list[0], d->d_lnb[0], d->M32, yO, wt, bE, so, se)));
+    for (int q = 0; q < 5; ++q) dw_note_launch();
+  }
+  for (int q = 0; q < R && !contiguous; ++q) {
     const float* wr = w + (size_t)idx[q] * N2;
     float* be = bE + (size_t)q * n_e * 2;
     float* wo = wO + (size_t)q * n_o * 2;
@@ -2895,7 +2923,16 @@ static int little_solve_mrhs(dfl_ctx* d, const float* w, float* v, const double*
   if (!launched) { dw_set_error("multi-RHS little solver: unsupported Ns"); return DW_EINVAL; }
   DW_CUDA(le);
   dw_note_launch();
-  for (int q = 0; q < R; ++q) {
+  if (contiguous) {
+    float* vr = v + (size_t)idx[0] * N2;
+    const size_t se = 2 * (size_t)n_e, so = 2 * (size_t)n_o;
+    NS_DISPATCH(Ns, (little_hop_kernel<float, NSV><<<dim3(d->No, R), 256, 0, s>>>(
+                         d->No, Ns, d->d_list[1], d->d_lnb[1], d->M32, vE, yO, wO, se, so)));
+    little_scatter_kernel<float, float><<<dim3(ge, R), 256, 0, s>>>(d->Ne, Ns, d->d_list[0], vE, vr, se, N2);
+    little_scatter_kernel<float, float><<<dim3(go, R), 256, 0, s>>>(d->No, Ns, d->d_list[1], wO, vr, so, N2);
+    for (int q = 0; q < 3; ++q) dw_note_launch();
+  }
+  for (int q = 0; q < R && !contiguous; ++q) {
     float* vr = v + (size_t)idx[q] * N2;
     float* ve = vE + (size_t)q * n_e * 2;
     float* wo = wO + (size_t)q * n_o * 2;
