@@ -271,8 +271,9 @@ int gcr_solve(dw_ctx* ctx, dfl_ctx* d, const sol_params* p, int nrhs, const doub
               double* psi_dev, sol_info* info, void* stream);
 
 /* Autotuner: times the candidate launch shapes of the hot kernels on this
- * context's lattice for nrhs right-hand sides (multi-RHS D: right-hand sides per
- * pass 1..3; Schwarz kernel: staged or generic FP32 variant) with CUDA events,
+ * context's lattice for nrhs right-hand sides (multi-RHS D: one thread per site and
+ * right-hand side with the site chunks interleaved, or one thread per site with
+ * 1..3 right-hand sides per pass; Schwarz kernel: staged or generic FP32 variant) with CUDA events,
  * keeps the fastest in the context and writes a JSON summary to report
  * (may be NULL).  Synchronous; allocates two temporary batches of fields. */
 int dw_autotune(dw_ctx* ctx, int nrhs, char* report, size_t report_len);

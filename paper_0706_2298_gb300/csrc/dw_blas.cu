@@ -60,7 +60,14 @@ __device__ void grid_reduce(double* v, double* partial, unsigned* count, double*
 // thread), combined across threads in FP64.  vec: 16-byte loads when both pointers allow them.
 template <typename T>
 __global__ void __launch_bounds__(RB) dot_kernel(const T* __restrict__ a, const T* __restrict__ b, size_t n,
-                                                 int vec, double* partial, unsigned* count, double* out) {
+                                                 int vec, double* partial, unsigned* count, double* out,
+                                                 size_t sys_stride = 0) {
+  // blockIdx.y: field of a batch (sys_stride reals apart), with its own scratch, counter and result
+  a += blockIdx.y * sys_stride;
+  b += blockIdx.y * sys_stride;
+  partial += (size_t)blockIdx.y * gridDim.x * 3;
+  count += blockIdx.y;
+  out += 3 * blockIdx.y;
   T r0 = 0, r1 = 0, r2 = 0;   // re, im of (a, b), |a|^2
   const size_t tid = blockIdx.x * (size_t)RB + threadIdx.x, nth = (size_t)gridDim.x * RB;
   const cplx<T>* A = reinterpret_cast<const cplx<T>*>(a);
@@ -97,7 +104,16 @@ __global__ void __launch_bounds__(RB) dot_kernel(const T* __restrict__ a, const 
 
 template <typename T, int K>
 __global__ void __launch_bounds__(RB) multi_dot_kernel(Ptrs<T, MAXK> vs, const T* __restrict__ b, size_t n,
-                                                       double* partial, unsigned* count, double* out) {
+                                                       double* partial, unsigned* count, double* out,
+                                                       size_t sys_stride = 0, size_t out_stride = 0) {
+  // blockIdx.y: field of a batch (every vector and b sys_stride reals further on), own scratch
+  const size_t so = blockIdx.y * sys_stride;
+#pragma unroll
+  for (int k = 0; k < K; ++k) vs.p[k] += so;
+  b += so;
+  partial += (size_t)blockIdx.y * gridDim.x * 2 * K;
+  count += blockIdx.y;
+  out += blockIdx.y * out_stride;
   T r[2 * K];
 #pragma unroll
   for (int k = 0; k < 2 * K; ++k) r[k] = 0;
@@ -115,6 +131,35 @@ __global__ void __launch_bounds__(RB) multi_dot_kernel(Ptrs<T, MAXK> vs, const T
 #pragma unroll
   for (int k = 0; k < 2 * K; ++k) v[k] = (double)r[k];
   grid_reduce<2 * K>(v, partial, count, out);
+}
+
+// One GCR step for a batch of fields (grid.y = field r, fields sys_stride reals apart): chi_r *=
+// inv_r, rho_r -= a_r chi_r, and |rho_r|^2 reduced as in dot_kernel (FP64 across threads); fields
+// whose live flag is 0 are left alone.
+struct GcrStepCoefs {
+  float inv[16], ar[16], ai[16];
+  int live[16];
+};
+template <typename T>
+__global__ void __launch_bounds__(RB) gcr_step_batch_kernel(T* __restrict__ chi, T* __restrict__ rho, size_t n,
+                                                            size_t sys_stride, GcrStepCoefs cf, double* partial,
+                                                            unsigned* count, double* out) {
+  const int r = blockIdx.y;
+  if (!cf.live[r]) return;
+  cplx<T>* X = reinterpret_cast<cplx<T>*>(chi + r * sys_stride);
+  cplx<T>* Y = reinterpret_cast<cplx<T>*>(rho + r * sys_stride);
+  const T inv = cf.inv[r];
+  const cplx<T> a = {(T)cf.ar[r], (T)cf.ai[r]};
+  T nr = 0;
+  for (size_t i = blockIdx.x * (size_t)RB + threadIdx.x; i < n; i += (size_t)gridDim.x * RB) {
+    const cplx<T> x = inv * X[i];
+    X[i] = x;
+    const cplx<T> y = Y[i] - a * x;
+    Y[i] = y;
+    nr += y.re * y.re + y.im * y.im;
+  }
+  double v[3] = {0.0, 0.0, (double)nr};
+  grid_reduce<3>(v, partial + (size_t)r * gridDim.x * 3, count + r, out + 3 * r);
 }
 
 template <typename T>
@@ -178,6 +223,26 @@ __global__ void multi_axpy_kernel(Ptrs<T, MAXK> vs, Coefs<T> cf, T* __restrict__
   }
 }
 
+// y_r -= sum_k c_{r,k} v_{k,r} for a batch of fields (grid.y = r; v_{k,r} = vs.p[k] + r sys_stride)
+struct CoefsBatch {
+  float c[16][2 * MAXK];
+};
+template <typename T, int K>
+__global__ void multi_axpy_batch_kernel(Ptrs<T, MAXK> vs, CoefsBatch cf, T* __restrict__ y0, size_t n,
+                                        size_t sys_stride) {
+  const int rr = blockIdx.y;
+  cplx<T>* Y = reinterpret_cast<cplx<T>*>(y0 + rr * sys_stride);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    cplx<T> acc = Y[i];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const cplx<T> ck = {(T)cf.c[rr][2 * k], (T)cf.c[rr][2 * k + 1]};
+      acc -= ck * reinterpret_cast<const cplx<T>*>(vs.p[k] + rr * sys_stride)[i];
+    }
+    Y[i] = acc;
+  }
+}
+
 inline unsigned ew_grid(size_t n) {
   size_t b = (n + 255) / 256;
   return (unsigned)(b < 152 * 16 ? b : 152 * 16);
@@ -190,6 +255,42 @@ int blas_dot(dw_ctx* c, const T* a, const T* b, size_t n, double* out3, cudaStre
   // out3 (device): re, im of (a, b) and |a|^2
   const int vec = ((((uintptr_t)a) | ((uintptr_t)b)) % 16) == 0;
   dot_kernel<T><<<RGRID, RB, 0, s>>>(a, b, n, vec, c->d_red, c->d_count, out3); dw_note_launch();
+  return DW_OK;
+}
+
+// nrhs dot products (fields sys_stride reals apart) in one launch: out3[3 r ..] as blas_dot.
+// At most 16 fields (their reduction counters); more are done one by one.
+template <typename T>
+int blas_dot_batch(dw_ctx* c, const T* a, const T* b, size_t n, size_t sys_stride, int nrhs, double* out3,
+                   cudaStream_t s) {
+  if (nrhs > 16) {
+    for (int r = 0; r < nrhs; ++r) blas_dot<T>(c, a + r * sys_stride, b + r * sys_stride, n, out3 + 3 * r, s);
+    return DW_OK;
+  }
+  const int vec = ((((uintptr_t)a) | ((uintptr_t)b) | (sys_stride * sizeof(T))) % 16) == 0;
+  dot_kernel<T><<<dim3(RGRID / 4, nrhs), RB, 0, s>>>(a, b, n, vec, c->d_red, c->d_count + 16, out3, sys_stride);
+  dw_note_launch();
+  return DW_OK;
+}
+template int blas_dot_batch<float>(dw_ctx*, const float*, const float*, size_t, size_t, int, double*, cudaStream_t);
+template int blas_dot_batch<double>(dw_ctx*, const double*, const double*, size_t, size_t, int, double*,
+                                    cudaStream_t);
+
+// chi_r *= inv_r, rho_r -= (ar_r + i ai_r) chi_r and |rho_r|^2 -> out3[3 r + 2] for the live fields
+// of a batch of at most 16 (fields sys_stride reals apart), one launch.
+int gcr_step_batch(dw_ctx* c, float* chi, float* rho, size_t n, size_t sys_stride, int nrhs, const double* inv,
+                   const double* ar, const double* ai, const int* live, double* out3, cudaStream_t s) {
+  if (nrhs > 16) return DW_EINVAL;
+  GcrStepCoefs cf{};
+  for (int r = 0; r < nrhs; ++r) {
+    cf.inv[r] = (float)inv[r];
+    cf.ar[r] = (float)ar[r];
+    cf.ai[r] = (float)ai[r];
+    cf.live[r] = live[r];
+  }
+  gcr_step_batch_kernel<float><<<dim3(RGRID / 4, nrhs), RB, 0, s>>>(chi, rho, n, sys_stride, cf, c->d_red,
+                                                                    c->d_count + 16, out3);
+  dw_note_launch();
   return DW_OK;
 }
 
@@ -213,6 +314,60 @@ int blas_multi_dot(dw_ctx* c, const T* const* vs, int k, const T* b, size_t n, d
   }
   return DW_OK;
 }
+
+// The Gram-Schmidt pair of a batched GCR step for nrhs <= 16 fields (sys_stride reals apart):
+// out[r ostride + 2j ..] = (v_j, b) for j < k, then (separately, with the coefficients the host
+// formed) b -= sum_j c_{r,j} v_j.  One launch per chunk of 16 vectors instead of one per field.
+template <typename T, int K>
+static void launch_md_batch(dw_ctx* c, const Ptrs<T, MAXK>& p, const T* b, size_t n, size_t st, int nrhs,
+                            double* out, size_t ostride, cudaStream_t s) {
+  multi_dot_kernel<T, K><<<dim3(RGRID / 4, nrhs), RB, 0, s>>>(p, b, n, c->d_red, c->d_count + 16, out, st, ostride);
+  dw_note_launch();
+}
+template <typename T>
+int blas_multi_dot_batch(dw_ctx* c, const T* const* vs, int k, const T* b, size_t n, size_t sys_stride, int nrhs,
+                         double* out, size_t ostride, cudaStream_t s) {
+  if (nrhs > 16) return DW_EINVAL;
+  for (int j0 = 0; j0 < k; j0 += MAXK) {
+    const int kk = k - j0 < MAXK ? k - j0 : MAXK;
+    Ptrs<T, MAXK> p{};
+    for (int j = 0; j < kk; ++j) p.p[j] = vs[j0 + j];
+    double* o = out + 2 * j0;
+    switch (kk) {
+#define MDB(K) case K: launch_md_batch<T, K>(c, p, b, n, sys_stride, nrhs, o, ostride, s); break;
+      MDB(1) MDB(2) MDB(3) MDB(4) MDB(5) MDB(6) MDB(7) MDB(8) MDB(9) MDB(10) MDB(11) MDB(12) MDB(13) MDB(14)
+      MDB(15) MDB(16)
+#undef MDB
+    }
+  }
+  return DW_OK;
+}
+template <typename T>
+int blas_multi_axpy_batch(const T* const* vs, int k, const double* coef, size_t cstride, T* y, size_t n,
+                          size_t sys_stride, int nrhs, cudaStream_t s) {
+  if (nrhs > 16) return DW_EINVAL;
+  for (int j0 = 0; j0 < k; j0 += MAXK) {
+    const int kk = k - j0 < MAXK ? k - j0 : MAXK;
+    Ptrs<T, MAXK> p{};
+    CoefsBatch cf{};
+    for (int j = 0; j < kk; ++j) p.p[j] = vs[j0 + j];
+    for (int r = 0; r < nrhs; ++r)
+      for (int j = 0; j < 2 * kk; ++j) cf.c[r][j] = (float)coef[r * cstride + 2 * j0 + j];
+    const dim3 grid((ew_grid(n) + nrhs - 1) / nrhs + 1, nrhs);
+    switch (kk) {
+#define MAB(K) case K: multi_axpy_batch_kernel<T, K><<<grid, 256, 0, s>>>(p, cf, y, n, sys_stride); break;
+      MAB(1) MAB(2) MAB(3) MAB(4) MAB(5) MAB(6) MAB(7) MAB(8) MAB(9) MAB(10) MAB(11) MAB(12) MAB(13) MAB(14)
+      MAB(15) MAB(16)
+#undef MAB
+    }
+    dw_note_launch();
+  }
+  return DW_OK;
+}
+template int blas_multi_dot_batch<float>(dw_ctx*, const float* const*, int, const float*, size_t, size_t, int,
+                                         double*, size_t, cudaStream_t);
+template int blas_multi_axpy_batch<float>(const float* const*, int, const double*, size_t, float*, size_t, size_t,
+                                          int, cudaStream_t);
 
 template <typename T>
 void blas_axpy(const T* x, T* y, double ar, double ai, size_t n, cudaStream_t s) {

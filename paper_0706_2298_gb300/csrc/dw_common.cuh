@@ -346,7 +346,7 @@ struct dw_ctx {
   void* sap_r[2] = {nullptr, nullptr};    // SAP residual workspace
   void* sap_d[2] = {nullptr, nullptr};    // SAP last-correction workspace
   int sap_cap = 1;                        // right-hand sides the FP32 SAP workspace holds
-  int tune_rgroup = 3;                    // right-hand sides per pass of the multi-RHS D (autotuned)
+  int tune_rgroup = 0;                    // multi-RHS D variant: 0 interleaved, 1..3 per pass (autotuned)
   int tune_sap_staged = 1;                // 1: staged FP32 Schwarz kernel, 0: generic kernel (autotuned)
   void* graph_cache = nullptr;            // captured M_sap launch sequences (dw_sap.cu)
   cudaStream_t cap_stream = nullptr;      // stream used only for graph capture
@@ -414,6 +414,19 @@ inline size_t real_size(int prec) { return prec == DW_F64 ? 8 : 4; }
 template <typename T> int blas_dot(dw_ctx* c, const T* a, const T* b, size_t n_cplx, double* out2, cudaStream_t s);
 template <typename T> int blas_multi_dot(dw_ctx* c, const T* const* vs, int k, const T* b, size_t n_cplx,
                                          double* out2, cudaStream_t s);
+// nrhs dots of fields sys_stride reals apart in one launch (results 3 per field, as blas_dot)
+template <typename T> int blas_dot_batch(dw_ctx* c, const T* a, const T* b, size_t n_cplx, size_t sys_stride,
+                                         int nrhs, double* out3, cudaStream_t s);
+// Gram-Schmidt of a batch (<= 16 fields, sys_stride reals apart): dots of k vectors with b, and
+// b -= sum_j c_{r,j} v_j with host coefficients coef[r cstride + 2j ..]
+template <typename T> int blas_multi_dot_batch(dw_ctx* c, const T* const* vs, int k, const T* b, size_t n_cplx,
+                                               size_t sys_stride, int nrhs, double* out, size_t ostride,
+                                               cudaStream_t s);
+template <typename T> int blas_multi_axpy_batch(const T* const* vs, int k, const double* coef, size_t cstride, T* y,
+                                                size_t n_cplx, size_t sys_stride, int nrhs, cudaStream_t s);
+// one GCR step for live fields of a batch (<= 16): chi_r *= inv_r, rho_r -= a_r chi_r, |rho_r|^2
+int gcr_step_batch(dw_ctx* c, float* chi, float* rho, size_t n_cplx, size_t sys_stride, int nrhs, const double* inv,
+                   const double* ar, const double* ai, const int* live, double* out3, cudaStream_t s);
 // y = a*x + y  (complex a)
 template <typename T> void blas_axpy(const T* x, T* y, double ar, double ai, size_t n_cplx, cudaStream_t s);
 // y = x + b*y  (complex b)

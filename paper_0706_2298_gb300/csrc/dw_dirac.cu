@@ -32,6 +32,31 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) dirac_full_kernel
   store_site<T, 12>(out, V, i, y);
 }
 
+// Multi-RHS D with one thread per (site, right-hand side): the nrhs CTAs of one chunk of 128 sites
+// are consecutive in launch order (blockIdx.x = chunk * nrhs + rhs), so the chunk's links and clover
+// term come from HBM once and from L2 for the other right-hand sides (fields fstride reals apart).
+template <typename T>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) dirac_interleaved_kernel(
+    Geom g, const T* __restrict__ links, const T* __restrict__ clov, const T* __restrict__ in0, T* __restrict__ out0,
+    int nrhs, size_t fstride) {
+  const int r = blockIdx.x % nrhs;
+  const long long i = (long long)(blockIdx.x / nrhs) * blockDim.x + threadIdx.x;
+  if (i >= g.V) return;
+  const T* in = in0 + (size_t)r * fstride;
+  T* out = out0 + (size_t)r * fstride;
+  const size_t V = g.V;
+  SiteRef s = decode(g, i);
+  cplx<T> psi[12], y[12], acc[12];
+  load_site<T, 12>(in, V, i, psi);
+  clover_apply(clov, V, i, psi, y);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = {T(0), T(0)};
+  hop_all(g, s, i, links, in, acc);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) y[k] -= T(0.5) * acc[k];
+  store_site<T, 12>(out, V, i, y);
+}
+
 // t_o = A_oo^{-1} D_oe in_e   (odd sites; D_oe = -1/2 * hops)
 template <typename T>
 __global__ void __launch_bounds__(128) schur_odd_kernel(Geom g, const T* __restrict__ links,
@@ -215,6 +240,12 @@ void dirac_mrhs(dw_ctx* c, const T* in, T* out, int nrhs, int rgroup, cudaStream
   const size_t fs = (size_t)c->V * 24;
   const T* L = (const T*)c->links[P];
   const T* K = (const T*)c->clov[P];
+  if (rgroup == 0) {
+    const unsigned chunks = (unsigned)((c->V + 127) / 128);
+    dirac_interleaved_kernel<T><<<chunks * (unsigned)nrhs, 128, 0, st>>>(c->g, L, K, in, out, nrhs, fs);
+    dw_note_launch();
+    return;
+  }
   if (rgroup >= 3) { dirac_mrhs_kernel<T, 3><<<blocks, 128, 0, st>>>(c->g, L, K, in, out, nrhs, fs); dw_note_launch(); }
   else if (rgroup == 2) { dirac_mrhs_kernel<T, 2><<<blocks, 128, 0, st>>>(c->g, L, K, in, out, nrhs, fs); dw_note_launch(); }
   else { dirac_mrhs_kernel<T, 1><<<blocks, 128, 0, st>>>(c->g, L, K, in, out, nrhs, fs); dw_note_launch(); }

@@ -673,7 +673,8 @@ int sap_apply_mrhs_graph(dw_ctx* c, int ncy, int nmr, const float* rho, float* x
 
 // ---------------------------------------------------------------- autotuner
 // Times the candidate launch shapes on this lattice with CUDA events (median of 5 after 2 warm-ups)
-// and keeps the fastest: right-hand sides per pass of the multi-RHS D (1, 2, 3) and the staged or
+// and keeps the fastest: the multi-RHS D as one thread per (site, right-hand side) with the chunks
+// interleaved, or one thread per site with 1, 2 or 3 right-hand sides per pass; the staged or
 // generic FP32 Schwarz kernel.
 extern "C" int dw_autotune(dw_ctx* c, int nrhs, char* report, size_t report_len) {
   if (!c || nrhs < 1 || nrhs > 64) { dw_set_error("dw_autotune: bad argument"); return DW_EINVAL; }
@@ -701,8 +702,8 @@ extern "C" int dw_autotune(dw_ctx* c, int nrhs, char* report, size_t report_len)
     return ts[ts.size() / 2];
   };
   float td[4] = {0, 0, 0, 0};
-  int best_r = 1;
-  for (int rg = 1; rg <= 3; ++rg) {
+  int best_r = 0;
+  for (int rg = 0; rg <= 3; ++rg) {     // 0: one thread per (site, right-hand side), chunk-interleaved
     td[rg] = time_it([&] { dirac_mrhs<float>(c, x, y, nrhs, rg, 0); });
     if (td[rg] < td[best_r]) best_r = rg;
   }
@@ -720,9 +721,10 @@ extern "C" int dw_autotune(dw_ctx* c, int nrhs, char* report, size_t report_len)
   cudaFree(y);
   if (report && report_len) {
     snprintf(report, report_len,
-             "{\"nrhs\": %d, \"dirac_mrhs_ms\": {\"1\": %.4f, \"2\": %.4f, \"3\": %.4f}, \"rgroup\": %d, "
+             "{\"nrhs\": %d, \"dirac_mrhs_ms\": {\"interleaved\": %.4f, \"1\": %.4f, \"2\": %.4f, \"3\": %.4f}, "
+             "\"rgroup\": %d, "
              "\"sap_pass_ms\": {\"generic\": %.4f, \"staged\": %.4f}, \"sap_staged\": %d}",
-             nrhs, td[1], td[2], td[3], best_r, ts[0], ts[1], c->tune_sap_staged);
+             nrhs, td[0], td[1], td[2], td[3], best_r, ts[0], ts[1], c->tune_sap_staged);
   }
   DW_CUDA(cudaGetLastError());
   return DW_OK;

@@ -359,7 +359,7 @@ int solve_batch_f32(dw_ctx* c, dfl_ctx* d, const sol_params* p, int nrhs, const 
   auto F64 = [&](double* base, int r) { return base + (size_t)r * fs; };
   // batched norms / dots: one kernel per right-hand side, one read for all
   auto norms64 = [&](double* base, std::vector<double>& out) -> int {
-    for (int r = 0; r < nrhs; ++r) blas_dot<double>(c, F64(base, r), F64(base, r), n, dres + 3 * r, s);
+    blas_dot_batch<double>(c, base, base, n, fs, nrhs, dres, s);
     int e = read_host(c, dres, 3 * nrhs, h.data(), s);
     for (int r = 0; r < nrhs; ++r) out[r] = sqrt(h[3 * r + 2]);
     return e;
@@ -383,10 +383,8 @@ int solve_batch_f32(dw_ctx* c, dfl_ctx* d, const sol_params* p, int nrhs, const 
       dirac_full_dd(c, dda, ddb, s);
       dd_to_f64(ddb, F64(W.t64, r), fs, 0, s);
     }
-    for (int r = 0; r < nrhs; ++r) {
-      DW_CUDA(cudaMemcpyAsync(F64(W.r64, r), F64(W.eta, r), fs * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      blas_axpy<double>(F64(W.t64, r), F64(W.r64, r), -1.0, 0.0, n, s);
-    }
+    DW_CUDA(cudaMemcpyAsync(W.r64, W.eta, fb64, cudaMemcpyDeviceToDevice, s));
+    blas_axpy<double>(W.t64, W.r64, -1.0, 0.0, n * nrhs, s);   // the batch's fields are contiguous
     tm.end();
     return norms64(W.r64, rn);
   };
@@ -450,7 +448,7 @@ int solve_batch_f32(dw_ctx* c, dfl_ctx* d, const sol_params* p, int nrhs, const 
       tm.end();
       if (d) {
         tm.begin(PH_PROJECT);
-        for (int r = 0; r < nrhs; ++r) blas_dot<float>(c, F32(W.chi[k], r), F32(W.chi[k], r), n, dres + 3 * r, s);
+        blas_dot_batch<float>(c, W.chi[k], W.chi[k], n, fs, nrhs, dres, s);
         dfl_restrict_mrhs_f32(d, W.chi[k], W.lc, nrhs, s);
         tm.end();
         if ((rc = read_host(c, dres, 3 * nrhs, h.data(), s))) return rc;
@@ -470,38 +468,62 @@ int solve_batch_f32(dw_ctx* c, dfl_ctx* d, const sol_params* p, int nrhs, const 
           if (!use[r]) DW_CUDA(cudaMemsetAsync(W.lv + (size_t)r * Nl * 2, 0, (size_t)Nl * 2 * sizeof(float), s));
         dfl_prolong_mrhs_f32(d, W.lv, W.t1, 0, nrhs, s);
         dirac_mrhs<float>(c, W.t1, W.w, nrhs, c->tune_rgroup, s);
-        for (int r = 0; r < nrhs; ++r) blas_axpy<float>(F32(W.w, r), F32(W.chi[k], r), -1.0, 0.0, n, s);
+        blas_axpy<float>(W.w, W.chi[k], -1.0, 0.0, n * nrhs, s);   // contiguous fields
         tm.end();
       }
       tm.begin(PH_ORTH);
       if (k > 0) {
-        for (int r = 0; r < nrhs; ++r) {
-          std::vector<const float*> prev(k);
-          for (int j = 0; j < k; ++j) prev[j] = F32(W.chi[j], r);
-          blas_multi_dot<float>(c, prev.data(), k, F32(W.chi[k], r), n, dres + (size_t)r * 2 * nkv, s);
+        std::vector<const float*> prev0(k);
+        for (int j = 0; j < k; ++j) prev0[j] = W.chi[j];
+        const bool batched = nrhs <= 16;
+        if (batched) {
+          blas_multi_dot_batch<float>(c, prev0.data(), k, W.chi[k], n, fs, nrhs, dres, 2 * (size_t)nkv, s);
+        } else {
+          for (int r = 0; r < nrhs; ++r) {
+            std::vector<const float*> prev(k);
+            for (int j = 0; j < k; ++j) prev[j] = F32(W.chi[j], r);
+            blas_multi_dot<float>(c, prev.data(), k, F32(W.chi[k], r), n, dres + (size_t)r * 2 * nkv, s);
+          }
         }
         if ((rc = read_host(c, dres, 2 * nkv * nrhs, h.data(), s))) return rc;
-        for (int r = 0; r < nrhs; ++r) {
-          std::vector<const float*> prev(k);
-          for (int j = 0; j < k; ++j) {
-            prev[j] = F32(W.chi[j], r);
+        for (int r = 0; r < nrhs; ++r)
+          for (int j = 0; j < k; ++j)
             bb[((size_t)r * nkvmax + j) * nkvmax + k] = cd(h[r * 2 * nkv + 2 * j], h[r * 2 * nkv + 2 * j + 1]);
+        if (batched) {
+          blas_multi_axpy_batch<float>(prev0.data(), k, h.data(), 2 * (size_t)nkv, W.chi[k], n, fs, nrhs, s);
+        } else {
+          for (int r = 0; r < nrhs; ++r) {
+            std::vector<const float*> prev(k);
+            for (int j = 0; j < k; ++j) prev[j] = F32(W.chi[j], r);
+            blas_multi_axpy<float>(prev.data(), k, h.data() + (size_t)r * 2 * nkv, F32(W.chi[k], r), n, s);
           }
-          blas_multi_axpy<float>(prev.data(), k, h.data() + (size_t)r * 2 * nkv, F32(W.chi[k], r), n, s);
         }
       }
-      for (int r = 0; r < nrhs; ++r) blas_dot<float>(c, F32(W.chi[k], r), F32(W.rho, r), n, dres + 3 * r, s);
+      blas_dot_batch<float>(c, W.chi[k], W.rho, n, fs, nrhs, dres, s);
       if ((rc = read_host(c, dres, 3 * nrhs, h.data(), s))) return rc;
+      std::vector<double> sinv(nrhs, 0.0), sar(nrhs, 0.0), sai(nrhs, 0.0);
       for (int r = 0; r < nrhs; ++r) {
         double ck = sqrt(h[3 * r + 2]);
         if (!live[r] || !(ck > 0)) { live[r] = 0; continue; }
         cc[(size_t)r * nkvmax + k] = ck;
         a[(size_t)r * nkvmax + k] = cd(h[3 * r], h[3 * r + 1]) / ck;
         nsteps[r] = k + 1;
-        cd ak = a[(size_t)r * nkvmax + k];
-        blas_scale<float>(F32(W.chi[k], r), 1.0 / ck, 0.0, n, s);
-        blas_axpy<float>(F32(W.chi[k], r), F32(W.rho, r), -ak.real(), -ak.imag(), n, s);
-        blas_dot<float>(c, F32(W.rho, r), F32(W.rho, r), n, dres + 3 * r, s);
+        sinv[r] = 1.0 / ck;
+        sar[r] = a[(size_t)r * nkvmax + k].real();
+        sai[r] = a[(size_t)r * nkvmax + k].imag();
+      }
+      // chi_k /= c_k, rho -= a_k chi_k and |rho|^2 for the live right-hand sides in one launch
+      if (nrhs <= 16) {
+        if ((rc = gcr_step_batch(c, W.chi[k], W.rho, n, fs, nrhs, sinv.data(), sar.data(), sai.data(), live.data(),
+                                 dres, s)))
+          return rc;
+      } else {
+        for (int r = 0; r < nrhs; ++r) {
+          if (!live[r]) continue;
+          blas_scale<float>(F32(W.chi[k], r), sinv[r], 0.0, n, s);
+          blas_axpy<float>(F32(W.chi[k], r), F32(W.rho, r), -sar[r], -sai[r], n, s);
+          blas_dot<float>(c, F32(W.rho, r), F32(W.rho, r), n, dres + 3 * r, s);
+        }
       }
       if ((rc = read_host(c, dres, 3 * nrhs, h.data(), s))) return rc;
       tm.end();

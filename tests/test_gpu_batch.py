@@ -121,7 +121,7 @@ def test_multi_rhs_little_solver_matches_per_rhs(setup, dfl):
 def test_autotune(setup):
     ctx, D = setup
     rep = dw.dw_autotune(ctx, 4)
-    assert rep["rgroup"] in (1, 2, 3) and rep["sap_staged"] in (0, 1)
+    assert rep["rgroup"] in (0, 1, 2, 3) and rep["sap_staged"] in (0, 1)
     assert all(v > 0 for v in rep["dirac_mrhs_ms"].values())
 
 
