@@ -2263,55 +2263,60 @@ DW_D void dot2_acc(float& s, float& e, float f, dd x) {
 // c[L][k] = (phi^L_k, psi) for a double-float psi and the BF16 basis (its entries are exact FP32
 // numbers): per thread a compensated dot product (dot2_acc: about 11 FP32 operations per real
 // product, against about 30 for full double-float arithmetic), then the threads' s + e combined
-// in double-float arithmetic.  The result carries about twice the FP32 precision.
-template <int NS>
-__global__ void __launch_bounds__(128, 2) restrict_dd_bf16_kernel(Geom g, const int* __restrict__ sub, int nsub,
+// in double-float arithmetic.  The result carries about twice the FP32 precision.  The Ns basis
+// vectors are split over KG thread groups (warp-uniform), so each thread keeps 2 Ns / KG sums and
+// the CTA has KG times the threads in flight on the basis loads.
+template <int NS, int KG>
+__global__ void __launch_bounds__(128 * KG) restrict_dd_bf16_kernel(Geom g, const int* __restrict__ sub, int nsub,
                                                                    const uint4* __restrict__ b16,
                                                                    const dd* __restrict__ psi0, dd* __restrict__ c0,
                                                                    int nrhs, size_t fstride, size_t cstride) {
-  using WH = WarpHalve<dd, 2 * NS, 16>;
+  static_assert(NS % KG == 0, "the groups share the basis vectors evenly");
+  constexpr int KP = NS / KG;                        // basis vectors per group
+  using WH = WarpHalve<dd, 2 * KP, 16>;
   constexpr int MF = WH::final_m();
-  __shared__ dd sh[4][2 * NS];
+  __shared__ dd sh[4 * KG][2 * KP];
   const int L = blockIdx.x;
   const size_t V = g.V;
   const int nsite = nsub * g.svol;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int grp = threadIdx.x >> 7, tl = threadIdx.x & 127, k0 = grp * KP;
   for (int rhs = 0; rhs < nrhs; ++rhs) {
     const dd* psi = psi0 + (size_t)rhs * fstride;
     dd* c = c0 + (size_t)rhs * cstride;
-    float sa[2 * NS], ea[2 * NS];
+    float sa[2 * KP], ea[2 * KP];
 #pragma unroll
-    for (int m = 0; m < 2 * NS; ++m) sa[m] = ea[m] = 0.f;
-    for (int t = threadIdx.x; t < nsite; t += blockDim.x) {
+    for (int m = 0; m < 2 * KP; ++m) sa[m] = ea[m] = 0.f;
+    for (int t = tl; t < nsite; t += 128) {
       const long long i = dfl_site(g, sub, nsub, L, t);
       cplx<dd> p[12];
       load_site<dd, 12>(psi, V, i, p);
 #pragma unroll
-      for (int k = 0; k < NS; ++k) {
+      for (int kk = 0; kk < KP; ++kk) {
         cplx<float> f[12];
-        load_basis<float>(nullptr, b16, V, k, i, f);
+        load_basis<float>(nullptr, b16, V, k0 + kk, i, f);
 #pragma unroll
         for (int j = 0; j < 12; ++j) {   // (f, p) = sum conj(f) p
-          dot2_acc(sa[2 * k], ea[2 * k], f[j].re, p[j].re);
-          dot2_acc(sa[2 * k], ea[2 * k], f[j].im, p[j].im);
-          dot2_acc(sa[2 * k + 1], ea[2 * k + 1], f[j].re, p[j].im);
-          dot2_acc(sa[2 * k + 1], ea[2 * k + 1], -f[j].im, p[j].re);
+          dot2_acc(sa[2 * kk], ea[2 * kk], f[j].re, p[j].re);
+          dot2_acc(sa[2 * kk], ea[2 * kk], f[j].im, p[j].im);
+          dot2_acc(sa[2 * kk + 1], ea[2 * kk + 1], f[j].re, p[j].im);
+          dot2_acc(sa[2 * kk + 1], ea[2 * kk + 1], -f[j].im, p[j].re);
         }
       }
     }
-    dd acc[2 * NS];
+    dd acc[2 * KP];
 #pragma unroll
-    for (int m = 0; m < 2 * NS; ++m) acc[m] = dd_two_sum(sa[m], ea[m]);
+    for (int m = 0; m < 2 * KP; ++m) acc[m] = dd_two_sum(sa[m], ea[m]);
     int base = 0;
     WH::run(acc, lane, base);
 #pragma unroll
     for (int m = 0; m < MF; ++m) sh[w][base + m] = acc[m];
     __syncthreads();
-    if (threadIdx.x < 2 * NS) {
-      dd y = sh[0][threadIdx.x];
+    if (tl < 2 * KP) {                 // warps 4 grp .. 4 grp + 3 hold group grp's sums
+      dd y = sh[4 * grp][tl];
 #pragma unroll
-      for (int q = 1; q < 4; ++q) y += sh[q][threadIdx.x];
-      c[(size_t)L * 2 * NS + threadIdx.x] = y;
+      for (int q = 1; q < 4; ++q) y += sh[4 * grp + q][tl];
+      c[(size_t)L * 2 * NS + 2 * k0 + tl] = y;
     }
     __syncthreads();
   }
@@ -2328,8 +2333,8 @@ static bool launch_restrict_dd(dfl_ctx* d, const dd* psi, dd* c, cudaStream_t s)
     return false;
   } else {
     if (d->basis16 && !dd_dot2_disabled())
-      restrict_dd_bf16_kernel<NS><<<d->Nb, 128, 0, s>>>(d->c->g, d->d_sub, d->nsub, d->basis16, psi, c, 1,
-                                                        (size_t)d->c->V * 24, (size_t)d->N * 2);
+      restrict_dd_bf16_kernel<NS, (NS % 4 == 0 ? 4 : 2)><<<d->Nb, 128 * (NS % 4 == 0 ? 4 : 2), 0, s>>>(
+          d->c->g, d->d_sub, d->nsub, d->basis16, psi, c, 1, (size_t)d->c->V * 24, (size_t)d->N * 2);
     else
       restrict_ns_kernel<dd, NS><<<d->Nb, 128, 0, s>>>(d->c->g, d->d_sub, d->nsub, d->basis16 ? nullptr : d->basis64,
                                                        d->basis16, psi, c, 1, (size_t)d->c->V * 24, (size_t)d->N * 2);
