@@ -2322,6 +2322,40 @@ __global__ void __launch_bounds__(128 * KG) restrict_dd_bf16_kernel(Geom g, cons
   }
 }
 
+// psi = Phi c (the prolongation) for a double-float c and the BF16 basis: every output component a
+// compensated sum (dot2_acc) of its 2 Ns products of an exact FP32 basis entry with a double-float
+// coefficient; one thread per site.
+template <int NS>
+__global__ void __launch_bounds__(128) prolong_dd_bf16_kernel(Geom g, const int* __restrict__ sap2dfl,
+                                                              const uint4* __restrict__ b16,
+                                                              const dd* __restrict__ c, dd* __restrict__ psi) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= g.V) return;
+  const size_t V = g.V;
+  const int L = __ldg(sap2dfl + (int)(i >> g.lsvol));
+  const cplx<dd>* cc = reinterpret_cast<const cplx<dd>*>(c) + (size_t)L * NS;
+  float sa[24], ea[24];
+#pragma unroll
+  for (int m = 0; m < 24; ++m) sa[m] = ea[m] = 0.f;
+#pragma unroll 4
+  for (int k = 0; k < NS; ++k) {
+    const cplx<dd> ck = cc[k];
+    cplx<float> f[12];
+    load_basis<float>(nullptr, b16, V, k, i, f);
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {   // ck f_j
+      dot2_acc(sa[2 * j], ea[2 * j], f[j].re, ck.re);
+      dot2_acc(sa[2 * j], ea[2 * j], -f[j].im, ck.im);
+      dot2_acc(sa[2 * j + 1], ea[2 * j + 1], f[j].im, ck.re);
+      dot2_acc(sa[2 * j + 1], ea[2 * j + 1], f[j].re, ck.im);
+    }
+  }
+  cplx<dd> out[12];
+#pragma unroll
+  for (int j = 0; j < 12; ++j) out[j] = {dd_two_sum(sa[2 * j], ea[2 * j]), dd_two_sum(sa[2 * j + 1], ea[2 * j + 1])};
+  store_site<dd, 12>(psi, V, i, out);
+}
+
 // DW_DD_DOT2=0: full double-float arithmetic in the restriction (the compensated kernel's reference)
 static bool dd_dot2_disabled() {
   const char* e = getenv("DW_DD_DOT2");
@@ -2361,14 +2395,26 @@ int dfl_restrict_f64x(dfl_ctx* d, const double* psi, double* c, cudaStream_t s) 
   return DW_OK;
 }
 // psi = Phi c (add = 0) or psi += Phi c (add = 1), FP64 fields, double-float arithmetic
+template <int NS>
+static bool launch_prolong_dd(dfl_ctx* d, unsigned blocks, cudaStream_t s) {
+  if constexpr (NS == 0) {
+    return false;
+  } else {
+    prolong_dd_bf16_kernel<NS><<<blocks, 128, 0, s>>>(d->c->g, d->d_sap2dfl, d->basis16, d->ddl, d->ddf);
+    return true;
+  }
+}
 int dfl_prolong_f64x(dfl_ctx* d, const double* c, double* psi, int add, cudaStream_t s) {
   int rc = ensure_dd(d);
   if (rc) return rc;
   f64_to_dd(c, d->ddl, (size_t)d->N * 2, s);
   unsigned blocks = (unsigned)((d->c->V + 127) / 128);
-  prolong_kernel<dd><<<blocks, 128, 0, s>>>(d->c->g, d->d_sap2dfl, d->Ns, d->basis16 ? nullptr : d->basis64,
-                                            d->basis16, d->ddl, d->ddf, 0, 1, (size_t)d->c->V * 24,
-                                            (size_t)d->N * 2);
+  bool done = false;
+  if (d->basis16 && !dd_dot2_disabled()) NS_DISPATCH_FEW(d->Ns, (done = launch_prolong_dd<NSV>(d, blocks, s)));
+  if (!done)
+    prolong_kernel<dd><<<blocks, 128, 0, s>>>(d->c->g, d->d_sap2dfl, d->Ns, d->basis16 ? nullptr : d->basis64,
+                                              d->basis16, d->ddl, d->ddf, 0, 1, (size_t)d->c->V * 24,
+                                              (size_t)d->N * 2);
   dw_note_launch();
   dd_to_f64(d->ddf, psi, (size_t)d->c->V * 24, add, s);
   return DW_OK;
